@@ -1,0 +1,366 @@
+"""GB300 (sm_103a) contour-guided demons registration (CG-DIR, arXiv:1301.0970).
+
+Thin ctypes binding of ``libcgdir.so`` (the C ABI in ``include/cgdir.h``).
+Every step of the registration runs in the library's CUDA kernels; this
+module only marshals arguments.  PyTorch supplies device memory and the
+stream.  There is no CPU fallback: if the library has not been built (see
+``paper_1301_0970_gb300.build``) importing the binding's functions raises.
+
+The functions ``cgdir_*`` mirror the C entry points one to one and take raw
+pointers; ``Context`` wraps them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int, c_int8, c_longlong, c_size_t, c_uint, c_void_p
+from typing import List, Optional, Sequence
+
+from . import build as _build
+
+# ---- constants (include/cgdir.h) ------------------------------------------
+CGDIR_OK, CGDIR_EINVAL, CGDIR_ENOMEM, CGDIR_ECUDA, CGDIR_ETIMEDOUT, CGDIR_ECANCELED, CGDIR_EBUSY = range(7)
+CGDIR_F32, CGDIR_F16, CGDIR_BF16 = 0, 1, 2
+CGDIR_HOST, CGDIR_DEVICE = 0, 1
+CGDIR_STOP_FIXED, CGDIR_STOP_WINDOW10, CGDIR_STOP_PAPER_LITERAL = 0, 1, 2
+CGDIR_COMPOSE, CGDIR_ADDITIVE = 0, 1
+CGDIR_REASON_CAP, CGDIR_REASON_CONVERGED, CGDIR_REASON_SKIPPED = 0, 1, 2
+CGDIR_MAX_MASKS, CGDIR_MAX_LEVELS = 8, 8
+
+
+class cgdir_config(ctypes.Structure):
+    _fields_ = [("device", c_int), ("stream", c_void_p), ("mem_budget_bytes", c_size_t)]
+
+
+class cgdir_volume(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("dtype", c_int),
+                ("where", c_int), ("data", c_void_p)]
+
+
+class cgdir_masks(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("where", c_int),
+                ("data", POINTER(c_void_p)), ("count", c_int)]
+
+
+class cgdir_params(ctypes.Structure):
+    _fields_ = [("levels", c_int), ("iters", POINTER(c_int)), ("sigma_fluid", c_float),
+                ("sigma_diff", c_float), ("lambda_", POINTER(c_float)), ("sign", POINTER(c_int8)),
+                ("contour_level_mask", c_uint), ("stop_mode", c_int), ("eps", c_double),
+                ("spacing_mm", c_double * 3), ("margin_mm", c_double),
+                ("intensity_offset", c_float), ("compose_mode", c_int),
+                ("init_dvf", c_void_p), ("init_dvf_where", c_int)]
+
+
+class cgdir_level_stats(ctypes.Structure):
+    _fields_ = [("level", c_int), ("nx", c_int), ("ny", c_int), ("nz", c_int),
+                ("iters_run", c_int), ("stop_reason", c_int), ("hist_len", c_int),
+                ("rms_id", POINTER(c_double))]
+
+
+_SIGNATURES = {
+    "cgdir_default_params": (None, [POINTER(cgdir_params)]),
+    "cgdir_create": (c_int, [POINTER(c_void_p), POINTER(cgdir_config)]),
+    "cgdir_destroy": (None, [c_void_p]),
+    "cgdir_strerror": (ctypes.c_char_p, [c_int]),
+    "cgdir_last_error": (ctypes.c_char_p, [c_void_p]),
+    "cgdir_mem_in_use": (c_size_t, [c_void_p]),
+    "cgdir_register": (c_int, [c_void_p, POINTER(cgdir_volume), POINTER(cgdir_volume),
+                               POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
+                               c_void_p, c_int, POINTER(cgdir_level_stats)]),
+    "cgdir_pack_masks": (c_int, [c_void_p, POINTER(c_void_p), c_int, c_size_t, c_void_p]),
+    "cgdir_warp": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "cgdir_force": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                            POINTER(c_float), POINTER(c_int8), c_float, c_int, c_void_p, c_int,
+                            c_int, c_int, c_void_p, c_void_p, POINTER(c_double)]),
+    "cgdir_smooth": (c_int, [c_void_p, c_void_p, c_int, c_float, c_int, c_int, c_int, c_void_p]),
+    "cgdir_compose": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_float, c_int, c_int, c_int,
+                              c_void_p]),
+    "cgdir_iterate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                              POINTER(c_float), POINTER(c_int8), c_float, c_int, c_float, c_float,
+                              c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
+                              POINTER(c_double)]),
+    "cgdir_restrict_image": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "cgdir_restrict_bits": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "cgdir_prolong": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_int,
+                              c_void_p]),
+    "cgdir_uroi": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, POINTER(c_double),
+                           c_double, c_void_p]),
+    "cgdir_auto_sign": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                POINTER(c_int8)]),
+    "cgdir_rms_id": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int,
+                             c_int, POINTER(c_double), POINTER(c_longlong)]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libcgdir.so (building it with nvcc if it is missing or stale).
+    Raises if it cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CG-DIR CUDA library missing at {path}; build it with "
+                           "`python -m paper_1301_0970_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class CgdirError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} [{status}]")
+        self.status = status
+
+
+def _lib_fn(name):
+    def call(*args):
+        return getattr(load(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+# the C entry points, same names, raw arguments
+for _name in _SIGNATURES:
+    globals()[_name] = _lib_fn(_name)
+
+
+# --------------------------------------------------------------------------- #
+# torch-facing wrapper
+# --------------------------------------------------------------------------- #
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+def _dims(t):
+    nz, ny, nx = t.shape[-3:]
+    return int(nx), int(ny), int(nz)
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    return {torch.float32: CGDIR_F32, torch.float16: CGDIR_F16, torch.bfloat16: CGDIR_BF16}[t.dtype]
+
+
+class Context:
+    """One device + one stream (default: torch's current stream on `device`)."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget_bytes: int = 0):
+        torch = _torch()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        cfg = cgdir_config(device, c_void_p(int(stream.cuda_stream)), mem_budget_bytes)
+        h = c_void_p()
+        st = load().cgdir_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != CGDIR_OK:
+            raise CgdirError(st, f"cgdir_create: {load().cgdir_strerror(st).decode()}")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cgdir_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int, what: str):
+        if st != CGDIR_OK:
+            lib = load()
+            raise CgdirError(st, f"{what}: {lib.cgdir_strerror(st).decode()}: "
+                                 f"{lib.cgdir_last_error(self._h).decode()}")
+
+    def mem_in_use(self) -> int:
+        return int(load().cgdir_mem_in_use(self._h))
+
+    # ---- whole registration ------------------------------------------------
+    def register(self, static, moving, static_masks=None, moving_masks=None, *,
+                 levels: int = 2, iters: Sequence[int] = (100, 50), sigma_fluid: float = 1.0,
+                 sigma_diff: float = 1.0, lam: Optional[Sequence[float]] = None,
+                 sign: Optional[Sequence[int]] = None, contour_level_mask: Optional[int] = None,
+                 stop_mode: int = CGDIR_STOP_WINDOW10, eps: float = 1e-4,
+                 spacing_mm=(1.97, 1.97, 2.5), margin_mm: float = 10.0,
+                 intensity_offset: float = 1000.0, compose_mode: int = CGDIR_COMPOSE,
+                 init_dvf=None, dvf_out=None):
+        """Algorithm A on (static, moving) [nz,ny,nx] tensors (CUDA or CPU;
+        float32/16/bf16) with k-long lists (or [k,nz,ny,nx] tensors) of uint8
+        masks.  Returns (dvf [3,nz,ny,nx] float32, stats list coarse->fine)."""
+        torch = _torch()
+        nx, ny, nz = _dims(static)
+        sm = list(static_masks) if static_masks is not None else []
+        mm = list(moving_masks) if moving_masks is not None else []
+        k = len(sm)
+        S = cgdir_volume(nx, ny, nz, _dtype_code(static), CGDIR_DEVICE if static.is_cuda else CGDIR_HOST,
+                         c_void_p(_ptr(static)))
+        M = cgdir_volume(*_dims(moving), _dtype_code(moving),
+                         CGDIR_DEVICE if moving.is_cuda else CGDIR_HOST, c_void_p(_ptr(moving)))
+        for m in sm + mm:
+            if m.dtype != torch.uint8 or not m.is_contiguous():
+                raise ValueError("masks must be contiguous uint8 tensors")
+        sptr = (c_void_p * max(k, 1))(*[c_void_p(_ptr(m)) for m in sm])
+        mptr = (c_void_p * max(len(mm), 1))(*[c_void_p(_ptr(m)) for m in mm])
+        SMk = cgdir_masks(nx, ny, nz, CGDIR_DEVICE if (k and sm[0].is_cuda) else CGDIR_HOST,
+                          ctypes.cast(sptr, POINTER(c_void_p)), k)
+        MMk = cgdir_masks(nx, ny, nz, CGDIR_DEVICE if (mm and mm[0].is_cuda) else CGDIR_HOST,
+                          ctypes.cast(mptr, POINTER(c_void_p)), len(mm))
+        it = (c_int * levels)(*[int(v) for v in iters])
+        p = cgdir_params()
+        load().cgdir_default_params(ctypes.byref(p))
+        p.levels = levels
+        p.iters = ctypes.cast(it, POINTER(c_int))
+        p.sigma_fluid, p.sigma_diff = sigma_fluid, sigma_diff
+        lam_a = (c_float * max(k, 1))(*([float(v) for v in lam] if lam is not None else [1e-3] * k))
+        p.lambda_ = ctypes.cast(lam_a, POINTER(c_float))
+        sg_a = (c_int8 * max(k, 1))(*([int(v) for v in sign] if sign is not None else [0] * k))
+        p.sign = ctypes.cast(sg_a, POINTER(c_int8))
+        p.contour_level_mask = (1 << (levels - 1)) if contour_level_mask is None else contour_level_mask
+        p.stop_mode, p.eps = stop_mode, eps
+        p.spacing_mm = (c_double * 3)(*spacing_mm)
+        p.margin_mm = margin_mm
+        p.intensity_offset = intensity_offset
+        p.compose_mode = compose_mode
+        if init_dvf is not None:
+            p.init_dvf = c_void_p(_ptr(init_dvf))
+            p.init_dvf_where = CGDIR_DEVICE if init_dvf.is_cuda else CGDIR_HOST
+        if dvf_out is None:
+            dvf_out = torch.empty((3, nz, ny, nx), dtype=torch.float32,
+                                  device=static.device if static.is_cuda else "cpu")
+        stats = (cgdir_level_stats * levels)()
+        st = load().cgdir_register(self._h, ctypes.byref(S), ctypes.byref(M), ctypes.byref(SMk),
+                                   ctypes.byref(MMk), ctypes.byref(p), c_void_p(_ptr(dvf_out)),
+                                   CGDIR_DEVICE if dvf_out.is_cuda else CGDIR_HOST, stats)
+        self._check(st, "cgdir_register")
+        out = []
+        for s in stats:
+            hist = [s.rms_id[i] for i in range(s.hist_len)] if s.hist_len else []
+            out.append({"level": s.level, "shape": (s.nz, s.ny, s.nx), "iters_run": s.iters_run,
+                        "stop_reason": s.stop_reason, "rms_id": hist})
+        return dvf_out, out
+
+    # ---- primitives ------------------------------------------------------------
+    def pack_masks(self, masks, out=None):
+        torch = _torch()
+        masks = list(masks)
+        n = masks[0].numel() if masks else 0
+        if out is None:
+            out = torch.empty(masks[0].shape, dtype=torch.uint8, device=masks[0].device)
+        ptrs = (c_void_p * max(len(masks), 1))(*[c_void_p(_ptr(m)) for m in masks])
+        self._check(load().cgdir_pack_masks(self._h, ptrs, len(masks), n, c_void_p(_ptr(out))),
+                    "cgdir_pack_masks")
+        return out
+
+    def warp(self, f, u, out=None):
+        out = _torch().empty_like(f) if out is None else out
+        self._check(load().cgdir_warp(self._h, _ptr(f), _ptr(u), *_dims(f), _ptr(out)), "cgdir_warp")
+        return out
+
+    def force(self, I0, T0, mbits, sbits, lam, sign, u, *, offset=1000.0, contour=True, uroi=None,
+              du=None, warped=None, want_stats=False):
+        torch = _torch()
+        k = len(lam)
+        du = torch.empty((3,) + tuple(I0.shape), dtype=torch.float32, device=I0.device) if du is None else du
+        lam_a = (c_float * max(k, 1))(*[float(v) for v in lam])
+        sg_a = (c_int8 * max(k, 1))(*[int(v) for v in sign])
+        stats = (c_double * 3)() if want_stats else None
+        st = load().cgdir_force(self._h, _ptr(I0), _ptr(T0), _ptr(mbits), _ptr(sbits), _ptr(uroi), k,
+                                lam_a, sg_a, offset, int(bool(contour)), _ptr(u), *_dims(I0), _ptr(du),
+                                _ptr(warped), stats)
+        self._check(st, "cgdir_force")
+        return (du, list(stats)) if want_stats else du
+
+    def smooth(self, f, sigma, out=None):
+        ncomp = 1 if f.dim() == 3 else int(f.shape[0])
+        out = _torch().empty_like(f) if out is None else out
+        self._check(load().cgdir_smooth(self._h, _ptr(f), ncomp, sigma, *_dims(f), _ptr(out)), "cgdir_smooth")
+        return out
+
+    def compose(self, u, du, mode=CGDIR_COMPOSE, sigma=0.0, out=None):
+        out = _torch().empty_like(u) if out is None else out
+        self._check(load().cgdir_compose(self._h, _ptr(u), _ptr(du), mode, sigma, *_dims(u), _ptr(out)),
+                    "cgdir_compose")
+        return out
+
+    def iterate(self, I0, T0, mbits, sbits, lam, sign, u, *, offset=1000.0, contour=True, uroi=None,
+                sigma_fluid=1.0, sigma_diff=1.0, compose_mode=CGDIR_COMPOSE, out=None, du_out=None,
+                want_stats=False):
+        k = len(lam)
+        out = _torch().empty_like(u) if out is None else out
+        lam_a = (c_float * max(k, 1))(*[float(v) for v in lam])
+        sg_a = (c_int8 * max(k, 1))(*[int(v) for v in sign])
+        stats = (c_double * 3)() if want_stats else None
+        st = load().cgdir_iterate(self._h, _ptr(I0), _ptr(T0), _ptr(mbits), _ptr(sbits), _ptr(uroi), k,
+                                  lam_a, sg_a, offset, int(bool(contour)), sigma_fluid, sigma_diff,
+                                  compose_mode, _ptr(u), *_dims(I0), _ptr(out), _ptr(du_out), stats)
+        self._check(st, "cgdir_iterate")
+        return (out, list(stats)) if want_stats else out
+
+    def restrict_image(self, f):
+        nx, ny, nz = _dims(f)
+        out = _torch().empty(((nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2), dtype=f.dtype, device=f.device)
+        self._check(load().cgdir_restrict_image(self._h, _ptr(f), nx, ny, nz, _ptr(out)), "cgdir_restrict_image")
+        return out
+
+    def restrict_bits(self, b):
+        nx, ny, nz = _dims(b)
+        out = _torch().empty(((nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2), dtype=b.dtype, device=b.device)
+        self._check(load().cgdir_restrict_bits(self._h, _ptr(b), nx, ny, nz, _ptr(out)), "cgdir_restrict_bits")
+        return out
+
+    def prolong(self, uc, fine_shape):
+        cx, cy, cz = _dims(uc)
+        nz, ny, nx = fine_shape
+        out = _torch().empty((3, nz, ny, nx), dtype=uc.dtype, device=uc.device)
+        self._check(load().cgdir_prolong(self._h, _ptr(uc), cx, cy, cz, nx, ny, nz, _ptr(out)), "cgdir_prolong")
+        return out
+
+    def uroi(self, sbits, k, spacing=(1.97, 1.97, 2.5), margin=10.0):
+        nx, ny, nz = _dims(sbits)
+        out = _torch().empty_like(sbits)
+        sp = (c_double * 3)(*spacing)
+        self._check(load().cgdir_uroi(self._h, _ptr(sbits), k, nx, ny, nz, sp, margin, _ptr(out)), "cgdir_uroi")
+        return out
+
+    def auto_sign(self, T0, sbits, k) -> List[int]:
+        out = (c_int8 * max(k, 1))()
+        self._check(load().cgdir_auto_sign(self._h, _ptr(T0), _ptr(sbits), k, *_dims(T0), out),
+                    "cgdir_auto_sign")
+        return [int(out[i]) for i in range(k)]
+
+    def rms_id(self, I0, T0, u, uroi=None):
+        r = c_double()
+        c = c_longlong()
+        self._check(load().cgdir_rms_id(self._h, _ptr(I0), _ptr(T0), _ptr(u), _ptr(uroi), *_dims(I0),
+                                        ctypes.byref(r), ctypes.byref(c)), "cgdir_rms_id")
+        return float(r.value), int(c.value)

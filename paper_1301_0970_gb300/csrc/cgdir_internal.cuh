@@ -1,0 +1,117 @@
+// Internal declarations of the CG-DIR CUDA library (sm_103a).  Kernels live
+// in kernels_*.cu, each with a host launcher declared here; runtime.cu owns
+// the contexts, the pyramid and the C ABI of include/cgdir.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "cgdir.h"
+
+namespace cgdir {
+
+constexpr int kMaxMasks = CGDIR_MAX_MASKS;
+constexpr int kMaxRadius = 6;            // Gaussian radius ceil(3 sigma), sigma <= 2
+
+struct Grid {
+    int nx, ny, nz;
+    __host__ __device__ size_t n() const { return (size_t)nx * ny * nz; }
+};
+
+__host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+__host__ __device__ __forceinline__ size_t vox(int x, int y, int z, int nx, int ny) {
+    return ((size_t)z * ny + y) * nx + x;
+}
+
+// Trilinear corner set of a continuous position: coordinates clamped to
+// [0, n-1], lower corner floor(p), upper corner clamped, weight p - floor(p).
+struct Corners {
+    int x0, x1, y0, y1, z0, z1;
+    float wx, wy, wz;
+};
+__device__ __forceinline__ Corners corners(float px, float py, float pz, int nx, int ny, int nz) {
+    Corners c;
+    px = fminf(fmaxf(px, 0.f), (float)(nx - 1));
+    py = fminf(fmaxf(py, 0.f), (float)(ny - 1));
+    pz = fminf(fmaxf(pz, 0.f), (float)(nz - 1));
+    float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+    c.x0 = (int)fx; c.y0 = (int)fy; c.z0 = (int)fz;
+    c.x1 = min(c.x0 + 1, nx - 1); c.y1 = min(c.y0 + 1, ny - 1); c.z1 = min(c.z0 + 1, nz - 1);
+    c.wx = px - fx; c.wy = py - fy; c.wz = pz - fz;
+    return c;
+}
+
+// Gaussian taps for kernel 1: exp(-j^2 / (2 sigma^2)) / sum, j in [-R, R].
+struct Taps {
+    int r;
+    float w[2 * kMaxRadius + 1];
+};
+int gauss_radius(float sigma);
+Taps gauss_taps(float sigma);
+
+// Per-block partial sums of the stopping metric: {sum (I0~ - T0)^2 over the
+// UROI, UROI count, max |du|}, FP64, written by the force / metric kernels.
+constexpr int kPartialStride = 4;
+
+struct ForceArgs {
+    const float *I0, *T0;
+    const uint8_t *mbits, *sbits, *uroi;
+    const float *u;
+    float *du, *warped;
+    double *partial;          // [gridDim.x*gridDim.y*gridDim.z][kPartialStride] or null
+    const int *stop_flag;     // kernels return at once when *stop_flag != 0 (may be null)
+    int nx, ny, nz;
+    int k, contour;
+    float offset;
+    float lambda[kMaxMasks];
+    float half_sign[kMaxMasks];   // s_i / 2
+};
+
+// Device-side state of one level's stopping logic, updated by finalize.
+struct LevelState {
+    double *hist;       // [hist_cap]
+    int *hist_len;
+    int *iters_run;
+    int *stop_reason;
+    int *stop_flag;
+    int hist_cap;
+};
+
+// ---- launchers (return the launch status; all async on `s`) ------------
+cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s);
+size_t force_partial_count(int nx, int ny, int nz, int zchunk);
+int force_default_zchunk(int nx, int ny, int nz);
+cudaError_t launch_metric(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
+                          int nx, int ny, int nz, double *partial, const int *stop_flag,
+                          int *nblocks_out, cudaStream_t s);
+size_t metric_partial_count(int nx, int ny, int nz);
+cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
+                            int stop_mode, double eps, double *stats_out, cudaStream_t s);
+
+cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int ny, int nz,
+                          float *out, const int *stop_flag, cudaStream_t s);
+cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
+                           float *out, const int *stop_flag, cudaStream_t s);
+cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,
+                        cudaStream_t s);
+
+cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint8_t *bits,
+                              cudaStream_t s);
+cudaError_t launch_restrict_image(const float *in, int nx, int ny, int nz, float *out,
+                                  cudaStream_t s);
+cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint8_t *out,
+                                 cudaStream_t s);
+cudaError_t launch_prolong(const float *uc, int cx, int cy, int cz, int nx, int ny, int nz,
+                           float *uf, cudaStream_t s);
+cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, const double *spacing,
+                        double margin, uint8_t *scratch_rowdist, uint8_t *out, cudaStream_t s);
+cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int nx, int ny, int nz,
+                             uint8_t *tmp_a, uint8_t *tmp_b, double *partial,
+                             double *sums /* [k][4] */, cudaStream_t s);
+size_t sign_partial_rows(size_t n);
+cudaError_t launch_convert_image(const void *in, int dtype, size_t n, float *out, cudaStream_t s);
+
+}  // namespace cgdir

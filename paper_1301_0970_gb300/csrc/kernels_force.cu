@@ -1,0 +1,356 @@
+// Moving-vector kernel of CG-DIR (kernels 2, 3 and the image half of 4 in
+// Sec. 2.2; Algorithm A steps 1, 5 and 6): warp of the moving image and of
+// the structure terms, central-difference gradients, the amplitude v of
+// Eq. 7 with beta = (T0 - I0~)^2, du = v n, and the per-block partial sums of
+// the UROI RMS-ID.  Plus the metric-only warp and the deterministic FP64
+// finalisation of the stopping metric.
+//
+// Structure terms without stored modified images: with J = I0 + offset and
+// m_i(c) the moving mask bit at interpolation corner c,
+//   I_i~ = sum_c w_c (1 + s_i m_i(c)/2) J(c) = J~ + (s_i/2) P_i,
+//   P_i  = sum_c w_c m_i(c) J(c),
+// and J~ = I0~ + offset, so grad I_i~ = grad I0~ + (s_i/2) grad P_i and
+//   a_i = grad I_i~ . n = |grad I0~| + (s_i/2) grad P_i . n,
+//   r_i = T_i - I_i~ = r0 + (s_i/2) (n_i (T0 + offset) - P_i).
+// These are the quantities of Eq. 7 rearranged exactly; only P_i (k values)
+// is interpolated per point besides I0~.
+//
+// Tiling: a CTA owns a 32 x 8 column of voxels in x-y and marches along z
+// over `zchunk` planes.  For each plane it interpolates I0~ and P_i at the
+// (32+2) x (8+2) points of the tile plus a one-voxel halo into a three-plane
+// ring in shared memory; the gradients of the middle plane are then read
+// from the ring.  Halo points outside the volume take the clamped index,
+// which reproduces the clamped central difference at the border.
+#include "cgdir_internal.cuh"
+
+namespace cgdir {
+
+namespace {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Fixed-order block reduction of (ssd, count, max) into partial[bid].
+template <int NTHREADS>
+__device__ void block_partial(double ssd, double cnt, float mx, double *partial, int bid) {
+    __shared__ double rs[NTHREADS / 32], rc[NTHREADS / 32];
+    __shared__ float rm[NTHREADS / 32];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    ssd = warp_sum(ssd);
+    cnt = warp_sum(cnt);
+    mx = warp_max(mx);
+    if ((tid & 31) == 0) { rs[tid >> 5] = ssd; rc[tid >> 5] = cnt; rm[tid >> 5] = mx; }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0, c = 0;
+        float m = 0.f;
+        for (int w = 0; w < NTHREADS / 32; ++w) { s += rs[w]; c += rc[w]; m = fmaxf(m, rm[w]); }
+        partial[(size_t)bid * kPartialStride + 0] = s;
+        partial[(size_t)bid * kPartialStride + 1] = c;
+        partial[(size_t)bid * kPartialStride + 2] = (double)m;
+        partial[(size_t)bid * kPartialStride + 3] = 0.0;
+    }
+}
+
+// Interpolate I0~ and the k structure sums P_i at the halo points of plane zz.
+// slot layout: [1 + k][HP].
+template <bool CONTOUR>
+__device__ __forceinline__ void force_plane(const ForceArgs &a, int zz, float *slot, int x0, int y0,
+                                            int tid) {
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const size_t N = (size_t)nx * ny * nz;
+    const int gz = clampi(zz, 0, nz - 1);
+    for (int p = tid; p < HP; p += NT) {
+        const int hx = p % HX, hy = p / HX;
+        const int gx = clampi(x0 - 1 + hx, 0, nx - 1), gy = clampi(y0 - 1 + hy, 0, ny - 1);
+        const size_t i = vox(gx, gy, gz, nx, ny);
+        const float ux = __ldg(a.u + i), uy = __ldg(a.u + N + i), uz = __ldg(a.u + 2 * N + i);
+        const Corners c = corners((float)gx + ux, (float)gy + uy, (float)gz + uz, nx, ny, nz);
+        float acc = 0.f;
+        float P[kMaxMasks];
+#pragma unroll
+        for (int j = 0; j < kMaxMasks; ++j) P[j] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int cx = (q & 1) ? c.x1 : c.x0;
+            const int cy = (q & 2) ? c.y1 : c.y0;
+            const int cz = (q & 4) ? c.z1 : c.z0;
+            const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
+                            ((q & 4) ? c.wz : 1.f - c.wz);
+            const size_t ci = vox(cx, cy, cz, nx, ny);
+            const float v = __ldg(a.I0 + ci);
+            acc = fmaf(w, v, acc);
+            if (CONTOUR) {
+                const unsigned b = __ldg(a.mbits + ci);
+                const float wj = w * (v + a.offset);
+#pragma unroll
+                for (int j = 0; j < kMaxMasks; ++j)
+                    if (j < a.k && ((b >> j) & 1u)) P[j] += wj;
+            }
+        }
+        slot[p] = acc;
+        if (CONTOUR) {
+#pragma unroll
+            for (int j = 0; j < kMaxMasks; ++j)
+                if (j < a.k) slot[(1 + j) * HP + p] = P[j];
+        }
+    }
+}
+
+template <bool CONTOUR>
+__global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
+    if (a.stop_flag && *a.stop_flag) return;
+    extern __shared__ float sm[];
+    const int plane = (1 + (CONTOUR ? a.k : 0)) * HP;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const size_t N = (size_t)nx * ny * nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    const int c = (ty + 1) * HX + (tx + 1);
+
+    force_plane<CONTOUR>(a, zb - 1, sm, x0, y0, tid);
+    force_plane<CONTOUR>(a, zb, sm + plane, x0, y0, tid);
+    double ssd = 0.0, cnt = 0.0;
+    float mx = 0.f;
+    for (int z = zb; z < ze; ++z) {
+        const int r = z - zb;
+        float *Pm = sm + (r % 3) * plane, *Pc = sm + ((r + 1) % 3) * plane,
+              *Pp = sm + ((r + 2) % 3) * plane;
+        force_plane<CONTOUR>(a, z + 1, Pp, x0, y0, tid);
+        __syncthreads();
+        if (act) {
+            const size_t i = vox(x, y, z, nx, ny);
+            const float w0 = Pc[c];
+            const float gx = 0.5f * (Pc[c + 1] - Pc[c - 1]);
+            const float gy = 0.5f * (Pc[c + HX] - Pc[c - HX]);
+            const float gz = 0.5f * (Pp[c] - Pm[c]);
+            const float T = __ldg(a.T0 + i);
+            const float r0 = T - w0;
+            if (a.warped) a.warped[i] = w0;
+            const float g2 = gx * gx + gy * gy + gz * gz;
+            float dux = 0.f, duy = 0.f, duz = 0.f;
+            if (g2 != 0.f) {
+                const float gn = sqrtf(g2);
+                const float inv = 1.f / gn;
+                const float nxv = gx * inv, nyv = gy * inv, nzv = gz * inv;
+                float num = gn * r0, den = gn * gn;
+                if (CONTOUR) {
+                    const unsigned sb = __ldg(a.sbits + i);
+                    const float Toff = T + a.offset;
+#pragma unroll
+                    for (int j = 0; j < kMaxMasks; ++j) {
+                        if (j < a.k) {
+                            const float *Pjm = Pm + (1 + j) * HP, *Pjc = Pc + (1 + j) * HP,
+                                        *Pjp = Pp + (1 + j) * HP;
+                            const float dPx = 0.5f * (Pjc[c + 1] - Pjc[c - 1]);
+                            const float dPy = 0.5f * (Pjc[c + HX] - Pjc[c - HX]);
+                            const float dPz = 0.5f * (Pjp[c] - Pjm[c]);
+                            const float hs = a.half_sign[j];
+                            const float aj = gn + hs * (dPx * nxv + dPy * nyv + dPz * nzv);
+                            const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
+                            const float rj = r0 + hs * (inside - Pjc[c]);
+                            num = fmaf(a.lambda[j] * aj, rj, num);
+                            den = fmaf(a.lambda[j] * aj, aj, den);
+                        }
+                    }
+                }
+                const float v = num / (den + r0 * r0);
+                dux = v * nxv; duy = v * nyv; duz = v * nzv;
+            }
+            a.du[i] = dux;
+            a.du[N + i] = duy;
+            a.du[2 * N + i] = duz;
+            if (a.uroi == nullptr || __ldg(a.uroi + i)) {
+                ssd += (double)(r0 * r0);
+                cnt += 1.0;
+            }
+            mx = fmaxf(mx, sqrtf(dux * dux + duy * duy + duz * duz));
+        }
+        __syncthreads();
+    }
+    if (a.partial)
+        block_partial<NT>(ssd, cnt, mx, a.partial,
+                          (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+// Metric-only pass: I0~ at every voxel and the UROI partial sums (the warp
+// of Algorithm A step 5 after a level's last update).
+constexpr int MT = 256;
+__global__ void __launch_bounds__(MT) k_metric(const float *__restrict__ I0,
+                                               const float *__restrict__ T0,
+                                               const float *__restrict__ u,
+                                               const uint8_t *__restrict__ uroi, int nx, int ny,
+                                               int nz, double *partial, const int *stop_flag) {
+    if (stop_flag && *stop_flag) return;
+    const size_t N = (size_t)nx * ny * nz;
+    double ssd = 0.0, cnt = 0.0;
+    for (size_t i = (size_t)blockIdx.x * MT + threadIdx.x; i < N; i += (size_t)gridDim.x * MT) {
+        if (uroi && !uroi[i]) continue;
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const Corners c = corners((float)x + __ldg(u + i), (float)y + __ldg(u + N + i),
+                                  (float)z + __ldg(u + 2 * N + i), nx, ny, nz);
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int cx = (q & 1) ? c.x1 : c.x0, cy = (q & 2) ? c.y1 : c.y0, cz = (q & 4) ? c.z1 : c.z0;
+            const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
+                            ((q & 4) ? c.wz : 1.f - c.wz);
+            acc = fmaf(w, __ldg(I0 + vox(cx, cy, cz, nx, ny)), acc);
+        }
+        const float r = __ldg(T0 + i) - acc;
+        ssd += (double)(r * r);
+        cnt += 1.0;
+    }
+    block_partial<MT>(ssd, cnt, 0.f, partial, blockIdx.x);
+}
+
+// Plain warp of one image (interpolation kernel 4).
+__global__ void k_warp(const float *__restrict__ f, const float *__restrict__ u, int nx, int ny,
+                       int nz, float *__restrict__ out) {
+    const size_t N = (size_t)nx * ny * nz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const Corners c = corners((float)x + __ldg(u + i), (float)y + __ldg(u + N + i),
+                                  (float)z + __ldg(u + 2 * N + i), nx, ny, nz);
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int cx = (q & 1) ? c.x1 : c.x0, cy = (q & 2) ? c.y1 : c.y0, cz = (q & 4) ? c.z1 : c.z0;
+            const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
+                            ((q & 4) ? c.wz : 1.f - c.wz);
+            acc = fmaf(w, __ldg(f + vox(cx, cy, cz, nx, ny)), acc);
+        }
+        out[i] = acc;
+    }
+}
+
+// Stopping test of Sec. 2.2 on delta^0..delta^n (same readings as the C ABI).
+__device__ int stop_test(const double *d, int n, int mode, double eps) {
+    if (mode == CGDIR_STOP_WINDOW10) return (n >= 10) && (d[n - 10] - d[n] <= eps);
+    if (mode == CGDIR_STOP_PAPER_LITERAL) {
+        if (n < 11) return 0;
+        const double ln = d[n] - d[n - 1], lm = d[n - 10] - d[n - 11];
+        return (lm - ln) <= eps;
+    }
+    return 0;
+}
+
+constexpr int FT = 256;
+__global__ void __launch_bounds__(FT) k_finalize(const double *__restrict__ partial, int nblocks,
+                                                 LevelState st, int n, int cap, int mode,
+                                                 double eps, double *stats_out) {
+    if (st.stop_flag && *st.stop_flag) return;
+    __shared__ double ss[FT], sc[FT], sx[FT];
+    double s = 0.0, c = 0.0, m = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += FT) {
+        s += partial[(size_t)b * kPartialStride + 0];
+        c += partial[(size_t)b * kPartialStride + 1];
+        m = fmax(m, partial[(size_t)b * kPartialStride + 2]);
+    }
+    ss[threadIdx.x] = s; sc[threadIdx.x] = c; sx[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = FT / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            ss[threadIdx.x] += ss[threadIdx.x + h];
+            sc[threadIdx.x] += sc[threadIdx.x + h];
+            sx[threadIdx.x] = fmax(sx[threadIdx.x], sx[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double S = ss[0], C = sc[0];
+        if (stats_out) { stats_out[0] = S; stats_out[1] = C; stats_out[2] = sx[0]; }
+        if (st.hist) {
+            const double d = C > 0 ? sqrt(S / C) : 0.0;
+            if (n < st.hist_cap) st.hist[n] = d;
+            *st.hist_len = n + 1;
+            if (stop_test(st.hist, n, mode, eps)) {
+                *st.stop_flag = 1; *st.iters_run = n; *st.stop_reason = CGDIR_REASON_CONVERGED;
+            } else if (n >= cap) {
+                *st.stop_flag = 1; *st.iters_run = n; *st.stop_reason = CGDIR_REASON_CAP;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int force_default_zchunk(int nx, int ny, int nz) {
+    const long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+    const long target = 152L * 6;   // resident CTAs on a full GPU
+    long chunks = (target + tiles - 1) / tiles;
+    if (chunks < 1) chunks = 1;
+    int zc = (int)((nz + chunks - 1) / chunks);
+    if (zc < 4) zc = 4;
+    return zc > nz ? nz : zc;
+}
+
+size_t force_partial_count(int nx, int ny, int nz, int zchunk) {
+    return (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zchunk - 1) / zchunk);
+}
+
+cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s) {
+    if (zchunk <= 0) zchunk = force_default_zchunk(a.nx, a.ny, a.nz);
+    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
+    dim3 block(TX, TY);
+    const bool contour = a.contour && a.k > 0;
+    const size_t smem = 3u * (1 + (contour ? a.k : 0)) * HP * sizeof(float);
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    if (contour) {
+        cudaFuncSetAttribute(k_force<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_force<true><<<grid, block, smem, s>>>(a, zchunk);
+    } else {
+        k_force<false><<<grid, block, smem, s>>>(a, zchunk);
+    }
+    return cudaGetLastError();
+}
+
+static int metric_grid(int nx, int ny, int nz) {
+    const size_t N = (size_t)nx * ny * nz;
+    size_t g = (N + MT - 1) / MT;
+    const size_t cap = 152 * 8;
+    return (int)(g < cap ? g : cap);
+}
+
+size_t metric_partial_count(int nx, int ny, int nz) { return (size_t)metric_grid(nx, ny, nz); }
+
+cudaError_t launch_metric(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
+                          int nx, int ny, int nz, double *partial, const int *stop_flag,
+                          int *nblocks_out, cudaStream_t s) {
+    const int g = metric_grid(nx, ny, nz);
+    if (nblocks_out) *nblocks_out = g;
+    k_metric<<<g, MT, 0, s>>>(I0, T0, u, uroi, nx, ny, nz, partial, stop_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
+                            int stop_mode, double eps, double *stats_out, cudaStream_t s) {
+    k_finalize<<<1, FT, 0, s>>>(partial, nblocks, st, n, cap, stop_mode, eps, stats_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,
+                        cudaStream_t s) {
+    const size_t N = (size_t)nx * ny * nz;
+    size_t g = (N + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    k_warp<<<(unsigned)g, 256, 0, s>>>(f, u, nx, ny, nz, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cgdir

@@ -1,0 +1,316 @@
+// Set-up kernels of CG-DIR: mask bit-packing, the factor-2 image pyramid and
+// the prolongation of the DVF between levels (multi-scale strategy,
+// Sec. 2.2), the UROI map of the stopping criterion (Sec. 2.2), the sums
+// behind the automatic sign of the modified images (Sec. 2.1) and image
+// type conversion.  None of these run per iteration.
+#include "cgdir_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace cgdir {
+
+namespace {
+
+unsigned flat_grid(size_t n, size_t cap = 152 * 16) {
+    size_t g = (n + 255) / 256;
+    if (g > cap) g = cap;
+    return (unsigned)(g ? g : 1);
+}
+
+struct MaskPtrs {
+    const uint8_t *p[kMaxMasks];
+};
+
+__global__ void k_pack(MaskPtrs m, int k, size_t n, uint8_t *__restrict__ bits) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        unsigned b = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxMasks; ++j)
+            if (j < k && __ldg(m.p[j] + i)) b |= 1u << j;
+        bits[i] = (uint8_t)b;
+    }
+}
+
+// 2x2x2 box mean, source indices clamped (odd sizes replicate the border).
+__global__ void k_restrict_image(const float *__restrict__ in, int nx, int ny, int nz,
+                                 float *__restrict__ out) {
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
+    const size_t Nc = (size_t)cx * cy * cz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < Nc;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(i % cx), Y = (int)((i / cx) % cy), Z = (int)(i / ((size_t)cx * cy));
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int x = min(2 * X + (q & 1), nx - 1), y = min(2 * Y + ((q >> 1) & 1), ny - 1),
+                      z = min(2 * Z + ((q >> 2) & 1), nz - 1);
+            s += __ldg(in + vox(x, y, z, nx, ny));
+        }
+        out[i] = s * 0.125f;
+    }
+}
+
+// Per bit: inside if at least 4 of the 8 source voxels are inside.
+__global__ void k_restrict_bits(const uint8_t *__restrict__ in, int nx, int ny, int nz,
+                                uint8_t *__restrict__ out) {
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
+    const size_t Nc = (size_t)cx * cy * cz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < Nc;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(i % cx), Y = (int)((i / cx) % cy), Z = (int)(i / ((size_t)cx * cy));
+        int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int x = min(2 * X + (q & 1), nx - 1), y = min(2 * Y + ((q >> 1) & 1), ny - 1),
+                      z = min(2 * Z + ((q >> 2) & 1), nz - 1);
+            const unsigned b = __ldg(in + vox(x, y, z, nx, ny));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cnt[j] += (b >> j) & 1u;
+        }
+        unsigned o = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o |= (cnt[j] >= 4 ? 1u : 0u) << j;
+        out[i] = (uint8_t)o;
+    }
+}
+
+// u_f(x) = 2 u_c((x + 0.5)/2 - 0.5), trilinear with clamped coordinates.
+__global__ void k_prolong(const float *__restrict__ uc, int cx, int cy, int cz, int nx, int ny,
+                          int nz, float *__restrict__ uf) {
+    const size_t N = (size_t)nx * ny * nz, Nc = (size_t)cx * cy * cz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const Corners c = corners((x + 0.5f) * 0.5f - 0.5f, (y + 0.5f) * 0.5f - 0.5f,
+                                  (z + 0.5f) * 0.5f - 0.5f, cx, cy, cz);
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+            const float *f = uc + comp * Nc;
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int qx = (q & 1) ? c.x1 : c.x0, qy = (q & 2) ? c.y1 : c.y0, qz = (q & 4) ? c.z1 : c.z0;
+                const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
+                                ((q & 4) ? c.wz : 1.f - c.wz);
+                acc = fmaf(w, __ldg(f + vox(qx, qy, qz, cx, cy)), acc);
+            }
+            uf[comp * N + i] = 2.f * acc;
+        }
+    }
+}
+
+// ---- UROI: exact ellipsoidal dilation in two passes -------------------
+// pass 1: per voxel, the distance |dx| (voxels) to the nearest union voxel of
+// its x-row within rx, 255 if none.  pass 2: a voxel is in the UROI if for
+// some row offset (dy, dz) that row holds a union voxel within the x extent
+// the ellipsoid allows at (dy, dz).  The extents are computed on the host
+// with the same double expression as the definition, so the decision equals
+// the brute-force test voxel by voxel.
+constexpr int kMaxUroiRadius = 15;
+struct UroiTable {
+    int rx, ry, rz;
+    int8_t ext[2 * kMaxUroiRadius + 1][2 * kMaxUroiRadius + 1];   // [dz][dy], -1 = none
+};
+
+__global__ void k_uroi_rows(const uint8_t *__restrict__ sbits, unsigned mask, int rx, int nx,
+                            int ny, int nz, uint8_t *__restrict__ rowdist) {
+    const size_t N = (size_t)nx * ny * nz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        int d = 255;
+        for (int dx = -rx; dx <= rx; ++dx) {
+            const int xx = x + dx;
+            if (xx < 0 || xx >= nx) continue;
+            if (__ldg(sbits + i - x + xx) & mask) d = min(d, abs(dx));
+        }
+        rowdist[i] = (uint8_t)d;
+    }
+}
+
+__global__ void k_uroi_dilate(const uint8_t *__restrict__ rowdist, UroiTable t, int nx, int ny,
+                              int nz, uint8_t *__restrict__ out) {
+    const size_t N = (size_t)nx * ny * nz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        uint8_t hit = 0;
+        for (int dz = -t.rz; dz <= t.rz && !hit; ++dz) {
+            const int zz = z + dz;
+            if (zz < 0 || zz >= nz) continue;
+            for (int dy = -t.ry; dy <= t.ry; ++dy) {
+                const int yy = y + dy;
+                if (yy < 0 || yy >= ny) continue;
+                const int e = t.ext[dz + t.rz][dy + t.ry];
+                if (e >= 0 && (int)__ldg(rowdist + vox(x, yy, zz, nx, ny)) <= e) { hit = 1; break; }
+            }
+        }
+        out[i] = hit;
+    }
+}
+
+__global__ void k_fill_u8(uint8_t *p, size_t n, uint8_t v) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// ---- automatic sign ---------------------------------------------------
+// Chebyshev dilation by 2 voxels of all mask bits, one axis per launch.
+__global__ void k_dilate_axis(const uint8_t *__restrict__ in, int axis, int nx, int ny, int nz,
+                              uint8_t *__restrict__ out) {
+    const size_t N = (size_t)nx * ny * nz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        unsigned b = 0;
+        for (int d = -2; d <= 2; ++d) {
+            int xx = x, yy = y, zz = z;
+            if (axis == 0) xx += d; else if (axis == 1) yy += d; else zz += d;
+            if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
+            b |= __ldg(in + vox(xx, yy, zz, nx, ny));
+        }
+        out[i] = (uint8_t)b;
+    }
+}
+
+constexpr int ST = 256;
+// Per block: {sum T0 inside j, count inside, sum T0 in shell, count shell}.
+__global__ void __launch_bounds__(ST) k_sign_partial(const float *__restrict__ T0,
+                                                     const uint8_t *__restrict__ sbits,
+                                                     const uint8_t *__restrict__ dil, int j,
+                                                     size_t n, double *__restrict__ partial) {
+    double a = 0, b = 0, c = 0, d = 0;
+    for (size_t i = (size_t)blockIdx.x * ST + threadIdx.x; i < n; i += (size_t)gridDim.x * ST) {
+        const bool in = (__ldg(sbits + i) >> j) & 1u;
+        const bool sh = !in && ((__ldg(dil + i) >> j) & 1u);
+        const double t = (double)__ldg(T0 + i);
+        if (in) { a += t; b += 1.0; }
+        if (sh) { c += t; d += 1.0; }
+    }
+    __shared__ double r[4][ST];
+    r[0][threadIdx.x] = a; r[1][threadIdx.x] = b; r[2][threadIdx.x] = c; r[3][threadIdx.x] = d;
+    __syncthreads();
+    for (int h = ST / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int q = 0; q < 4; ++q) r[q][threadIdx.x] += r[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) partial[(size_t)blockIdx.x * 4 + threadIdx.x] = r[threadIdx.x][0];
+}
+
+__global__ void k_sum_rows4(const double *__restrict__ partial, int rows, double *__restrict__ out) {
+    if (threadIdx.x < 4) {
+        double s = 0;
+        for (int b = 0; b < rows; ++b) s += partial[(size_t)b * 4 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ float to_f32(T v);
+template <>
+__device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__global__ void k_convert(const T *__restrict__ in, size_t n, float *__restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = to_f32<T>(in[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint8_t *bits,
+                              cudaStream_t s) {
+    MaskPtrs m{};
+    for (int j = 0; j < k && j < kMaxMasks; ++j) m.p[j] = masks[j];
+    k_pack<<<flat_grid(n), 256, 0, s>>>(m, k, n, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_image(const float *in, int nx, int ny, int nz, float *out,
+                                  cudaStream_t s) {
+    const size_t Nc = (size_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
+    k_restrict_image<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint8_t *out,
+                                 cudaStream_t s) {
+    const size_t Nc = (size_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
+    k_restrict_bits<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const float *uc, int cx, int cy, int cz, int nx, int ny, int nz,
+                           float *uf, cudaStream_t s) {
+    k_prolong<<<flat_grid((size_t)nx * ny * nz), 256, 0, s>>>(uc, cx, cy, cz, nx, ny, nz, uf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, const double *spacing,
+                        double margin, uint8_t *rowdist, uint8_t *out, cudaStream_t s) {
+    const size_t N = (size_t)nx * ny * nz;
+    if (k <= 0) {
+        k_fill_u8<<<flat_grid(N), 256, 0, s>>>(out, N, 1);
+        return cudaGetLastError();
+    }
+    if (!(margin >= 0.0) || !(spacing[0] > 0) || !(spacing[1] > 0) || !(spacing[2] > 0))
+        return cudaErrorInvalidValue;
+    UroiTable t{};
+    t.rx = (int)(margin / spacing[0]);
+    t.ry = (int)(margin / spacing[1]);
+    t.rz = (int)(margin / spacing[2]);
+    if (t.rx > kMaxUroiRadius || t.ry > kMaxUroiRadius || t.rz > kMaxUroiRadius)
+        return cudaErrorInvalidValue;
+    for (int dz = -t.rz; dz <= t.rz; ++dz)
+        for (int dy = -t.ry; dy <= t.ry; ++dy) {
+            int e = -1;
+            for (int dx = 0; dx <= t.rx; ++dx) {
+                const double d2 = (dx * spacing[0]) * (dx * spacing[0]) + (dy * spacing[1]) * (dy * spacing[1]) +
+                                  (dz * spacing[2]) * (dz * spacing[2]);
+                if (d2 <= margin * margin) e = dx;
+            }
+            t.ext[dz + t.rz][dy + t.ry] = (int8_t)e;
+        }
+    const unsigned mask = (k >= 8) ? 0xffu : ((1u << k) - 1u);
+    k_uroi_rows<<<flat_grid(N), 256, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist);
+    k_uroi_dilate<<<flat_grid(N), 256, 0, s>>>(rowdist, t, nx, ny, nz, out);
+    return cudaGetLastError();
+}
+
+// sums: device [k][4]; tmp_a, tmp_b: N bytes each; partial: sign_partial_rows(N) x 4 doubles.
+cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int nx, int ny,
+                                int nz, uint8_t *tmp_a, uint8_t *tmp_b, double *partial,
+                                double *sums, cudaStream_t s) {
+    const size_t N = (size_t)nx * ny * nz;
+    const unsigned g = flat_grid(N);
+    k_dilate_axis<<<g, 256, 0, s>>>(sbits, 0, nx, ny, nz, tmp_a);
+    k_dilate_axis<<<g, 256, 0, s>>>(tmp_a, 1, nx, ny, nz, tmp_b);
+    k_dilate_axis<<<g, 256, 0, s>>>(tmp_b, 2, nx, ny, nz, tmp_a);
+    const unsigned gp = flat_grid(N, 152 * 4);
+    for (int j = 0; j < k; ++j) {
+        k_sign_partial<<<gp, ST, 0, s>>>(T0, sbits, tmp_a, j, N, partial);
+        k_sum_rows4<<<1, 32, 0, s>>>(partial, (int)gp, sums + 4 * j);
+    }
+    return cudaGetLastError();
+}
+
+size_t sign_partial_rows(size_t n) { return flat_grid(n, 152 * 4); }
+
+cudaError_t launch_convert_image(const void *in, int dtype, size_t n, float *out, cudaStream_t s) {
+    if (dtype == CGDIR_F16)
+        k_convert<__half><<<flat_grid(n), 256, 0, s>>>((const __half *)in, n, out);
+    else if (dtype == CGDIR_BF16)
+        k_convert<__nv_bfloat16><<<flat_grid(n), 256, 0, s>>>((const __nv_bfloat16 *)in, n, out);
+    else
+        return cudaMemcpyAsync(out, in, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+}  // namespace cgdir

@@ -1,0 +1,346 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against
+the FP64 oracle on the same seeded inputs.
+
+Tolerances.  The kernels compute in FP32 and the oracle in FP64, so a value
+of magnitude |f| carries a rounding error of a few ulp(|f|) ~ 1e-7 |f| per
+operation.  Element-wise checks use 1e-5 of the field's scale (10 to 100
+ulps of headroom for the few dozen operations of a step).  The per-iteration
+DVF bar is the one the method's contract states: ||u_gpu - u_ref|| <= 1e-5
+||u_ref|| (plus an absolute floor of 1e-7 voxel per element for fields that
+are ~0), and the final DVF of a registration must be within 0.05 voxel RMS.
+Integer and mask work (bit packing, mask restriction, the UROI, the signs,
+iteration counts) must be bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import phantom
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1301_0970_gb300 as cg  # noqa: E402
+
+DEV = torch.device("cuda:0")
+RNG = np.random.default_rng(2024)
+SHAPES = [(9, 21, 45), (1, 1, 1), (3, 8, 32), (17, 33, 70), (5, 1, 7)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    with cg.Context(0) as c:
+        yield c
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def pack(masks):
+    b = np.zeros(masks.shape[1:], np.uint8)
+    for j in range(masks.shape[0]):
+        b |= (masks[j].astype(bool).astype(np.uint8) << j)
+    return b
+
+
+def close_elementwise(got, ref, rel=1e-5, floor=1e-6):
+    scale = max(float(np.abs(ref).max()), 1.0)
+    err = float(np.abs(got - ref).max())
+    assert err <= rel * scale + floor, f"max err {err:.3e} vs scale {scale:.3e}"
+
+
+def close_normwise(got, ref, rel=1e-5, floor=1e-7):
+    num = float(np.linalg.norm((got - ref).ravel()))
+    den = float(np.linalg.norm(ref.ravel()))
+    assert num <= rel * den + floor * math.sqrt(ref.size), f"{num:.3e} vs {rel:.0e} * {den:.3e}"
+
+
+def rand_field(shape, amp=2.5):
+    return RNG.uniform(-amp, amp, size=(3,) + shape).astype(np.float32)
+
+
+# ---------------------------------------------------------------- primitives
+@pytest.mark.parametrize("k", [0, 1, 5, 8])
+def test_pack_masks_bit_exact(ctx, k):
+    shape = (7, 13, 37)
+    m = (RNG.random((k,) + shape) < 0.3).astype(np.uint8) * RNG.integers(1, 255, size=(k,) + shape,
+                                                                           dtype=np.uint8)
+    out = ctx.pack_masks([dev(m[j]) for j in range(k)]) if k else None
+    if k:
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), pack(m))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_warp(ctx, shape):
+    f = (RNG.normal(size=shape) * 300).astype(np.float32)
+    u = rand_field(shape, 3.0)
+    got = host(ctx.warp(dev(f), dev(u)))
+    close_elementwise(got, oracle.warp(f, u))
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(8, 16, 64)])
+def test_restrict_image_and_bits(ctx, shape):
+    f = (RNG.normal(size=shape) * 300).astype(np.float32)
+    close_elementwise(host(ctx.restrict_image(dev(f))), oracle.restrict_image(f))
+    m = (RNG.random((8,) + shape) < 0.5).astype(np.uint8)
+    got = ctx.restrict_bits(dev(pack(m)))
+    torch.cuda.synchronize()
+    ref = pack(np.stack([oracle.restrict_mask(m[j]) for j in range(8)]))
+    assert np.array_equal(got.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("shape", [(5, 11, 23), (1, 1, 1), (4, 4, 4)])
+def test_prolong(ctx, shape):
+    fine = tuple(2 * s - (i % 2) for i, s in enumerate(shape))   # odd and even fine sizes
+    uc = rand_field(shape)
+    close_elementwise(host(ctx.prolong(dev(uc), fine)), oracle.prolong(uc, fine))
+
+
+@pytest.mark.parametrize("spacing,margin", [((1.97, 1.97, 2.5), 10.0), ((3.94, 3.94, 5.0), 10.0),
+                                            ((1.0, 1.0, 1.0), 3.0), ((2.0, 1.5, 1.0), 0.0)])
+def test_uroi_bit_exact(ctx, spacing, margin):
+    shape = (19, 27, 41)
+    m = np.zeros((3,) + shape, np.uint8)
+    m[0, 5:8, 10:14, 3:9] = 1
+    m[1, 15, 25, 39] = 1
+    m[2, 0:2, 0:3, 30:41] = 1
+    got = ctx.uroi(dev(pack(m)), 3, spacing, margin)
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), oracle.uroi(m, shape, spacing, margin))
+    allv = ctx.uroi(dev(pack(m)), 0, spacing, margin)
+    torch.cuda.synchronize()
+    assert int(allv.sum()) == int(np.prod(shape))
+
+
+def test_auto_sign_matches_oracle(ctx):
+    c = phantom.make_case("headneck256", shape=(24, 64, 64))
+    got = ctx.auto_sign(dev(c.static), dev(pack(c.static_masks)), c.k)
+    assert got == oracle.auto_sign(c.static, c.static_masks)
+
+
+@pytest.mark.parametrize("sigma", [1.0, 0.6, 2.0, 0.0])
+@pytest.mark.parametrize("shape", [(9, 21, 45), (17, 33, 70), (1, 1, 1), (2, 3, 1)])
+def test_smooth(ctx, sigma, shape):
+    u = rand_field(shape)
+    got = host(ctx.smooth(dev(u), sigma))
+    close_elementwise(got, oracle.gauss_field(u, sigma))
+    one = host(ctx.smooth(dev(u[0]), sigma))
+    close_elementwise(one, oracle.gauss(u[0], sigma))
+
+
+@pytest.mark.parametrize("mode", [cg.CGDIR_COMPOSE, cg.CGDIR_ADDITIVE])
+@pytest.mark.parametrize("sigma", [0.0, 1.0])
+def test_compose(ctx, mode, sigma):
+    shape = (9, 21, 45)
+    u, du = rand_field(shape, 4.0), rand_field(shape, 1.0)
+    got = host(ctx.compose(dev(u), dev(du), mode, sigma))
+    ref = oracle.compose(u, du, mode)
+    if sigma > 0:
+        ref = oracle.gauss_field(ref, sigma)
+    close_elementwise(got, ref)
+
+
+def case_inputs(shape=(12, 36, 40), masks=None, name="phantom64"):
+    c = phantom.make_case(name, shape=shape, masks=masks)
+    return c
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 8])
+@pytest.mark.parametrize("contour", [True, False])
+def test_force(ctx, k, contour):
+    c = case_inputs(shape=(11, 37, 45), name="headneck256")
+    sm = np.concatenate([c.static_masks] * 2)[:k]
+    mm = np.concatenate([c.moving_masks] * 2)[:k]
+    lam = list(RNG.uniform(1e-3, 1.0, size=k))
+    sign = [1 if j % 2 == 0 else -1 for j in range(k)]
+    u = (0.5 * c.u_gt).astype(np.float32)
+    ur = oracle.uroi(sm, c.shape) if k else np.ones(c.shape, np.uint8)
+    du, stats = ctx.force(dev(c.moving), dev(c.static), dev(pack(mm)), dev(pack(sm)), lam, sign,
+                          dev(u), contour=contour, uroi=dev(ur), want_stats=True)
+    ref, warped = oracle.force(c.moving, c.static, mm, sm, lam, sign, u=u, contour=contour,
+                               return_warped=True)
+    got = host(du)
+    close_normwise(got, ref)
+    sel = ur.astype(bool)
+    ssd = float(((warped - c.static)[sel] ** 2).sum())
+    assert stats[1] == sel.sum()
+    assert abs(stats[0] - ssd) <= 1e-5 * ssd + 1e-6
+    assert abs(stats[2] - float(np.sqrt((ref ** 2).sum(0)).max())) <= 1e-4
+
+
+def test_force_identical_images_is_exactly_zero(ctx):
+    c = case_inputs()
+    du = ctx.force(dev(c.static), dev(c.static), dev(pack(c.static_masks)), dev(pack(c.static_masks)),
+                   c.lam, c.signs, dev(np.zeros((3,) + c.shape, np.float32)))
+    torch.cuda.synchronize()
+    assert float(du.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("name,shape", [("phantom64", (12, 36, 40)), ("headneck256", (13, 45, 50)),
+                                        ("pelvis512", (10, 48, 40))])
+def test_single_iteration_meets_1e5(ctx, name, shape):
+    """One iteration (Algorithm A steps 1-4) from a nonzero DVF: relative
+    norm-wise difference <= 1e-5."""
+    c = phantom.make_case(name, shape=shape)
+    u = (0.7 * c.u_gt).astype(np.float32)
+    got = host(ctx.iterate(dev(c.moving), dev(c.static), dev(pack(c.moving_masks)),
+                           dev(pack(c.static_masks)), c.lam, c.signs, dev(u)))
+    ref = oracle.step(c.moving, c.static, c.moving_masks, c.static_masks, c.lam, c.signs, u)
+    close_normwise(got, ref, rel=1e-5)
+
+
+def test_rms_id(ctx):
+    c = case_inputs()
+    ur = oracle.uroi(c.static_masks, c.shape)
+    u = c.u_gt.astype(np.float32)
+    r, n = ctx.rms_id(dev(c.moving), dev(c.static), dev(u), dev(ur))
+    w = oracle.warp(c.moving, u)
+    ref, cnt = oracle.rms_id(w, c.static, ur)
+    assert n == cnt
+    assert abs(r - ref) <= 1e-5 * ref
+
+
+# --------------------------------------------------------- whole registration
+def run_both(c, levels, iters, **kw):
+    lam = kw.pop("lam", c.lam)
+    sign = kw.pop("sign", c.signs)
+    cmask = kw.pop("contour_level_mask", 1 << (levels - 1))
+    stop = kw.pop("stop_mode", cg.CGDIR_STOP_FIXED)
+    eps = kw.pop("eps", 1e-4)
+    with cg.Context(0) as ctx:
+        dvf, st = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                               [dev(m) for m in c.moving_masks], levels=levels, iters=iters, lam=lam,
+                               sign=sign, contour_level_mask=cmask, stop_mode=stop, eps=eps, **kw)
+        got = host(dvf)
+    ref, rst = oracle.register(c.static, c.moving, c.static_masks, c.moving_masks, levels=levels,
+                               iters=iters, lam=lam, sign=sign if sign is not None else None,
+                               contour_mask=cmask, stop_mode=stop, eps=eps)
+    return got, st, ref, rst
+
+
+def dvf_rms(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum(axis=0).mean()))
+
+
+def test_register_two_levels_matches_oracle():
+    c = phantom.make_case("phantom64", shape=(20, 48, 44))
+    got, st, ref, rst = run_both(c, 2, [40, 30], contour_level_mask=3)
+    assert [s["iters_run"] for s in st] == [40, 30]
+    assert dvf_rms(got, ref) <= 0.05
+    for s, r in zip(st, rst):
+        np.testing.assert_allclose(s["rms_id"], r["rms_id"], rtol=1e-3)
+
+
+def test_register_c1_full_config_matches_oracle():
+    """64x64x32, 2 masks, one level of 100 iterations, contour weight 1."""
+    c = phantom.make_case("phantom64")
+    got, st, ref, rst = run_both(c, 1, [100])
+    assert st[0]["iters_run"] == 100
+    assert dvf_rms(got, ref) <= 0.05
+
+
+def test_register_identical_images_give_zero_dvf():
+    c = phantom.make_case("phantom64", shape=(10, 30, 34))
+    c.moving = c.static.copy()
+    c.moving_masks = c.static_masks.copy()
+    got, st, _, _ = run_both(c, 2, [5, 5], contour_level_mask=3)
+    assert np.all(got == 0)
+    assert all(all(v == 0 for v in s["rms_id"]) for s in st)
+
+
+def test_register_without_masks_is_plain_demons_over_whole_volume():
+    c = phantom.make_case("phantom64", shape=(10, 30, 34))
+    c.static_masks = c.static_masks[:0]
+    c.moving_masks = c.moving_masks[:0]
+    got, st, ref, rst = run_both(c, 2, [10, 10], lam=[], sign=[])
+    assert dvf_rms(got, ref) <= 0.05
+
+
+def test_register_odd_sizes_three_levels_and_additive():
+    c = phantom.make_case("headneck256", shape=(13, 23, 37))
+    got, st, ref, rst = run_both(c, 3, [6, 4, 3], compose_mode=cg.CGDIR_ADDITIVE)
+    assert dvf_rms(got, ref) <= 0.05
+    assert [s["shape"] for s in st] == [(4, 6, 10), (7, 12, 19), (13, 23, 37)]
+
+
+def test_register_window10_stops_where_the_oracle_stops():
+    c = phantom.make_case("phantom64", shape=(12, 36, 40))
+    got, st, ref, rst = run_both(c, 1, [300], stop_mode=cg.CGDIR_STOP_WINDOW10, eps=5e-2)
+    assert st[0]["stop_reason"] == rst[0]["stop_reason"] == cg.CGDIR_REASON_CONVERGED
+    assert st[0]["iters_run"] == rst[0]["iters_run"]
+    assert dvf_rms(got, ref) <= 0.05
+
+
+def test_register_paper_literal_stops_at_eleven():
+    c = phantom.make_case("phantom64", shape=(12, 36, 40))
+    got, st, ref, rst = run_both(c, 1, [50], stop_mode=cg.CGDIR_STOP_PAPER_LITERAL)
+    assert st[0]["iters_run"] == rst[0]["iters_run"]
+
+
+def test_register_host_and_device_inputs_agree_bitwise():
+    c = phantom.make_case("phantom64", shape=(10, 30, 34))
+    kw = dict(levels=2, iters=[5, 5], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as ctx:
+        a, _ = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                            [dev(m) for m in c.moving_masks], **kw)
+        a = a.cpu()
+        b, _ = ctx.register(torch.from_numpy(c.static), torch.from_numpy(c.moving),
+                            [torch.from_numpy(m) for m in c.static_masks],
+                            [torch.from_numpy(m) for m in c.moving_masks], **kw)
+    assert torch.equal(a, b)
+
+
+def test_register_auto_sign_equals_explicit_sign():
+    c = phantom.make_case("headneck256", shape=(16, 48, 48))
+    kw = dict(levels=1, iters=[5], lam=c.lam, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as ctx:
+        a, _ = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                            [dev(m) for m in c.moving_masks], sign=None, **kw)
+        b, _ = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                            [dev(m) for m in c.moving_masks], sign=c.signs, **kw)
+        assert torch.equal(a, b)
+
+
+def test_register_init_dvf_skips_coarse_levels():
+    c = phantom.make_case("phantom64", shape=(12, 36, 40))
+    with cg.Context(0) as ctx:
+        dvf, st = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                               [dev(m) for m in c.moving_masks], levels=2, iters=[30, 4], lam=c.lam,
+                               sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED, init_dvf=dev(c.u_gt))
+        got = host(dvf)
+    assert st[0]["stop_reason"] == cg.CGDIR_REASON_SKIPPED and st[1]["iters_run"] == 4
+    ref, _ = oracle.register(c.static, c.moving, c.static_masks, c.moving_masks, levels=2, iters=[30, 4],
+                             lam=c.lam, sign=c.signs, init_dvf=c.u_gt)
+    assert dvf_rms(got, ref) <= 0.05
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    c = phantom.make_case("phantom64", shape=(6, 10, 12))
+    with pytest.raises(cg.CgdirError) as e:
+        ctx.register(dev(c.static), dev(c.moving[:, :, :-1].copy()), levels=1, iters=[1])
+    assert e.value.status == cg.CGDIR_EINVAL
+    with pytest.raises(cg.CgdirError) as e:
+        ctx.register(dev(c.static), dev(c.moving), levels=1, iters=[1], sigma_fluid=3.0)
+    assert e.value.status == cg.CGDIR_EINVAL
+    masks = [dev(c.static_masks[0])] * 9
+    with pytest.raises(cg.CgdirError) as e:
+        ctx.register(dev(c.static), dev(c.moving), masks, masks, levels=1, iters=[1])
+    assert e.value.status == cg.CGDIR_EINVAL
+    with pytest.raises(cg.CgdirError) as e:
+        ctx.register(dev(c.static), dev(c.moving), levels=9, iters=[1] * 9)
+    assert e.value.status == cg.CGDIR_EINVAL
