@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Throughput of contour-guided demons registration (CG-DIR) on GB300.
+
+One step = one whole registration (Algorithm A over the pyramid: restriction,
+UROI, every level's iterations, prolongation) of the head-and-neck-shaped
+synthetic case: 256 x 256 x 96 float32 CT, 5 structure masks, 3 levels with
+100 / 50 / 25 iterations, FIXED stopping.  Metric: voxel-iterations/s =
+sum over levels of (voxels x iterations) per step / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgdir|reference]
+
+N > 1 runs under torchrun as independent replicas (one case per rank, no
+collective on the data path; a barrier brackets the timed region).  The
+reference arm times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iters/s and p50/p99 latency per registration, batched vs plain FP32"
+UNIT = "voxel-iter/s"
+WORKLOAD = {"name": "headneck256", "levels": 3, "iters": [100, 50, 25]}
+# bounded sample of the same workload for the CPU oracle: same case, same
+# pyramid, iterations cut to 8 / 4 / 2 (about 16.5 M voxel-iterations)
+ORACLE_SAMPLE_ITERS = [8, 4, 2]
+FORCE_BYTES_PER_VOXEL = {True: 35, False: 33}   # contour terms on / off, FP32 images
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cgdir", choices=["cgdir", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", choices=["force", "smooth", "compose"], default=None,
+                    help="profiling aid: launch only the named kernel (via the C ABI primitive) "
+                         "on the workload's full-resolution inputs, W + K times, and print its "
+                         "CUDA-event time")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(case, n_gpus):
+    nz, ny, nx = case.shape
+    return {"workload": f"{WORKLOAD['name']}: {nx}x{ny}x{nz} float32 CT, {case.k} uint8 structure "
+                        f"masks, {WORKLOAD['levels']}-level pyramid "
+                        f"{'/'.join(map(str, WORKLOAD['iters']))} iterations, FIXED stop",
+            "shape_zyx": [nz, ny, nx], "masks": case.k, "levels": WORKLOAD["levels"],
+            "iters": WORKLOAD["iters"], "lambda": case.lam[0], "sigma": 1.0,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas x{n_gpus}"}
+
+
+def oracle_cores():
+    import oracle
+    return oracle.num_threads()
+
+
+def time_oracle_sample(case):
+    """One registration of the bounded sample by the FP64 CPU oracle."""
+    import oracle
+    import phantom
+    t0 = time.perf_counter()
+    oracle.register(case.static, case.moving, case.static_masks, case.moving_masks,
+                    levels=WORKLOAD["levels"], iters=ORACLE_SAMPLE_ITERS, lam=case.lam,
+                    sign=case.signs, stop_mode=oracle.STOP_FIXED)
+    dt = time.perf_counter() - t0
+    vi = phantom.voxel_iters(case.shape, WORKLOAD["levels"], ORACLE_SAMPLE_ITERS)
+    return vi, dt
+
+
+def sample_desc(case):
+    import phantom
+    vi = phantom.voxel_iters(case.shape, WORKLOAD["levels"], ORACLE_SAMPLE_ITERS)
+    return (f"same case and pyramid, iterations {'/'.join(map(str, ORACLE_SAMPLE_ITERS))} "
+            f"instead of {'/'.join(map(str, WORKLOAD['iters']))} ({vi / 1e6:.1f} M voxel-iters "
+            f"per run, set-up included)")
+
+
+# --------------------------------------------------------------------------- #
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons, power = [], 0.0, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+                power.append(float(f[3]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return str(dev)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def force_traffic_record(case):
+    """dram bytes per launch of the force kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "force_headneck256_traffic.json")
+    src = os.path.join(ROOT, "paper_1301_0970_gb300", "csrc", "kernels_force.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if rec.get("kernels_force_sha1") != h:
+        return None
+    return float(rec["dram_bytes_per_launch_full_size"])
+
+
+# --------------------------------------------------------------------------- #
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import phantom
+    case = phantom.make_case(WORKLOAD["name"])
+    times, vi = [], 0
+    for i in range(args.warmup + args.steps):
+        vi, dt = time_oracle_sample(case)
+        if i >= args.warmup:
+            times.append(dt)
+    value = vi * len(times) / sum(times)
+    cores = oracle_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(case, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample_desc(case)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cgdir(args):
+    import numpy as np
+    import torch
+
+    import paper_1301_0970_gb300 as cg
+    import phantom
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = phantom.make_case(WORKLOAD["name"], index=rank)
+    L, iters = WORKLOAD["levels"], WORKLOAD["iters"]
+    vox_iters = phantom.voxel_iters(case.shape, L, iters)
+    N = int(np.prod(case.shape))
+
+    S = torch.from_numpy(case.static).to(dev)
+    M = torch.from_numpy(case.moving).to(dev)
+    SM = [torch.from_numpy(m).to(dev) for m in case.static_masks]
+    MM = [torch.from_numpy(m).to(dev) for m in case.moving_masks]
+    dvf = torch.empty((3,) + case.shape, dtype=torch.float32, device=dev)
+    kw = dict(levels=L, iters=iters, lam=case.lam, sign=case.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    ctx = cg.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs, CUDA events on the ctx stream
+    ctx.profile([cg.CGDIR_K_FORCE])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = cg.launch_count()
+    with ClockSampler(gpu_uuid(torch, dev)) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = cg.launch_count() - launches0
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    prof = ctx.profile_read()
+    ctx.profile([])
+    tot = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+    max_total_ms = float(tot.item())
+    value = world * vox_iters * args.steps / (max_total_ms / 1e3)
+
+    # ---- one profiled step with every kernel class timed (breakdown only)
+    ctx.profile(list(range(7)))
+    flush.zero_()
+    ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
+    breakdown = ctx.profile_read()
+    ctx.profile([])
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Sh, Mh = torch.from_numpy(case.static).pin_memory(), torch.from_numpy(case.moving).pin_memory()
+        SMh = [torch.from_numpy(m).pin_memory() for m in case.static_masks]
+        MMh = [torch.from_numpy(m).pin_memory() for m in case.moving_masks]
+        dvf_h = torch.empty((3,) + case.shape, dtype=torch.float32).pin_memory()
+        ctx.register(Sh, Mh, SMh, MMh, dvf_out=dvf_h, **kw)      # warm the host path
+        barrier()
+        et = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = ctx.register(Sh, Mh, SMh, MMh, dvf_out=dvf_h, **kw)
+            et.append(time.perf_counter() - t0)
+        t = torch.tensor([sum(et)], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        h2d = 2 * N * 4 + 2 * case.k * N
+        d2h = 3 * N * 4 + L * (max(iters) + 1) * 8 + 4 * 8 * 4
+        e2e = {"value": world * vox_iters * args.steps / float(t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * float(t.item()) / args.steps}
+
+    # ---- roofline of the dominant kernel: force at the finest level
+    fine = [p for p in prof if p["kernel"] == "force" and p["level"] == L - 1]
+    roofline = None
+    if fine and fine[0]["launches"]:
+        avg_ms = fine[0]["total_ms"] / fine[0]["launches"]
+        bytes_per_launch = FORCE_BYTES_PER_VOXEL[True] * N
+        peak, peak_src = measured_peaks()
+        achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_force (finest level, contour terms on)",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": force_traffic_record(case),
+                    "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                    "launches": fine[0]["launches"], "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        vi, dt = time_oracle_sample(case)
+        cpu = {"value": vi / dt, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+               "sample": sample_desc(case), "seconds": dt}
+
+    if rank == 0:
+        lat = sorted(step_ms)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": workload_config(case, world),
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "per": "registration"},
+                "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": clk.summary(),
+                "kernel_breakdown_ms": {f"{p['kernel']}@L{p['level']}": round(p["total_ms"], 4)
+                                        for p in breakdown}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_only_kernel(args):
+    """One kernel alone on the full-resolution inputs (u = half the
+    ground-truth DVF, contour terms on for the force), for kernel profiling."""
+    import numpy as np
+    import torch
+
+    import paper_1301_0970_gb300 as cg
+    import phantom
+
+    dev = torch.device("cuda", 0)
+    case = phantom.make_case(WORKLOAD["name"])
+    bits = lambda m: torch.from_numpy(
+        np.bitwise_or.reduce([(x.astype(np.uint8) << j) for j, x in enumerate(m)], axis=0)).to(dev)
+    I0, T0 = torch.from_numpy(case.moving).to(dev), torch.from_numpy(case.static).to(dev)
+    mb, sb = bits(case.moving_masks), bits(case.static_masks)
+    u = torch.from_numpy(0.5 * case.u_gt).to(dev)
+    du = torch.empty_like(u)
+    dus = (0.1 * u).contiguous()
+    n = int(np.prod(case.shape))
+    if args.only == "force":
+        fn = lambda ctx: ctx.force(I0, T0, mb, sb, case.lam, case.signs, u, du=du)
+        nbytes = FORCE_BYTES_PER_VOXEL[True] * n
+    elif args.only == "smooth":
+        fn = lambda ctx: ctx.smooth(u, 1.0, out=du)
+        nbytes = 24 * n
+    else:
+        fn = lambda ctx: ctx.compose(u, dus, cg.CGDIR_COMPOSE, 0.0, out=du)
+        nbytes = 36 * n
+    with cg.Context(0) as ctx:
+        for _ in range(args.warmup):
+            fn(ctx)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            fn(ctx)
+        b.record()
+        torch.cuda.synchronize()
+        ctx.sync()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"kernel": args.only, "shape_zyx": list(case.shape), "avg_ms": ms,
+                      "algorithmic_GBps": nbytes / (ms / 1e3) / 1e9}))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.only:
+        return run_only_kernel(args)
+    return run_cgdir(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

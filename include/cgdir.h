@@ -92,7 +92,9 @@ typedef struct cgdir_ctx cgdir_ctx;          /* opaque; one device + one stream 
 typedef struct {
     int    device;              /* CUDA device ordinal                          */
     void  *stream;              /* cudaStream_t to order all work on; NULL = the
-                                   context creates (and later destroys) its own */
+                                   context creates (and later destroys) its own;
+                                   cudaStreamLegacy (0x1) = the legacy default
+                                   stream                                        */
     size_t mem_budget_bytes;    /* cap on device memory the context may hold;
                                    0 = no cap                                   */
 } cgdir_config;
@@ -173,6 +175,14 @@ const char *cgdir_last_error(const cgdir_ctx *ctx);
 
 /* Device bytes currently held by ctx (pyramid, fields, scratch). */
 size_t cgdir_mem_in_use(const cgdir_ctx *ctx);
+
+/* Wait for all work queued on ctx's stream.  Returns CGDIR_ETIMEDOUT if a
+   kernel's bounded wait for its own asynchronous (TMA) loads ran out since
+   the last check -- the kernel then wrote no output and returned -- and
+   CGDIR_ECUDA if the stream reports an error.  The blocking entry points
+   (cgdir_register, and cgdir_force / cgdir_iterate with stats) do this
+   check themselves. */
+int cgdir_sync(cgdir_ctx *ctx);
 
 /* ---- whole registration (Algorithm A) ----------------------------------- */
 
@@ -275,6 +285,38 @@ int cgdir_auto_sign(cgdir_ctx *ctx, const float *T0, const uint8_t *sbits, int k
 int cgdir_rms_id(cgdir_ctx *ctx, const float *I0, const float *T0, const float *u,
                  const uint8_t *uroi, int nx, int ny, int nz, double *rms_host,
                  long long *count_host);
+
+/* ---- instrumentation (not part of the paper's method) ------------------ */
+
+/* Number of CUDA kernels this library has launched in the process so far
+   (each kernel launch counts once; memcpy/memset do not count). */
+unsigned long long cgdir_launch_count(void);
+
+/* Kernel classes for per-kernel timing. */
+#define CGDIR_K_FORCE      0   /* warp + gradient + Eq. 7 (kernels 2, 3, 4)    */
+#define CGDIR_K_SMOOTH_DU  1   /* Gaussian of du (kernel 1, step 2)           */
+#define CGDIR_K_COMPOSE    2   /* composite update (kernel 4, step 3)        */
+#define CGDIR_K_SMOOTH_U   3   /* Gaussian of u (kernel 1, step 4)            */
+#define CGDIR_K_FINALIZE   4   /* RMS-ID reduction and stop test (kernel 5)  */
+#define CGDIR_K_METRIC     5   /* warp-only metric pass after a level's cap  */
+#define CGDIR_K_SETUP      6   /* pyramid, masks, UROI, signs, prolongation  */
+#define CGDIR_K_COUNT      7
+
+typedef struct {
+    int       kernel;     /* CGDIR_K_*                                       */
+    int       level;      /* pyramid level (0 = coarsest)                    */
+    long long launches;   /* launches timed                                  */
+    double    total_ms;   /* sum of their CUDA-event durations               */
+} cgdir_kernel_time;
+
+/* Time the kernels of the classes in kernel_mask (bit CGDIR_K_*) during later
+   cgdir_register calls on ctx, with a CUDA event pair on ctx's stream around
+   each launch; 0 switches timing off.  Clears earlier totals. */
+int cgdir_profile(cgdir_ctx *ctx, unsigned kernel_mask);
+
+/* Copy up to `cap` accumulated (kernel, level) totals into out; returns the
+   number of entries written (negative status on error). */
+int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap);
 
 #ifdef __cplusplus
 }

@@ -57,13 +57,25 @@ class cgdir_level_stats(ctypes.Structure):
                 ("rms_id", POINTER(c_double))]
 
 
+class cgdir_kernel_time(ctypes.Structure):
+    _fields_ = [("kernel", c_int), ("level", c_int), ("launches", c_longlong), ("total_ms", c_double)]
+
+
+CGDIR_K_FORCE, CGDIR_K_SMOOTH_DU, CGDIR_K_COMPOSE, CGDIR_K_SMOOTH_U, CGDIR_K_FINALIZE, \
+    CGDIR_K_METRIC, CGDIR_K_SETUP = range(7)
+KERNEL_NAMES = ["force", "smooth_du", "compose", "smooth_u", "finalize", "metric", "setup"]
+
 _SIGNATURES = {
+    "cgdir_launch_count": (ctypes.c_ulonglong, []),
+    "cgdir_profile": (c_int, [c_void_p, c_uint]),
+    "cgdir_profile_read": (c_int, [c_void_p, POINTER(cgdir_kernel_time), c_int]),
     "cgdir_default_params": (None, [POINTER(cgdir_params)]),
     "cgdir_create": (c_int, [POINTER(c_void_p), POINTER(cgdir_config)]),
     "cgdir_destroy": (None, [c_void_p]),
     "cgdir_strerror": (ctypes.c_char_p, [c_int]),
     "cgdir_last_error": (ctypes.c_char_p, [c_void_p]),
     "cgdir_mem_in_use": (c_size_t, [c_void_p]),
+    "cgdir_sync": (c_int, [c_void_p]),
     "cgdir_register": (c_int, [c_void_p, POINTER(cgdir_volume), POINTER(cgdir_volume),
                                POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
                                c_void_p, c_int, POINTER(cgdir_level_stats)]),
@@ -92,6 +104,11 @@ _SIGNATURES = {
 }
 
 _lib = None
+
+
+def launch_count() -> int:
+    """Kernels launched by the CUDA library in this process so far."""
+    return int(load().cgdir_launch_count())
 
 
 def library_path() -> str:
@@ -168,7 +185,10 @@ class Context:
         if stream is None:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
-        cfg = cgdir_config(device, c_void_p(int(stream.cuda_stream)), mem_budget_bytes)
+        # torch's default stream has handle 0; NULL asks the library for a
+        # stream of its own, so name the legacy default stream explicitly
+        handle = int(stream.cuda_stream) or 1      # cudaStreamLegacy
+        cfg = cgdir_config(device, c_void_p(handle), mem_budget_bytes)
         h = c_void_p()
         st = load().cgdir_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != CGDIR_OK:
@@ -202,8 +222,27 @@ class Context:
             raise CgdirError(st, f"{what}: {lib.cgdir_strerror(st).decode()}: "
                                  f"{lib.cgdir_last_error(self._h).decode()}")
 
+    def sync(self):
+        self._check(load().cgdir_sync(self._h), "cgdir_sync")
+
     def mem_in_use(self) -> int:
         return int(load().cgdir_mem_in_use(self._h))
+
+    def profile(self, kernels: Sequence[int] = ()):
+        """Time the given kernel classes (CGDIR_K_*) in later registrations."""
+        mask = 0
+        for k in kernels:
+            mask |= 1 << int(k)
+        self._check(load().cgdir_profile(self._h, mask), "cgdir_profile")
+
+    def profile_read(self):
+        buf = (cgdir_kernel_time * 256)()
+        n = load().cgdir_profile_read(self._h, buf, 256)
+        if n < 0:
+            raise CgdirError(-n, "cgdir_profile_read")
+        return [{"kernel": KERNEL_NAMES[buf[i].kernel], "level": buf[i].level,
+                 "launches": int(buf[i].launches), "total_ms": float(buf[i].total_ms)}
+                for i in range(n)]
 
     # ---- whole registration ------------------------------------------------
     def register(self, static, moving, static_masks=None, moving_masks=None, *,

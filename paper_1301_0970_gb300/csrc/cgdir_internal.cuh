@@ -80,8 +80,17 @@ struct LevelState {
     int hist_cap;
 };
 
+// Process-wide count of kernels launched by this library (instrumentation).
+void note_launch(unsigned n = 1);
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device (the runtime call is made once per kernel, device and size).
+cudaError_t ensure_smem(const void *func, size_t bytes);
+
 // ---- launchers (return the launch status; all async on `s`) ------------
-cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s);
+// err: device word for bounded-wait timeouts; nullptr selects the plain kernel.
+cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s,
+                         int *err = nullptr);
 size_t force_partial_count(int nx, int ny, int nz, int zchunk);
 int force_default_zchunk(int nx, int ny, int nz);
 cudaError_t launch_metric(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
@@ -91,8 +100,10 @@ size_t metric_partial_count(int nx, int ny, int nz);
 cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
                             int stop_mode, double eps, double *stats_out, cudaStream_t s);
 
+// err: device word set to 1 if a bounded wait inside the kernel ran out;
+// nullptr selects the plain-load kernel (no waits).
 cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int ny, int nz,
-                          float *out, const int *stop_flag, cudaStream_t s);
+                          float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr);
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
                            float *out, const int *stop_flag, cudaStream_t s);
 cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,

@@ -15,6 +15,16 @@
 // These are the quantities of Eq. 7 rearranged exactly; only P_i (k values)
 // is interpolated per point besides I0~.
 //
+// Two versions share the tiling below.  The TMA version (used whenever the
+// volume satisfies the tensor-map rules and fits 32-bit indexing) streams,
+// per plane, the DVF tile with its halo and the static-side tiles (T0, mask
+// bits, UROI) into a 4-stage shared-memory ring with cp.async.bulk.tensor,
+// interpolates with 32-bit corner offsets, and takes a fast path where all
+// 8 corners share the same mask bits (then P_i = bit_i (I0~ + offset) and,
+// where the whole 7-point stencil agrees, grad P_i = bit_i grad I0~), so
+// the per-structure work reduces to a few flops away from ROI borders.  The
+// plain version keeps the per-corner accumulation everywhere.
+//
 // Tiling: a CTA owns a 32 x 8 column of voxels in x-y and marches along z
 // over `zchunk` planes.  For each plane it interpolates I0~ and P_i at the
 // (32+2) x (8+2) points of the tile plus a one-voxel halo into a three-plane
@@ -22,6 +32,7 @@
 // from the ring.  Halo points outside the volume take the clamped index,
 // which reproduces the clamped central difference at the border.
 #include "cgdir_internal.cuh"
+#include "tma.cuh"
 
 namespace cgdir {
 
@@ -187,6 +198,240 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
                           (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
+
+// ---- TMA-fed version -------------------------------------------------------
+constexpr int kFStages = 4;
+constexpr int UBX = TX + 8;           // DVF box width: x0-4 .. x0+35
+constexpr int UBY = TY + 2;           // DVF box height: y0-1 .. y0+8
+constexpr int U_BYTES = 3 * UBY * UBX * 4;                 // 4800
+constexpr int T_OFF = (U_BYTES + 127) / 128 * 128;         // 4864
+constexpr int SB_OFF = T_OFF + TX * TY * 4;                // 5888
+constexpr int UR_OFF = SB_OFF + TX * TY;                   // 6144
+constexpr int STAGE_BYTES = (UR_OFF + TX * TY + 127) / 128 * 128;   // 6400
+constexpr int kRing = 4;              // warped planes kept (one barrier per plane)
+
+struct ForceMaps {
+    CUtensorMap u, t0, sb, ur;
+};
+
+__host__ __device__ constexpr size_t force2_smem_bytes(int nv) {
+    return 128 + (size_t)kFStages * STAGE_BYTES + (size_t)kRing * nv * HP * 4 + (size_t)kRing * HP * 2 + 8 +
+           kFStages * 8;
+}
+
+template <bool CONTOUR>
+__global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceMaps maps, ForceArgs a,
+                                                  int zchunk, int *err) {
+    if (a.stop_flag && *a.stop_flag) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char *stages = base;
+    const int nv = CONTOUR ? 1 + a.k : 1;
+    float *ring = reinterpret_cast<float *>(base + kFStages * STAGE_BYTES);      // [kRing][nv][HP]
+    uint16_t *state = reinterpret_cast<uint16_t *>(ring + kRing * nv * HP);      // [kRing][HP]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(state + kRing * HP) + 7) & ~uintptr_t(7));
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nxy = nx * ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
+    const int P = (ze - zb) + 2;                   // planes zb-1 .. ze
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    const int cidx = (ty + 1) * HX + (tx + 1);
+    const float off = a.offset;
+    const uint32_t tx_bytes = (uint32_t)(U_BYTES + TX * TY * 4 + (CONTOUR ? TX * TY : 0) +
+                                         (a.uroi ? TX * TY : 0));
+
+    auto issue = [&](int q) {
+        const int sidx = q % kFStages;
+        const int z = clampi(zb - 1 + q, 0, nz - 1);
+        unsigned char *st = stages + sidx * STAGE_BYTES;
+        mbar_expect_tx(&bar[sidx], tx_bytes);
+        tma_load_4d(st, &maps.u, x0 - 4, y0 - 1, z, 0, &bar[sidx]);
+        tma_load_3d(st + T_OFF, &maps.t0, x0, y0, z, &bar[sidx]);
+        if (CONTOUR) tma_load_3d(st + SB_OFF, &maps.sb, x0, y0, z, &bar[sidx]);
+        if (a.uroi) tma_load_3d(st + UR_OFF, &maps.ur, x0, y0, z, &bar[sidx]);
+    };
+    if (tid == 0) {
+        for (int q = 0; q < kFStages; ++q) mbar_init(&bar[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int issued = 0;
+    if (tid == 0)
+        for (; issued < kFStages && issued < P; ++issued) issue(issued);
+
+    double ssd = 0.0, cnt = 0.0;
+    float mx = 0.f;
+    int t = 0;
+    for (; t < P; ++t) {
+        const int sidx = t % kFStages;
+        const bool ok = mbar_wait_bounded(&bar[sidx], (uint32_t)((t / kFStages) & 1));
+        // ---- warp the halo points of plane zb-1+t into ring slot t % kRing
+        {
+            const float *U = reinterpret_cast<const float *>(stages + sidx * STAGE_BYTES);
+            float *W = ring + (t % kRing) * nv * HP;
+            uint16_t *Sg = state + (t % kRing) * HP;
+            const int gz = clampi(zb - 1 + t, 0, nz - 1);
+            for (int p = tid; p < HP; p += NT) {
+                const int hx = p % HX, hy = p / HX;
+                const int gx = clampi(x0 - 1 + hx, 0, nx - 1), gy = clampi(y0 - 1 + hy, 0, ny - 1);
+                const int lx = gx - (x0 - 4), ly = gy - (y0 - 1);
+                const float ux = U[(0 * UBY + ly) * UBX + lx];
+                const float uy = U[(1 * UBY + ly) * UBX + lx];
+                const float uz = U[(2 * UBY + ly) * UBX + lx];
+                const float px = fminf(fmaxf((float)gx + ux, 0.f), (float)(nx - 1));
+                const float py = fminf(fmaxf((float)gy + uy, 0.f), (float)(ny - 1));
+                const float pz = fminf(fmaxf((float)gz + uz, 0.f), (float)(nz - 1));
+                const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+                const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+                const float wx = px - fx, wy = py - fy, wz = pz - fz;
+                const int dx = ix < nx - 1 ? 1 : 0, dy = iy < ny - 1 ? nx : 0, dz = iz < nz - 1 ? nxy : 0;
+                const int b0 = (iz * ny + iy) * nx + ix;
+                const float c000 = __ldg(a.I0 + b0), c100 = __ldg(a.I0 + b0 + dx);
+                const float c010 = __ldg(a.I0 + b0 + dy), c110 = __ldg(a.I0 + b0 + dy + dx);
+                const float c001 = __ldg(a.I0 + b0 + dz), c101 = __ldg(a.I0 + b0 + dz + dx);
+                const float c011 = __ldg(a.I0 + b0 + dz + dy), c111 = __ldg(a.I0 + b0 + dz + dy + dx);
+                const float e00 = fmaf(wx, c100 - c000, c000), e10 = fmaf(wx, c110 - c010, c010);
+                const float e01 = fmaf(wx, c101 - c001, c001), e11 = fmaf(wx, c111 - c011, c011);
+                const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
+                const float acc = fmaf(wz, f1 - f0, f0);
+                W[p] = acc;
+                if (CONTOUR) {
+                    const unsigned m000 = __ldg(a.mbits + b0), m100 = __ldg(a.mbits + b0 + dx);
+                    const unsigned m010 = __ldg(a.mbits + b0 + dy), m110 = __ldg(a.mbits + b0 + dy + dx);
+                    const unsigned m001 = __ldg(a.mbits + b0 + dz), m101 = __ldg(a.mbits + b0 + dz + dx);
+                    const unsigned m011 = __ldg(a.mbits + b0 + dz + dy);
+                    const unsigned m111 = __ldg(a.mbits + b0 + dz + dy + dx);
+                    const unsigned andb = m000 & m100 & m010 & m110 & m001 & m101 & m011 & m111;
+                    const unsigned orb = m000 | m100 | m010 | m110 | m001 | m101 | m011 | m111;
+                    Sg[p] = (uint16_t)((andb << 8) | orb);
+                    if (andb == orb) {
+                        const float J = acc + off;
+#pragma unroll
+                        for (int j = 0; j < kMaxMasks; ++j)
+                            if (j < a.k) W[(1 + j) * HP + p] = ((andb >> j) & 1u) ? J : 0.f;
+                    } else {
+                        const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
+                        const float q000 = ax * ay * az * (c000 + off), q100 = wx * ay * az * (c100 + off);
+                        const float q010 = ax * wy * az * (c010 + off), q110 = wx * wy * az * (c110 + off);
+                        const float q001 = ax * ay * wz * (c001 + off), q101 = wx * ay * wz * (c101 + off);
+                        const float q011 = ax * wy * wz * (c011 + off), q111 = wx * wy * wz * (c111 + off);
+#pragma unroll
+                        for (int j = 0; j < kMaxMasks; ++j) {
+                            if (j < a.k) {
+                                float pj = 0.f;
+                                pj += ((m000 >> j) & 1u) ? q000 : 0.f;
+                                pj += ((m100 >> j) & 1u) ? q100 : 0.f;
+                                pj += ((m010 >> j) & 1u) ? q010 : 0.f;
+                                pj += ((m110 >> j) & 1u) ? q110 : 0.f;
+                                pj += ((m001 >> j) & 1u) ? q001 : 0.f;
+                                pj += ((m101 >> j) & 1u) ? q101 : 0.f;
+                                pj += ((m011 >> j) & 1u) ? q011 : 0.f;
+                                pj += ((m111 >> j) & 1u) ? q111 : 0.f;
+                                W[(1 + j) * HP + p] = pj;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) break;
+        if (tid == 0 && t >= 2 && issued < P) {
+            fence_proxy_async();
+            issue(issued);
+            ++issued;
+        }
+        // ---- force for plane z = zb + t - 2 from warped slots t-2, t-1, t
+        if (t >= 2 && act) {
+            const int z = zb + t - 2;
+            const unsigned char *st = stages + ((t - 1) % kFStages) * STAGE_BYTES;
+            const float *Pm = ring + ((t - 2) % kRing) * nv * HP;
+            const float *Pc = ring + ((t - 1) % kRing) * nv * HP;
+            const float *Pp = ring + (t % kRing) * nv * HP;
+            const size_t N = (size_t)nx * ny * nz;
+            const size_t i = ((size_t)z * ny + y) * nx + x;
+            const float w0 = Pc[cidx];
+            const float gxv = 0.5f * (Pc[cidx + 1] - Pc[cidx - 1]);
+            const float gyv = 0.5f * (Pc[cidx + HX] - Pc[cidx - HX]);
+            const float gzv = 0.5f * (Pp[cidx] - Pm[cidx]);
+            const float T = reinterpret_cast<const float *>(st + T_OFF)[ty * TX + tx];
+            const float r0 = T - w0;
+            if (a.warped) a.warped[i] = w0;
+            const float g2 = gxv * gxv + gyv * gyv + gzv * gzv;
+            float dux = 0.f, duy = 0.f, duz = 0.f;
+            if (g2 != 0.f) {
+                const float gn = sqrtf(g2);
+                const float inv = 1.f / gn;
+                const float nxv = gxv * inv, nyv = gyv * inv, nzv = gzv * inv;
+                float num = gn * r0, den = gn * gn;
+                if (CONTOUR) {
+                    const unsigned sb = st[SB_OFF + ty * TX + tx];
+                    const float Toff = T + off;
+                    const uint16_t *Sm = state + ((t - 2) % kRing) * HP;
+                    const uint16_t *Sc = state + ((t - 1) % kRing) * HP;
+                    const uint16_t *Sp = state + (t % kRing) * HP;
+                    const unsigned s0 = Sc[cidx], s1 = Sc[cidx - 1], s2 = Sc[cidx + 1], s3 = Sc[cidx - HX],
+                                   s4 = Sc[cidx + HX], s5 = Sm[cidx], s6 = Sp[cidx];
+                    const unsigned A = (s0 & s1 & s2 & s3 & s4 & s5 & s6) >> 8;      // inside at every corner
+                    const unsigned O = (s0 | s1 | s2 | s3 | s4 | s5 | s6) & 0xffu;   // inside at some corner
+#pragma unroll
+                    for (int j = 0; j < kMaxMasks; ++j) {
+                        if (j < a.k) {
+                            const float hs = a.half_sign[j];
+                            const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
+                            float aj, rj;
+                            if (!((O >> j) & 1u)) {
+                                aj = gn;
+                                rj = r0 + hs * inside;
+                            } else if ((A >> j) & 1u) {
+                                aj = gn + hs * gn;
+                                rj = r0 + hs * (inside - (w0 + off));
+                            } else {
+                                const float *Pjm = Pm + (1 + j) * HP, *Pjc = Pc + (1 + j) * HP,
+                                            *Pjp = Pp + (1 + j) * HP;
+                                const float dPx = 0.5f * (Pjc[cidx + 1] - Pjc[cidx - 1]);
+                                const float dPy = 0.5f * (Pjc[cidx + HX] - Pjc[cidx - HX]);
+                                const float dPz = 0.5f * (Pjp[cidx] - Pjm[cidx]);
+                                aj = gn + hs * (dPx * nxv + dPy * nyv + dPz * nzv);
+                                rj = r0 + hs * (inside - Pjc[cidx]);
+                            }
+                            num = fmaf(a.lambda[j] * aj, rj, num);
+                            den = fmaf(a.lambda[j] * aj, aj, den);
+                        }
+                    }
+                }
+                const float v = num / (den + r0 * r0);
+                dux = v * nxv; duy = v * nyv; duz = v * nzv;
+            }
+            a.du[i] = dux;
+            a.du[N + i] = duy;
+            a.du[2 * N + i] = duz;
+            if (a.uroi == nullptr || st[UR_OFF + ty * TX + tx]) {
+                ssd += (double)(r0 * r0);
+                cnt += 1.0;
+            }
+            mx = fmaxf(mx, sqrtf(dux * dux + duy * duy + duz * duz));
+        }
+    }
+    if (t < P) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int q = t; q < issued; ++q)
+                mbar_wait_bounded(&bar[q % kFStages], (uint32_t)((q / kFStages) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    if (a.partial)
+        block_partial<NT>(ssd, cnt, mx, a.partial,
+                          (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
 // Metric-only pass: I0~ at every voxel and the UROI partial sums (the warp
 // of Algorithm A step 5 after a level's last update).
 constexpr int MT = 256;
@@ -304,19 +549,45 @@ size_t force_partial_count(int nx, int ny, int nz, int zchunk) {
     return (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zchunk - 1) / zchunk);
 }
 
-cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s) {
+cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s, int *err) {
     if (zchunk <= 0) zchunk = force_default_zchunk(a.nx, a.ny, a.nz);
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
     dim3 block(TX, TY);
     const bool contour = a.contour && a.k > 0;
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    const size_t N = (size_t)a.nx * a.ny * a.nz;
+    if (err != nullptr && N < (size_t)1 << 31) {
+        ForceMaps m;
+        const uint64_t du4[4] = {(uint64_t)a.nx, (uint64_t)a.ny, (uint64_t)a.nz, 3};
+        const uint64_t d3[3] = {(uint64_t)a.nx, (uint64_t)a.ny, (uint64_t)a.nz};
+        const uint32_t ubox[4] = {UBX, UBY, 1, 3}, tbox[3] = {TX, TY, 1};
+        bool ok = encode_tensor_map(&m.u, a.u, 4, du4, ubox, 4) &&
+                  encode_tensor_map(&m.t0, a.T0, 3, d3, tbox, 4);
+        if (ok && contour) ok = encode_tensor_map(&m.sb, a.sbits, 3, d3, tbox, 1);
+        if (ok && a.uroi) ok = encode_tensor_map(&m.ur, a.uroi, 3, d3, tbox, 1);
+        if (ok) {
+            const size_t smem = force2_smem_bytes(contour ? 1 + a.k : 1);
+            cudaError_t e;
+            if (contour) {
+                e = ensure_smem((const void *)k_force_tma<true>, smem);
+                if (e == cudaSuccess) k_force_tma<true><<<grid, block, smem, s>>>(m, a, zchunk, err);
+            } else {
+                e = ensure_smem((const void *)k_force_tma<false>, smem);
+                if (e == cudaSuccess) k_force_tma<false><<<grid, block, smem, s>>>(m, a, zchunk, err);
+            }
+            note_launch();
+            return e != cudaSuccess ? e : cudaGetLastError();
+        }
+    }
     const size_t smem = 3u * (1 + (contour ? a.k : 0)) * HP * sizeof(float);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     if (contour) {
-        cudaFuncSetAttribute(k_force<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem((const void *)k_force<true>, smem);
         k_force<true><<<grid, block, smem, s>>>(a, zchunk);
     } else {
         k_force<false><<<grid, block, smem, s>>>(a, zchunk);
     }
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -335,12 +606,14 @@ cudaError_t launch_metric(const float *I0, const float *T0, const float *u, cons
     const int g = metric_grid(nx, ny, nz);
     if (nblocks_out) *nblocks_out = g;
     k_metric<<<g, MT, 0, s>>>(I0, T0, u, uroi, nx, ny, nz, partial, stop_flag);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
                             int stop_mode, double eps, double *stats_out, cudaStream_t s) {
     k_finalize<<<1, FT, 0, s>>>(partial, nblocks, st, n, cap, stop_mode, eps, stats_out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -350,6 +623,7 @@ cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, 
     size_t g = (N + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
     k_warp<<<(unsigned)g, 256, 0, s>>>(f, u, nx, ny, nz, out);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -229,27 +229,27 @@ cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint
                               cudaStream_t s) {
     MaskPtrs m{};
     for (int j = 0; j < k && j < kMaxMasks; ++j) m.p[j] = masks[j];
-    k_pack<<<flat_grid(n), 256, 0, s>>>(m, k, n, bits);
+    k_pack<<<flat_grid(n), 256, 0, s>>>(m, k, n, bits); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_restrict_image(const float *in, int nx, int ny, int nz, float *out,
                                   cudaStream_t s) {
     const size_t Nc = (size_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
-    k_restrict_image<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out);
+    k_restrict_image<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint8_t *out,
                                  cudaStream_t s) {
     const size_t Nc = (size_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
-    k_restrict_bits<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out);
+    k_restrict_bits<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(const float *uc, int cx, int cy, int cz, int nx, int ny, int nz,
                            float *uf, cudaStream_t s) {
-    k_prolong<<<flat_grid((size_t)nx * ny * nz), 256, 0, s>>>(uc, cx, cy, cz, nx, ny, nz, uf);
+    k_prolong<<<flat_grid((size_t)nx * ny * nz), 256, 0, s>>>(uc, cx, cy, cz, nx, ny, nz, uf); note_launch();
     return cudaGetLastError();
 }
 
@@ -257,7 +257,7 @@ cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, con
                         double margin, uint8_t *rowdist, uint8_t *out, cudaStream_t s) {
     const size_t N = (size_t)nx * ny * nz;
     if (k <= 0) {
-        k_fill_u8<<<flat_grid(N), 256, 0, s>>>(out, N, 1);
+        k_fill_u8<<<flat_grid(N), 256, 0, s>>>(out, N, 1); note_launch();
         return cudaGetLastError();
     }
     if (!(margin >= 0.0) || !(spacing[0] > 0) || !(spacing[1] > 0) || !(spacing[2] > 0))
@@ -279,8 +279,8 @@ cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, con
             t.ext[dz + t.rz][dy + t.ry] = (int8_t)e;
         }
     const unsigned mask = (k >= 8) ? 0xffu : ((1u << k) - 1u);
-    k_uroi_rows<<<flat_grid(N), 256, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist);
-    k_uroi_dilate<<<flat_grid(N), 256, 0, s>>>(rowdist, t, nx, ny, nz, out);
+    k_uroi_rows<<<flat_grid(N), 256, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist); note_launch();
+    k_uroi_dilate<<<flat_grid(N), 256, 0, s>>>(rowdist, t, nx, ny, nz, out); note_launch();
     return cudaGetLastError();
 }
 
@@ -293,10 +293,11 @@ cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int n
     k_dilate_axis<<<g, 256, 0, s>>>(sbits, 0, nx, ny, nz, tmp_a);
     k_dilate_axis<<<g, 256, 0, s>>>(tmp_a, 1, nx, ny, nz, tmp_b);
     k_dilate_axis<<<g, 256, 0, s>>>(tmp_b, 2, nx, ny, nz, tmp_a);
+    note_launch(3);
     const unsigned gp = flat_grid(N, 152 * 4);
     for (int j = 0; j < k; ++j) {
-        k_sign_partial<<<gp, ST, 0, s>>>(T0, sbits, tmp_a, j, N, partial);
-        k_sum_rows4<<<1, 32, 0, s>>>(partial, (int)gp, sums + 4 * j);
+        k_sign_partial<<<gp, ST, 0, s>>>(T0, sbits, tmp_a, j, N, partial); note_launch();
+        k_sum_rows4<<<1, 32, 0, s>>>(partial, (int)gp, sums + 4 * j); note_launch();
     }
     return cudaGetLastError();
 }
@@ -304,12 +305,14 @@ cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int n
 size_t sign_partial_rows(size_t n) { return flat_grid(n, 152 * 4); }
 
 cudaError_t launch_convert_image(const void *in, int dtype, size_t n, float *out, cudaStream_t s) {
-    if (dtype == CGDIR_F16)
+    if (dtype == CGDIR_F16) {
         k_convert<__half><<<flat_grid(n), 256, 0, s>>>((const __half *)in, n, out);
-    else if (dtype == CGDIR_BF16)
+    } else if (dtype == CGDIR_BF16) {
         k_convert<__nv_bfloat16><<<flat_grid(n), 256, 0, s>>>((const __nv_bfloat16 *)in, n, out);
-    else
+    } else {
         return cudaMemcpyAsync(out, in, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    }
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -12,10 +12,13 @@
 #include "cgdir_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -26,9 +29,41 @@ struct WsBuf {
     size_t cap = 0;
 };
 
+struct ProfPending {
+    int cls, level;
+    cudaEvent_t a, b;
+};
+
+// Event pairs recorded around profiled launches, with the events they use.
+struct ProfList {
+    std::vector<ProfPending> recs;
+    std::vector<cudaEvent_t> pool;
+    void release() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+        pool.clear();
+        recs.clear();
+    }
+};
+
+// One instantiated CUDA graph of the device part of a registration.
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    ProfList prof;
+    unsigned long long launches = 0;
+};
+
 struct cgdir_ctx {
+    unsigned prof_mask = 0;
+    ProfList eager;
+    std::map<std::pair<int, int>, std::pair<long long, double>> prof;
+    bool use_graphs = true;
+    unsigned long long ws_generation = 0;
+    std::map<std::string, GraphEntry> graphs;
     int device = 0;
+    bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
+    int *err_word = nullptr;      // device word set by a kernel whose bounded wait ran out
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
     bool own_stream = false;
     size_t budget = 0;
     size_t in_use = 0;
@@ -38,7 +73,73 @@ struct cgdir_ctx {
     std::vector<int> h_meta;
 };
 
+namespace cgdir {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t ensure_smem(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &have = done[{func, dev}];
+    if (have >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+}  // namespace cgdir
+
 namespace {
+
+// Event pair around one launch of class `cls` when that class is profiled.
+struct ProfScope {
+    ProfList *list = nullptr;
+    cudaStream_t stream;
+    int idx = -1;
+    ProfScope(ProfList *l, unsigned mask, cudaStream_t s, int cls, int level) : stream(s) {
+        if (!(mask & (1u << cls))) return;
+        const size_t need = 2 * (l->recs.size() + 1);
+        while (l->pool.size() < need) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+            l->pool.push_back(e);
+        }
+        ProfPending p{cls, level, l->pool[need - 2], l->pool[need - 1]};
+        // External: inside a stream capture this becomes an event-record node
+        cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal);
+        l->recs.push_back(p);
+        list = l;
+        idx = (int)l->recs.size() - 1;
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecordWithFlags(list->recs[idx].b, stream, cudaEventRecordExternal);
+    }
+};
+
+// After the stream has drained: fold the recorded pairs into the totals.
+void prof_collect(cgdir_ctx *ctx, const ProfList &l) {
+    for (const ProfPending &p : l.recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto &t = ctx->prof[{p.cls, p.level}];
+            t.first += 1;
+            t.second += ms;
+        } else {
+            cudaGetLastError();
+        }
+    }
+}
+
+void drop_graphs(cgdir_ctx *ctx) {
+    for (auto &kv : ctx->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        kv.second.prof.release();
+    }
+    ctx->graphs.clear();
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -84,10 +185,12 @@ int ws_get(cgdir_ctx *ctx, const char *name, size_t bytes, void **out) {
         return fail(ctx, CGDIR_ENOMEM, std::string("device budget exceeded growing '") + name + "'");
     if (b.p) {
         cudaStreamSynchronize(ctx->stream);
+        drop_graphs(ctx);              // cached graphs hold the old address
         cudaFree(b.p);
         ctx->in_use -= b.cap;
         b = WsBuf{};
     }
+    ++ctx->ws_generation;
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, cap);
     if (e != cudaSuccess) {
@@ -102,6 +205,22 @@ int ws_get(cgdir_ctx *ctx, const char *name, size_t bytes, void **out) {
 }
 
 bool dims_ok(int nx, int ny, int nz) { return nx >= 1 && ny >= 1 && nz >= 1; }
+
+// Error word handed to kernels with bounded waits; nullptr selects the
+// plain-load kernels.
+int *kerr(cgdir_ctx *ctx) { return ctx->plain_kernels ? nullptr : ctx->err_word; }
+
+// After the stream has drained: a kernel wait that ran out is a timeout.
+int check_err_word(cgdir_ctx *ctx) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, ctx->err_word, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(ctx, CGDIR_ECUDA, std::string("error word: ") + cudaGetErrorString(e));
+    if (h) {
+        cudaMemset(ctx->err_word, 0, sizeof(int));
+        return fail(ctx, CGDIR_ETIMEDOUT, "a bounded wait inside a kernel ran out (TMA load not completed)");
+    }
+    return CGDIR_OK;
+}
 
 bool sigma_ok(float s) { return std::isfinite(s) && s >= 0.f && s <= CGDIR_MAX_SIGMA; }
 
@@ -171,6 +290,36 @@ const char *cgdir_last_error(const cgdir_ctx *ctx) { return ctx ? ctx->err.c_str
 
 size_t cgdir_mem_in_use(const cgdir_ctx *ctx) { return ctx ? ctx->in_use : 0; }
 
+unsigned long long cgdir_launch_count(void) { return g_launches.load(); }
+
+int cgdir_sync(cgdir_ctx *ctx) {
+    if (!ctx) return CGDIR_EINVAL;
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_err_word(ctx);
+}
+
+int cgdir_profile(cgdir_ctx *ctx, unsigned kernel_mask) {
+    if (!ctx) return CGDIR_EINVAL;
+    ctx->prof_mask = kernel_mask & ((1u << CGDIR_K_COUNT) - 1u);
+    ctx->prof.clear();
+    return CGDIR_OK;
+}
+
+int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap) {
+    if (!ctx || (cap > 0 && !out)) return -CGDIR_EINVAL;
+    int n = 0;
+    for (const auto &kv : ctx->prof) {
+        if (n >= cap) break;
+        out[n].kernel = kv.first.first;
+        out[n].level = kv.first.second;
+        out[n].launches = kv.second.first;
+        out[n].total_ms = kv.second.second;
+        ++n;
+    }
+    return n;
+}
+
 int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     if (!out || !cfg) return CGDIR_EINVAL;
     *out = nullptr;
@@ -191,6 +340,22 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
         }
         c->own_stream = true;
     }
+    const char *kern = std::getenv("CGDIR_KERNELS");
+    c->plain_kernels = kern && std::strcmp(kern, "plain") == 0;
+    const char *gr = std::getenv("CGDIR_GRAPHS");
+    c->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c->use_graphs = false;
+        c->cap_stream = nullptr;
+    }
+    if (cudaMalloc(&c->err_word, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return CGDIR_ECUDA;
+    }
     *out = c;
     return CGDIR_OK;
 }
@@ -201,6 +366,10 @@ void cgdir_destroy(cgdir_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->ws)
         if (kv.second.p) cudaFree(kv.second.p);
+    drop_graphs(ctx);
+    ctx->eager.release();
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->err_word) cudaFree(ctx->err_word);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -235,12 +404,13 @@ static int force_impl(cgdir_ctx *ctx, const ForceArgs &a, double *stats_host) {
         b.partial = (double *)part;
     }
     int nb = 0;
-    CK(launch_force(b, zc, &nb, ctx->stream));
+    CK(launch_force(b, zc, &nb, ctx->stream, kerr(ctx)));
     if (stats_host) {
         LevelState ls{};
         CK(launch_finalize((double *)part, nb, ls, 0, 0, CGDIR_STOP_FIXED, 0.0, (double *)st, ctx->stream));
         CK(cudaMemcpyAsync(stats_host, st, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
+        TRY(check_err_word(ctx));
     }
     return CGDIR_OK;
 }
@@ -269,7 +439,7 @@ int cgdir_smooth(cgdir_ctx *ctx, const float *in, int ncomp, float sigma, int nx
     if (!in || !out || in == out || ncomp < 1 || ncomp > 3 || !dims_ok(nx, ny, nz) || !sigma_ok(sigma))
         return fail(ctx, CGDIR_EINVAL, "smooth: bad arguments");
     DeviceGuard g(ctx->device);
-    CK(launch_smooth(in, ncomp, sigma, nx, ny, nz, out, nullptr, ctx->stream));
+    CK(launch_smooth(in, ncomp, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx)));
     return CGDIR_OK;
 }
 
@@ -288,7 +458,7 @@ int cgdir_compose(cgdir_ctx *ctx, const float *u, const float *du, int mode, flo
     void *tmp = nullptr;
     TRY(ws_get(ctx, "field_tmp", 3 * N * sizeof(float), &tmp));
     CK(launch_compose(u, du, mode, nx, ny, nz, (float *)tmp, nullptr, ctx->stream));
-    CK(launch_smooth((float *)tmp, 3, sigma, nx, ny, nz, out, nullptr, ctx->stream));
+    CK(launch_smooth((float *)tmp, 3, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx)));
     return CGDIR_OK;
 }
 
@@ -316,9 +486,9 @@ int cgdir_iterate(cgdir_ctx *ctx, const float *I0, const float *T0, const uint8_
     a.warped = nullptr; a.stop_flag = nullptr;
     a.nx = nx; a.ny = ny; a.nz = nz;
     TRY(force_impl(ctx, a, stats_host));
-    CK(launch_smooth(du, 3, sigma_fluid, nx, ny, nz, dus, nullptr, ctx->stream));
+    CK(launch_smooth(du, 3, sigma_fluid, nx, ny, nz, dus, nullptr, ctx->stream, kerr(ctx)));
     CK(launch_compose(u_in, dus, compose_mode, nx, ny, nz, du, nullptr, ctx->stream));
-    CK(launch_smooth(du, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream));
+    CK(launch_smooth(du, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx)));
     return CGDIR_OK;
 }
 
@@ -563,21 +733,7 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     };
     TRY(pack(SM, SB[L - 1]));
     TRY(pack(MM, MB[L - 1]));
-    // ---- pyramid
-    for (int l = L - 2; l >= 0; --l) {
-        const int *d = dims[l + 1];
-        CK(launch_restrict_image(T[l + 1], d[0], d[1], d[2], T[l], s));
-        CK(launch_restrict_image(I[l + 1], d[0], d[1], d[2], I[l], s));
-        CK(launch_restrict_bits(SB[l + 1], d[0], d[1], d[2], SB[l], s));
-        CK(launch_restrict_bits(MB[l + 1], d[0], d[1], d[2], MB[l], s));
-    }
-    for (int l = 0; l < L; ++l) {
-        const double f = (double)(1 << (L - 1 - l));
-        const double sp[3] = {P->spacing_mm[0] * f, P->spacing_mm[1] * f, P->spacing_mm[2] * f};
-        CK(launch_uroi(SB[l], k, dims[l][0], dims[l][1], dims[l][2], sp, P->margin_mm,
-                       (uint8_t *)p_rowdist, UR[l], s));
-    }
-    // ---- signs
+    // ---- signs (decided on the host before the device part is enqueued)
     int8_t sign[kMaxMasks];
     bool need_auto = false;
     for (int j = 0; j < k; ++j) {
@@ -594,53 +750,132 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     }
     for (int j = 0; j < k; ++j) base.half_sign[j] = 0.5f * (float)sign[j];
 
-    // ---- levels
-    CK(cudaMemsetAsync(p_state, 0, state_bytes, s));
     const int first = P->init_dvf ? L - 1 : 0;
-    float *ucur = ua, *uoth = ub;
-    for (int l = first; l < L; ++l) {
-        const int lx = dims[l][0], ly = dims[l][1], lz = dims[l][2];
-        const size_t N = Nl[l];
-        if (l == first) {
-            if (P->init_dvf) {
-                CK(cudaMemcpyAsync(ucur, P->init_dvf, 3 * N * sizeof(float),
-                                   P->init_dvf_where == CGDIR_HOST ? cudaMemcpyHostToDevice
-                                                                   : cudaMemcpyDeviceToDevice, s));
+    if (P->init_dvf)
+        CK(cudaMemcpyAsync(ua, P->init_dvf, 3 * Nf * sizeof(float),
+                           P->init_dvf_where == CGDIR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    float *ufinal = ((L - 1 - first) % 2 == 0) ? ua : ub;
+
+    // ---- the device part: pyramid, UROI, every level.  Its launches depend
+    // only on the context's workspace, so it is captured once per shape and
+    // parameter set into a CUDA graph and replayed.
+    auto enqueue = [&](ProfList *pl, cudaStream_t s) -> int {
+        for (int l = L - 2; l >= 0; --l) {
+            const int *d = dims[l + 1];
+            ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
+            CK(launch_restrict_image(T[l + 1], d[0], d[1], d[2], T[l], s));
+            CK(launch_restrict_image(I[l + 1], d[0], d[1], d[2], I[l], s));
+            CK(launch_restrict_bits(SB[l + 1], d[0], d[1], d[2], SB[l], s));
+            CK(launch_restrict_bits(MB[l + 1], d[0], d[1], d[2], MB[l], s));
+        }
+        for (int l = 0; l < L; ++l) {
+            const double f = (double)(1 << (L - 1 - l));
+            const double sp[3] = {P->spacing_mm[0] * f, P->spacing_mm[1] * f, P->spacing_mm[2] * f};
+            ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
+            CK(launch_uroi(SB[l], k, dims[l][0], dims[l][1], dims[l][2], sp, P->margin_mm,
+                           (uint8_t *)p_rowdist, UR[l], s));
+        }
+        CK(cudaMemsetAsync(p_state, 0, state_bytes, s));
+        float *ucur = ua, *uoth = ub;
+        for (int l = first; l < L; ++l) {
+            const int lx = dims[l][0], ly = dims[l][1], lz = dims[l][2];
+            const size_t N = Nl[l];
+            if (l == first) {
+                if (!P->init_dvf) CK(cudaMemsetAsync(ucur, 0, 3 * N * sizeof(float), s));
             } else {
-                CK(cudaMemsetAsync(ucur, 0, 3 * N * sizeof(float), s));
+                ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
+                CK(launch_prolong(ucur, dims[l - 1][0], dims[l - 1][1], dims[l - 1][2], lx, ly, lz, uoth, s));
+                std::swap(ucur, uoth);
             }
-        } else {
-            CK(launch_prolong(ucur, dims[l - 1][0], dims[l - 1][1], dims[l - 1][2], lx, ly, lz, uoth, s));
-            std::swap(ucur, uoth);
-        }
-        LevelState st{};
-        st.hist = hist + (size_t)l * hcap;
-        st.hist_len = hist_len + l;
-        st.iters_run = iters_run + l;
-        st.stop_reason = reason + l;
-        st.stop_flag = flags + l;
-        st.hist_cap = hcap;
-        ForceArgs a = base;
-        a.I0 = I[l]; a.T0 = T[l]; a.mbits = MB[l]; a.sbits = SB[l]; a.uroi = UR[l];
-        a.u = ucur; a.du = du; a.warped = nullptr; a.partial = partial; a.stop_flag = flags + l;
-        a.nx = lx; a.ny = ly; a.nz = lz;
-        a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
-        const int zc = force_default_zchunk(lx, ly, lz);
-        const int cap = P->iters[l];
-        for (int n = 0; n < cap; ++n) {
+            LevelState st{};
+            st.hist = hist + (size_t)l * hcap;
+            st.hist_len = hist_len + l;
+            st.iters_run = iters_run + l;
+            st.stop_reason = reason + l;
+            st.stop_flag = flags + l;
+            st.hist_cap = hcap;
+            ForceArgs a = base;
+            a.I0 = I[l]; a.T0 = T[l]; a.mbits = MB[l]; a.sbits = SB[l]; a.uroi = UR[l];
+            a.u = ucur; a.du = du; a.warped = nullptr; a.partial = partial; a.stop_flag = flags + l;
+            a.nx = lx; a.ny = ly; a.nz = lz;
+            a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
+            const int zc = force_default_zchunk(lx, ly, lz);
+            const int cap = P->iters[l];
+            const unsigned m = ctx->prof_mask;
+            for (int n = 0; n < cap; ++n) {
+                int nb = 0;
+                { ProfScope ps(pl, m, s, CGDIR_K_FORCE, l); CK(launch_force(a, zc, &nb, s, kerr(ctx))); }
+                { ProfScope ps(pl, m, s, CGDIR_K_FINALIZE, l);
+                  CK(launch_finalize(partial, nb, st, n, cap, P->stop_mode, P->eps, nullptr, s)); }
+                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_DU, l);
+                  CK(launch_smooth(du, 3, P->sigma_fluid, lx, ly, lz, du2, flags + l, s, kerr(ctx))); }
+                { ProfScope ps(pl, m, s, CGDIR_K_COMPOSE, l);
+                  CK(launch_compose(ucur, du2, P->compose_mode, lx, ly, lz, du, flags + l, s)); }
+                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_U, l);
+                  CK(launch_smooth(du, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx))); }
+            }
             int nb = 0;
-            CK(launch_force(a, zc, &nb, s));
-            CK(launch_finalize(partial, nb, st, n, cap, P->stop_mode, P->eps, nullptr, s));
-            CK(launch_smooth(du, 3, P->sigma_fluid, lx, ly, lz, du2, flags + l, s));
-            CK(launch_compose(ucur, du2, P->compose_mode, lx, ly, lz, du, flags + l, s));
-            CK(launch_smooth(du, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s));
+            { ProfScope ps(pl, m, s, CGDIR_K_METRIC, l);
+              CK(launch_metric(I[l], T[l], ucur, UR[l], lx, ly, lz, partial, flags + l, &nb, s)); }
+            { ProfScope ps(pl, m, s, CGDIR_K_FINALIZE, l);
+              CK(launch_finalize(partial, nb, st, cap, cap, P->stop_mode, P->eps, nullptr, s)); }
         }
-        int nb = 0;
-        CK(launch_metric(I[l], T[l], ucur, UR[l], lx, ly, lz, partial, flags + l, &nb, s));
-        CK(launch_finalize(partial, nb, st, cap, cap, P->stop_mode, P->eps, nullptr, s));
+        return CGDIR_OK;
+    };
+
+    const ProfList *used = nullptr;
+    if (ctx->use_graphs) {
+        char key[1024];
+        int len = std::snprintf(key, sizeof key, "%d %d %d|%d|%d %d %.9g %.9g %d %u %d %.17g %.17g %.17g %.17g "
+                                "%.17g %.9g %d %d %llu %u|", nx, ny, nz, L, k, first, P->sigma_fluid, P->sigma_diff,
+                                P->compose_mode, P->contour_level_mask, P->stop_mode, P->eps, P->spacing_mm[0],
+                                P->spacing_mm[1], P->spacing_mm[2], P->margin_mm, P->intensity_offset,
+                                (int)ctx->plain_kernels, maxcap, ctx->ws_generation, ctx->prof_mask);
+        std::string skey(key, (size_t)len);
+        for (int l = 0; l < L; ++l) skey += std::to_string(P->iters[l]) + ",";
+        for (int j = 0; j < k; ++j) {
+            char b[48];
+            std::snprintf(b, sizeof b, "%.9g:%d,", base.lambda[j], (int)sign[j]);
+            skey += b;
+        }
+        auto it = ctx->graphs.find(skey);
+        if (it == ctx->graphs.end()) {
+            GraphEntry ge;
+            const unsigned long long before = g_launches.load();
+            CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            const int rc = enqueue(&ge.prof, ctx->cap_stream);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            ge.launches = g_launches.load() - before;
+            g_launches.fetch_sub(ge.launches);        // captured, not yet launched
+            if (rc != CGDIR_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                ge.prof.release();
+                return rc;
+            }
+            if (ec != cudaSuccess) {
+                ge.prof.release();
+                return fail(ctx, CGDIR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&ge.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                ge.prof.release();
+                return fail(ctx, CGDIR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+            }
+            it = ctx->graphs.emplace(skey, std::move(ge)).first;
+        }
+        CK(cudaGraphLaunch(it->second.exec, s));
+        note_launch((unsigned)it->second.launches);
+        used = &it->second.prof;
+    } else {
+        ctx->eager.recs.clear();
+        TRY(enqueue(&ctx->eager, s));
+        used = &ctx->eager;
     }
+
     // ---- outputs
-    CK(cudaMemcpyAsync(dvf_out, ucur, 3 * Nf * sizeof(float),
+    CK(cudaMemcpyAsync(dvf_out, ufinal, 3 * Nf * sizeof(float),
                        dvf_where == CGDIR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     ctx->h_hist.assign((size_t)L * hcap, 0.0);
     ctx->h_meta.assign(4 * CGDIR_MAX_LEVELS, 0);
@@ -648,6 +883,8 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     CK(cudaMemcpyAsync(ctx->h_meta.data(), meta, 4 * CGDIR_MAX_LEVELS * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
+    prof_collect(ctx, *used);
+    TRY(check_err_word(ctx));
     if (stats_out) {
         for (int l = 0; l < L; ++l) {
             cgdir_level_stats &o = stats_out[l];

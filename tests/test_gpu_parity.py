@@ -29,13 +29,31 @@ import paper_1301_0970_gb300 as cg  # noqa: E402
 
 DEV = torch.device("cuda:0")
 RNG = np.random.default_rng(2024)
-SHAPES = [(9, 21, 45), (1, 1, 1), (3, 8, 32), (17, 33, 70), (5, 1, 7)]
+# nx % 4 == 0 shapes take the TMA kernels, the others the plain-load kernels
+SHAPES = [(9, 21, 45), (1, 1, 1), (3, 8, 32), (17, 33, 70), (5, 1, 7), (9, 21, 44), (17, 33, 68),
+          (6, 17, 36)]
 
 
-@pytest.fixture(scope="module")
-def ctx():
-    with cg.Context(0) as c:
-        yield c
+def make_context(kernels: str):
+    """A context whose kernels are the TMA ones where eligible ("tma") or the
+    plain-load ones everywhere ("plain")."""
+    import os
+    old = os.environ.get("CGDIR_KERNELS")
+    os.environ["CGDIR_KERNELS"] = kernels
+    try:
+        return cg.Context(0)
+    finally:
+        if old is None:
+            del os.environ["CGDIR_KERNELS"]
+        else:
+            os.environ["CGDIR_KERNELS"] = old
+
+
+@pytest.fixture(scope="module", params=["tma", "plain"])
+def ctx(request):
+    c = make_context(request.param)
+    yield c
+    c.close()
 
 
 def dev(a, dtype=None):
@@ -134,7 +152,8 @@ def test_auto_sign_matches_oracle(ctx):
 
 
 @pytest.mark.parametrize("sigma", [1.0, 0.6, 2.0, 0.0])
-@pytest.mark.parametrize("shape", [(9, 21, 45), (17, 33, 70), (1, 1, 1), (2, 3, 1)])
+@pytest.mark.parametrize("shape", [(9, 21, 45), (17, 33, 70), (1, 1, 1), (2, 3, 1), (9, 21, 44),
+                                   (17, 33, 72), (30, 8, 4), (3, 5, 8)])
 def test_smooth(ctx, sigma, shape):
     u = rand_field(shape)
     got = host(ctx.smooth(dev(u), sigma))
@@ -162,8 +181,9 @@ def case_inputs(shape=(12, 36, 40), masks=None, name="phantom64"):
 
 @pytest.mark.parametrize("k", [0, 1, 2, 5, 8])
 @pytest.mark.parametrize("contour", [True, False])
-def test_force(ctx, k, contour):
-    c = case_inputs(shape=(11, 37, 45), name="headneck256")
+@pytest.mark.parametrize("shape", [(11, 37, 45), (11, 37, 48), (5, 9, 16), (13, 20, 64)])
+def test_force(ctx, k, contour, shape):
+    c = case_inputs(shape=shape, name="headneck256")
     sm = np.concatenate([c.static_masks] * 2)[:k]
     mm = np.concatenate([c.moving_masks] * 2)[:k]
     lam = list(RNG.uniform(1e-3, 1.0, size=k))
@@ -183,6 +203,24 @@ def test_force(ctx, k, contour):
     assert abs(stats[2] - float(np.sqrt((ref ** 2).sum(0)).max())) <= 1e-4
 
 
+def test_force_uniform_mask_fast_path_matches_general_path():
+    """The TMA kernel's shortcut where all corners share their mask bits must
+    agree with the plain kernel's per-corner accumulation."""
+    c = phantom.make_case("headneck256", shape=(16, 64, 64))
+    u = (0.5 * c.u_gt).astype(np.float32)
+    args = (dev(c.moving), dev(c.static), dev(pack(c.moving_masks)), dev(pack(c.static_masks)),
+            [0.5] * c.k, c.signs, dev(u))
+    a = make_context("tma")
+    b = make_context("plain")
+    try:
+        da = host(a.force(*args))
+        db = host(b.force(*args))
+    finally:
+        a.close()
+        b.close()
+    close_normwise(da, db, rel=2e-6)
+
+
 def test_force_identical_images_is_exactly_zero(ctx):
     c = case_inputs()
     du = ctx.force(dev(c.static), dev(c.static), dev(pack(c.static_masks)), dev(pack(c.static_masks)),
@@ -192,7 +230,7 @@ def test_force_identical_images_is_exactly_zero(ctx):
 
 
 @pytest.mark.parametrize("name,shape", [("phantom64", (12, 36, 40)), ("headneck256", (13, 45, 50)),
-                                        ("pelvis512", (10, 48, 40))])
+                                        ("pelvis512", (10, 48, 40)), ("headneck256", (24, 64, 64))])
 def test_single_iteration_meets_1e5(ctx, name, shape):
     """One iteration (Algorithm A steps 1-4) from a nonzero DVF: relative
     norm-wise difference <= 1e-5."""
@@ -344,3 +382,66 @@ def test_invalid_arguments_are_rejected(ctx):
     with pytest.raises(cg.CgdirError) as e:
         ctx.register(dev(c.static), dev(c.moving), levels=9, iters=[1] * 9)
     assert e.value.status == cg.CGDIR_EINVAL
+
+
+def _register_with_env(c, env, repeat=1, **kw):
+    import os
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        ctx = cg.Context(0)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    outs = []
+    try:
+        for _ in range(repeat):
+            dvf, st = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                                   [dev(m) for m in c.moving_masks], **kw)
+            outs.append((dvf.cpu(), st))
+    finally:
+        ctx.close()
+    return outs
+
+
+def test_graph_replay_equals_eager_launches_bitwise():
+    """The captured CUDA graph runs the same kernels in the same order as the
+    eager launch sequence: identical results, also on a second replay."""
+    c = phantom.make_case("headneck256", shape=(24, 64, 64))
+    kw = dict(levels=2, iters=[6, 4], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_WINDOW10, eps=1e-3)
+    g = _register_with_env(c, {"CGDIR_GRAPHS": "1"}, repeat=2, **kw)
+    e = _register_with_env(c, {"CGDIR_GRAPHS": "0"}, repeat=1, **kw)
+    assert torch.equal(g[0][0], g[1][0]) and torch.equal(g[0][0], e[0][0])
+    assert g[0][1] == g[1][1] == e[0][1]
+
+
+def test_one_context_serves_changing_shapes():
+    """Workspace growth drops cached graphs; each call must still match a
+    fresh context."""
+    shapes = [(12, 32, 32), (20, 48, 64), (12, 32, 32), (8, 16, 16)]
+    with cg.Context(0) as ctx:
+        for shp in shapes:
+            c = phantom.make_case("phantom64", shape=shp)
+            kw = dict(levels=2, iters=[4, 3], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+            a, _ = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                                [dev(m) for m in c.moving_masks], **kw)
+            b = _register_with_env(c, {}, **kw)[0][0]
+            assert torch.equal(a.cpu(), b)
+
+
+def test_profile_reports_every_kernel_class():
+    c = phantom.make_case("phantom64", shape=(12, 32, 32))
+    with cg.Context(0) as ctx:
+        ctx.profile(list(range(7)))
+        ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                     [dev(m) for m in c.moving_masks], levels=2, iters=[3, 2], lam=c.lam, sign=c.signs,
+                     stop_mode=cg.CGDIR_STOP_FIXED)
+        prof = ctx.profile_read()
+    kinds = {p["kernel"] for p in prof}
+    assert {"force", "smooth_du", "compose", "smooth_u", "finalize", "metric", "setup"} <= kinds
+    force = {p["level"]: p["launches"] for p in prof if p["kernel"] == "force"}
+    assert force == {0: 3, 1: 2}
+    assert all(p["total_ms"] > 0 for p in prof)
