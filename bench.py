@@ -49,6 +49,8 @@ def parse():
                     help="profiling aid: launch only the named kernel (via the C ABI primitive) "
                          "on the workload's full-resolution inputs, W + K times, and print its "
                          "CUDA-event time")
+    ap.add_argument("--shape", default=None,
+                    help="with --only: nz,ny,nx of the inputs (the workload's case resampled)")
     return ap.parse_args()
 
 
@@ -354,7 +356,8 @@ def run_only_kernel(args):
     import phantom
 
     dev = torch.device("cuda", 0)
-    case = phantom.make_case(WORKLOAD["name"])
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+    case = phantom.make_case(WORKLOAD["name"], shape=shape)
     bits = lambda m: torch.from_numpy(
         np.bitwise_or.reduce([(x.astype(np.uint8) << j) for j, x in enumerate(m)], axis=0)).to(dev)
     I0, T0 = torch.from_numpy(case.moving).to(dev), torch.from_numpy(case.static).to(dev)

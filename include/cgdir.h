@@ -294,8 +294,9 @@ unsigned long long cgdir_launch_count(void);
 
 /* Kernel classes for per-kernel timing. */
 #define CGDIR_K_FORCE      0   /* warp + gradient + Eq. 7 (kernels 2, 3, 4)    */
-#define CGDIR_K_SMOOTH_DU  1   /* Gaussian of du (kernel 1, step 2)           */
-#define CGDIR_K_COMPOSE    2   /* composite update (kernel 4, step 3)        */
+#define CGDIR_K_SMOOTH_DU  1   /* Gaussian of du and, fused into it, the
+                                  composite update (kernels 1 + 4, steps 2-3) */
+#define CGDIR_K_COMPOSE    2   /* composite update when it runs on its own    */
 #define CGDIR_K_SMOOTH_U   3   /* Gaussian of u (kernel 1, step 4)            */
 #define CGDIR_K_FINALIZE   4   /* RMS-ID reduction and stop test (kernel 5)  */
 #define CGDIR_K_METRIC     5   /* warp-only metric pass after a level's cap  */

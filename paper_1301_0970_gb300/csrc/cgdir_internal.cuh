@@ -56,21 +56,7 @@ Taps gauss_taps(float sigma);
 // UROI, UROI count, max |du|}, FP64, written by the force / metric kernels.
 constexpr int kPartialStride = 4;
 
-struct ForceArgs {
-    const float *I0, *T0;
-    const uint8_t *mbits, *sbits, *uroi;
-    const float *u;
-    float *du, *warped;
-    double *partial;          // [gridDim.x*gridDim.y*gridDim.z][kPartialStride] or null
-    const int *stop_flag;     // kernels return at once when *stop_flag != 0 (may be null)
-    int nx, ny, nz;
-    int k, contour;
-    float offset;
-    float lambda[kMaxMasks];
-    float half_sign[kMaxMasks];   // s_i / 2
-};
-
-// Device-side state of one level's stopping logic, updated by finalize.
+// Device-side state of one level's stopping logic, updated by the reduction.
 struct LevelState {
     double *hist;       // [hist_cap]
     int *hist_len;
@@ -80,12 +66,47 @@ struct LevelState {
     int hist_cap;
 };
 
+// The reduction and stop test of one iteration, run by the last CTA of the
+// kernel that wrote the per-CTA partials (the CTA that brings `done` to the
+// grid size); it sums the partials in a fixed order, so the result does not
+// depend on which CTA finishes last.
+struct FinishArgs {
+    unsigned *done;      // completion counter, 0 before the launch (reset by the last CTA);
+                         // null = no fused reduction
+    LevelState st;
+    int n, cap, stop_mode;
+    double eps;
+    double *stats_out;   // optional {sum, count, max}
+};
+
+struct ForceArgs {
+    const float *I0, *T0;
+    const uint8_t *mbits, *sbits, *uroi;
+    const float2 *mtex;       // moving texels {I0, mask bits as uint32}; used by the TMA
+                              // kernel when the contour terms are on (null otherwise)
+    const float *u;
+    float *du, *warped;
+    double *partial;          // [gridDim.x*gridDim.y*gridDim.z][kPartialStride] or null
+    const int *stop_flag;     // kernels return at once when *stop_flag != 0 (may be null)
+    int nx, ny, nz;
+    int k, contour;
+    float offset;
+    float lambda[kMaxMasks];
+    float half_sign[kMaxMasks];   // s_i / 2
+    FinishArgs fin;               // fused reduction (fin.done null = none)
+};
+
 // Process-wide count of kernels launched by this library (instrumentation).
 void note_launch(unsigned n = 1);
 
 // Raise a kernel's dynamic shared-memory limit to `bytes` on the current
 // device (the runtime call is made once per kernel, device and size).
 cudaError_t ensure_smem(const void *func, size_t bytes);
+
+// z-chunk length for a z-marching kernel with `xy_ctas` CTAs per chunk so the
+// grid covers about `waves` x (resident CTAs per SM x SM count).
+int pick_zchunk(int nz, long xy_ctas, int resident_per_sm, int waves);
+int sm_count();
 
 // ---- launchers (return the launch status; all async on `s`) ------------
 // err: device word for bounded-wait timeouts; nullptr selects the plain kernel.
@@ -95,7 +116,7 @@ size_t force_partial_count(int nx, int ny, int nz, int zchunk);
 int force_default_zchunk(int nx, int ny, int nz);
 cudaError_t launch_metric(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
                           int nx, int ny, int nz, double *partial, const int *stop_flag,
-                          int *nblocks_out, cudaStream_t s);
+                          int *nblocks_out, cudaStream_t s, const FinishArgs *fin = nullptr);
 size_t metric_partial_count(int nx, int ny, int nz);
 cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
                             int stop_mode, double eps, double *stats_out, cudaStream_t s);
@@ -106,6 +127,11 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
                           float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr);
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
                            float *out, const int *stop_flag, cudaStream_t s);
+// Algorithm A steps 2 + 3 in one pass: out = G(du) + u(x + G(du)) (or u + G(du));
+// tmp (3N floats) is used only when the fused TMA kernel is not eligible.
+cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
+                                  int nz, float *out, float *tmp, const int *stop_flag, cudaStream_t s,
+                                  int *err);
 cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,
                         cudaStream_t s);
 
@@ -118,11 +144,14 @@ cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint
 cudaError_t launch_prolong(const float *uc, int cx, int cy, int cz, int nx, int ny, int nz,
                            float *uf, cudaStream_t s);
 cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, const double *spacing,
-                        double margin, uint8_t *scratch_rowdist, uint8_t *out, cudaStream_t s);
+                        double margin, uint8_t *scratch, uint8_t *out, cudaStream_t s);
+size_t uroi_scratch_bytes(size_t n);
 cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int nx, int ny, int nz,
                              uint8_t *tmp_a, uint8_t *tmp_b, double *partial,
                              double *sums /* [k][4] */, cudaStream_t s);
 size_t sign_partial_rows(size_t n);
 cudaError_t launch_convert_image(const void *in, int dtype, size_t n, float *out, cudaStream_t s);
+// Interleave the moving image with its mask bits: tex[v] = {I0[v], bits[v]}.
+cudaError_t launch_make_texels(const float *I0, const uint8_t *bits, size_t n, float2 *tex, cudaStream_t s);
 
 }  // namespace cgdir

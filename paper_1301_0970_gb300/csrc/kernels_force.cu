@@ -52,9 +52,13 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Fixed-order block reduction of (ssd, count, max) into partial[bid].
+// Fixed-order block reduction of (ssd, count, max) into partial[bid].  Each
+// thread's sum covers only its own column of a z-chunk (a few dozen
+// non-negative terms), so it is kept in FP32 and widened here; everything
+// from the warp level up is FP64.
 template <int NTHREADS>
-__device__ void block_partial(double ssd, double cnt, float mx, double *partial, int bid) {
+__device__ void block_partial(float ssd_f, int cnt_i, float mx, double *partial, int bid) {
+    double ssd = (double)ssd_f, cnt = (double)cnt_i;
     __shared__ double rs[NTHREADS / 32], rc[NTHREADS / 32];
     __shared__ float rm[NTHREADS / 32];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -71,6 +75,77 @@ __device__ void block_partial(double ssd, double cnt, float mx, double *partial,
         partial[(size_t)bid * kPartialStride + 1] = c;
         partial[(size_t)bid * kPartialStride + 2] = (double)m;
         partial[(size_t)bid * kPartialStride + 3] = 0.0;
+    }
+}
+
+// Stopping test of Sec. 2.2 on delta^0..delta^n (same readings as the C ABI).
+__device__ int stop_test(const double *d, int n, int mode, double eps) {
+    if (mode == CGDIR_STOP_WINDOW10) return (n >= 10) && (d[n - 10] - d[n] <= eps);
+    if (mode == CGDIR_STOP_PAPER_LITERAL) {
+        if (n < 11) return 0;
+        const double ln = d[n] - d[n - 1], lm = d[n - 10] - d[n - 11];
+        return (lm - ln) <= eps;
+    }
+    return 0;
+}
+
+// Fixed-order sum of the per-CTA partials, RMS-ID into the level history and
+// the stop decision (kernel 5).  Run by one CTA of blockDim >= 1 (any shape).
+__device__ void finalize_block(const double *__restrict__ partial, int nblocks, const FinishArgs &f) {
+    constexpr int FT = 256;
+    __shared__ double ss[FT], sc[FT], sx[FT];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    if (tid < FT) {
+        double s = 0.0, c = 0.0, m = 0.0;
+        for (int b = tid; b < nblocks; b += FT) {
+            s += __ldcg(partial + (size_t)b * kPartialStride + 0);
+            c += __ldcg(partial + (size_t)b * kPartialStride + 1);
+            m = fmax(m, __ldcg(partial + (size_t)b * kPartialStride + 2));
+        }
+        ss[tid] = s; sc[tid] = c; sx[tid] = m;
+    }
+    (void)nt;
+    __syncthreads();
+    for (int h = FT / 2; h > 0; h >>= 1) {
+        if (tid < h) {
+            ss[tid] += ss[tid + h];
+            sc[tid] += sc[tid + h];
+            sx[tid] = fmax(sx[tid], sx[tid + h]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double S = ss[0], C = sc[0];
+        if (f.stats_out) { f.stats_out[0] = S; f.stats_out[1] = C; f.stats_out[2] = sx[0]; }
+        const LevelState &st = f.st;
+        if (st.hist) {
+            const double d = C > 0 ? sqrt(S / C) : 0.0;
+            if (f.n < st.hist_cap) st.hist[f.n] = d;
+            *st.hist_len = f.n + 1;
+            if (stop_test(st.hist, f.n, f.stop_mode, f.eps)) {
+                *st.stop_flag = 1; *st.iters_run = f.n; *st.stop_reason = CGDIR_REASON_CONVERGED;
+            } else if (f.n >= f.cap) {
+                *st.stop_flag = 1; *st.iters_run = f.n; *st.stop_reason = CGDIR_REASON_CAP;
+            }
+        }
+    }
+}
+
+// Called by every CTA after its partial is written: the CTA that completes
+// the grid runs finalize_block and resets the counter for the next launch.
+__device__ void finish_if_last(const double *partial, int nblocks, const FinishArgs &f) {
+    __shared__ int last;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(f.done, 1u) == (unsigned)(nblocks - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        finalize_block(partial, nblocks, f);
+        if (tid == 0) *f.done = 0u;
     }
 }
 
@@ -135,7 +210,8 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
 
     force_plane<CONTOUR>(a, zb - 1, sm, x0, y0, tid);
     force_plane<CONTOUR>(a, zb, sm + plane, x0, y0, tid);
-    double ssd = 0.0, cnt = 0.0;
+    float ssd = 0.f;
+    int cnt = 0;
     float mx = 0.f;
     for (int z = zb; z < ze; ++z) {
         const int r = z - zb;
@@ -186,21 +262,23 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
             a.du[N + i] = duy;
             a.du[2 * N + i] = duz;
             if (a.uroi == nullptr || __ldg(a.uroi + i)) {
-                ssd += (double)(r0 * r0);
-                cnt += 1.0;
+                ssd = fmaf(r0, r0, ssd);
+                cnt += 1;
             }
             mx = fmaxf(mx, sqrtf(dux * dux + duy * duy + duz * duz));
         }
         __syncthreads();
     }
-    if (a.partial)
+    if (a.partial) {
         block_partial<NT>(ssd, cnt, mx, a.partial,
                           (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+        if (a.fin.done) finish_if_last(a.partial, gridDim.x * gridDim.y * gridDim.z, a.fin);
+    }
 }
 
 
 // ---- TMA-fed version -------------------------------------------------------
-constexpr int kFStages = 4;
+constexpr int kFStages = 3;
 constexpr int UBX = TX + 8;           // DVF box width: x0-4 .. x0+35
 constexpr int UBY = TY + 2;           // DVF box height: y0-1 .. y0+8
 constexpr int U_BYTES = 3 * UBY * UBX * 4;                 // 4800
@@ -265,7 +343,8 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
     if (tid == 0)
         for (; issued < kFStages && issued < P; ++issued) issue(issued);
 
-    double ssd = 0.0, cnt = 0.0;
+    float ssd = 0.f;
+    int cnt = 0;
     float mx = 0.f;
     int t = 0;
     for (; t < P; ++t) {
@@ -292,21 +371,31 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
                 const float wx = px - fx, wy = py - fy, wz = pz - fz;
                 const int dx = ix < nx - 1 ? 1 : 0, dy = iy < ny - 1 ? nx : 0, dz = iz < nz - 1 ? nxy : 0;
                 const int b0 = (iz * ny + iy) * nx + ix;
-                const float c000 = __ldg(a.I0 + b0), c100 = __ldg(a.I0 + b0 + dx);
-                const float c010 = __ldg(a.I0 + b0 + dy), c110 = __ldg(a.I0 + b0 + dy + dx);
-                const float c001 = __ldg(a.I0 + b0 + dz), c101 = __ldg(a.I0 + b0 + dz + dx);
-                const float c011 = __ldg(a.I0 + b0 + dz + dy), c111 = __ldg(a.I0 + b0 + dz + dy + dx);
+                float c000, c100, c010, c110, c001, c101, c011, c111;
+                unsigned m000 = 0, m100 = 0, m010 = 0, m110 = 0, m001 = 0, m101 = 0, m011 = 0, m111 = 0;
+                if (CONTOUR) {
+                    const float2 *q0 = a.mtex + b0;
+                    const float2 t000 = __ldg(q0), t100 = __ldg(q0 + dx), t010 = __ldg(q0 + dy),
+                                 t110 = __ldg(q0 + dy + dx), t001 = __ldg(q0 + dz), t101 = __ldg(q0 + dz + dx),
+                                 t011 = __ldg(q0 + dz + dy), t111 = __ldg(q0 + dz + dy + dx);
+                    c000 = t000.x; c100 = t100.x; c010 = t010.x; c110 = t110.x;
+                    c001 = t001.x; c101 = t101.x; c011 = t011.x; c111 = t111.x;
+                    m000 = __float_as_uint(t000.y); m100 = __float_as_uint(t100.y);
+                    m010 = __float_as_uint(t010.y); m110 = __float_as_uint(t110.y);
+                    m001 = __float_as_uint(t001.y); m101 = __float_as_uint(t101.y);
+                    m011 = __float_as_uint(t011.y); m111 = __float_as_uint(t111.y);
+                } else {
+                    const float *q0 = a.I0 + b0;
+                    c000 = __ldg(q0); c100 = __ldg(q0 + dx); c010 = __ldg(q0 + dy); c110 = __ldg(q0 + dy + dx);
+                    c001 = __ldg(q0 + dz); c101 = __ldg(q0 + dz + dx); c011 = __ldg(q0 + dz + dy);
+                    c111 = __ldg(q0 + dz + dy + dx);
+                }
                 const float e00 = fmaf(wx, c100 - c000, c000), e10 = fmaf(wx, c110 - c010, c010);
                 const float e01 = fmaf(wx, c101 - c001, c001), e11 = fmaf(wx, c111 - c011, c011);
                 const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
                 const float acc = fmaf(wz, f1 - f0, f0);
                 W[p] = acc;
                 if (CONTOUR) {
-                    const unsigned m000 = __ldg(a.mbits + b0), m100 = __ldg(a.mbits + b0 + dx);
-                    const unsigned m010 = __ldg(a.mbits + b0 + dy), m110 = __ldg(a.mbits + b0 + dy + dx);
-                    const unsigned m001 = __ldg(a.mbits + b0 + dz), m101 = __ldg(a.mbits + b0 + dz + dx);
-                    const unsigned m011 = __ldg(a.mbits + b0 + dz + dy);
-                    const unsigned m111 = __ldg(a.mbits + b0 + dz + dy + dx);
                     const unsigned andb = m000 & m100 & m010 & m110 & m001 & m101 & m011 & m111;
                     const unsigned orb = m000 | m100 | m010 | m110 | m001 | m101 | m011 | m111;
                     Sg[p] = (uint16_t)((andb << 8) | orb);
@@ -365,8 +454,10 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
             const float g2 = gxv * gxv + gyv * gyv + gzv * gzv;
             float dux = 0.f, duy = 0.f, duz = 0.f;
             if (g2 != 0.f) {
-                const float gn = sqrtf(g2);
-                const float inv = 1.f / gn;
+                // approximate reciprocal root (well inside the 1e-5 parity bar);
+                // exact path for subnormal g2, which the approximation flushes
+                const float inv = g2 > 1e-30f ? rsqrtf(g2) : 1.f / sqrtf(g2);
+                const float gn = g2 * inv;
                 const float nxv = gxv * inv, nyv = gyv * inv, nzv = gzv * inv;
                 float num = gn * r0, den = gn * gn;
                 if (CONTOUR) {
@@ -405,17 +496,17 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
                         }
                     }
                 }
-                const float v = num / (den + r0 * r0);
+                const float v = __fdividef(num, den + r0 * r0);
                 dux = v * nxv; duy = v * nyv; duz = v * nzv;
             }
             a.du[i] = dux;
             a.du[N + i] = duy;
             a.du[2 * N + i] = duz;
             if (a.uroi == nullptr || st[UR_OFF + ty * TX + tx]) {
-                ssd += (double)(r0 * r0);
-                cnt += 1.0;
+                ssd = fmaf(r0, r0, ssd);
+                cnt += 1;
             }
-            mx = fmaxf(mx, sqrtf(dux * dux + duy * duy + duz * duz));
+            mx = fmaxf(mx, dux * dux + duy * duy + duz * duz);      // squared; root taken per block
         }
     }
     if (t < P) {
@@ -427,9 +518,11 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
         __syncthreads();
         return;
     }
-    if (a.partial)
-        block_partial<NT>(ssd, cnt, mx, a.partial,
+    if (a.partial) {
+        block_partial<NT>(ssd, cnt, sqrtf(mx), a.partial,
                           (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+        if (a.fin.done) finish_if_last(a.partial, gridDim.x * gridDim.y * gridDim.z, a.fin);
+    }
 }
 
 // Metric-only pass: I0~ at every voxel and the UROI partial sums (the warp
@@ -439,10 +532,12 @@ __global__ void __launch_bounds__(MT) k_metric(const float *__restrict__ I0,
                                                const float *__restrict__ T0,
                                                const float *__restrict__ u,
                                                const uint8_t *__restrict__ uroi, int nx, int ny,
-                                               int nz, double *partial, const int *stop_flag) {
+                                               int nz, double *partial, const int *stop_flag,
+                                               FinishArgs fin) {
     if (stop_flag && *stop_flag) return;
     const size_t N = (size_t)nx * ny * nz;
-    double ssd = 0.0, cnt = 0.0;
+    float ssd = 0.f;
+    int cnt = 0;
     for (size_t i = (size_t)blockIdx.x * MT + threadIdx.x; i < N; i += (size_t)gridDim.x * MT) {
         if (uroi && !uroi[i]) continue;
         const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
@@ -457,10 +552,11 @@ __global__ void __launch_bounds__(MT) k_metric(const float *__restrict__ I0,
             acc = fmaf(w, __ldg(I0 + vox(cx, cy, cz, nx, ny)), acc);
         }
         const float r = __ldg(T0 + i) - acc;
-        ssd += (double)(r * r);
-        cnt += 1.0;
+        ssd = fmaf(r, r, ssd);
+        cnt += 1;
     }
     block_partial<MT>(ssd, cnt, 0.f, partial, blockIdx.x);
+    if (fin.done) finish_if_last(partial, gridDim.x, fin);
 }
 
 // Plain warp of one image (interpolation kernel 4).
@@ -484,65 +580,20 @@ __global__ void k_warp(const float *__restrict__ f, const float *__restrict__ u,
     }
 }
 
-// Stopping test of Sec. 2.2 on delta^0..delta^n (same readings as the C ABI).
-__device__ int stop_test(const double *d, int n, int mode, double eps) {
-    if (mode == CGDIR_STOP_WINDOW10) return (n >= 10) && (d[n - 10] - d[n] <= eps);
-    if (mode == CGDIR_STOP_PAPER_LITERAL) {
-        if (n < 11) return 0;
-        const double ln = d[n] - d[n - 1], lm = d[n - 10] - d[n - 11];
-        return (lm - ln) <= eps;
-    }
-    return 0;
-}
-
 constexpr int FT = 256;
 __global__ void __launch_bounds__(FT) k_finalize(const double *__restrict__ partial, int nblocks,
-                                                 LevelState st, int n, int cap, int mode,
-                                                 double eps, double *stats_out) {
-    if (st.stop_flag && *st.stop_flag) return;
-    __shared__ double ss[FT], sc[FT], sx[FT];
-    double s = 0.0, c = 0.0, m = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += FT) {
-        s += partial[(size_t)b * kPartialStride + 0];
-        c += partial[(size_t)b * kPartialStride + 1];
-        m = fmax(m, partial[(size_t)b * kPartialStride + 2]);
-    }
-    ss[threadIdx.x] = s; sc[threadIdx.x] = c; sx[threadIdx.x] = m;
-    __syncthreads();
-    for (int h = FT / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            ss[threadIdx.x] += ss[threadIdx.x + h];
-            sc[threadIdx.x] += sc[threadIdx.x + h];
-            sx[threadIdx.x] = fmax(sx[threadIdx.x], sx[threadIdx.x + h]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double S = ss[0], C = sc[0];
-        if (stats_out) { stats_out[0] = S; stats_out[1] = C; stats_out[2] = sx[0]; }
-        if (st.hist) {
-            const double d = C > 0 ? sqrt(S / C) : 0.0;
-            if (n < st.hist_cap) st.hist[n] = d;
-            *st.hist_len = n + 1;
-            if (stop_test(st.hist, n, mode, eps)) {
-                *st.stop_flag = 1; *st.iters_run = n; *st.stop_reason = CGDIR_REASON_CONVERGED;
-            } else if (n >= cap) {
-                *st.stop_flag = 1; *st.iters_run = n; *st.stop_reason = CGDIR_REASON_CAP;
-            }
-        }
-    }
+                                                 FinishArgs f) {
+    if (f.st.stop_flag && *f.st.stop_flag) return;
+    finalize_block(partial, nblocks, f);
 }
 
 }  // namespace
 
+// z chunk of the force kernels: enough CTAs for about two waves of 4
+// resident CTAs per SM; a chunk re-warps 2 halo planes, so big volumes keep
+// long chunks and small ones get short, parallel marches.
 int force_default_zchunk(int nx, int ny, int nz) {
-    const long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
-    const long target = 152L * 6;   // resident CTAs on a full GPU
-    long chunks = (target + tiles - 1) / tiles;
-    if (chunks < 1) chunks = 1;
-    int zc = (int)((nz + chunks - 1) / chunks);
-    if (zc < 4) zc = 4;
-    return zc > nz ? nz : zc;
+    return pick_zchunk(nz, (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY), 4, 2);
 }
 
 size_t force_partial_count(int nx, int ny, int nz, int zchunk) {
@@ -556,7 +607,7 @@ cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaS
     const bool contour = a.contour && a.k > 0;
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     const size_t N = (size_t)a.nx * a.ny * a.nz;
-    if (err != nullptr && N < (size_t)1 << 31) {
+    if (err != nullptr && N < (size_t)1 << 31 && (!contour || a.mtex != nullptr)) {
         ForceMaps m;
         const uint64_t du4[4] = {(uint64_t)a.nx, (uint64_t)a.ny, (uint64_t)a.nz, 3};
         const uint64_t d3[3] = {(uint64_t)a.nx, (uint64_t)a.ny, (uint64_t)a.nz};
@@ -591,28 +642,32 @@ cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaS
     return cudaGetLastError();
 }
 
+// At most 16 voxels per thread, so each thread's FP32 partial sum stays short.
 static int metric_grid(int nx, int ny, int nz) {
     const size_t N = (size_t)nx * ny * nz;
-    size_t g = (N + MT - 1) / MT;
-    const size_t cap = 152 * 8;
-    return (int)(g < cap ? g : cap);
+    const size_t g = (N + MT * 16 - 1) / (MT * 16);
+    return (int)(g > 0 ? g : 1);
 }
 
 size_t metric_partial_count(int nx, int ny, int nz) { return (size_t)metric_grid(nx, ny, nz); }
 
 cudaError_t launch_metric(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
                           int nx, int ny, int nz, double *partial, const int *stop_flag,
-                          int *nblocks_out, cudaStream_t s) {
+                          int *nblocks_out, cudaStream_t s, const FinishArgs *fin) {
     const int g = metric_grid(nx, ny, nz);
     if (nblocks_out) *nblocks_out = g;
-    k_metric<<<g, MT, 0, s>>>(I0, T0, u, uroi, nx, ny, nz, partial, stop_flag);
+    FinishArgs f{};
+    if (fin) f = *fin;
+    k_metric<<<g, MT, 0, s>>>(I0, T0, u, uroi, nx, ny, nz, partial, stop_flag, f);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
                             int stop_mode, double eps, double *stats_out, cudaStream_t s) {
-    k_finalize<<<1, FT, 0, s>>>(partial, nblocks, st, n, cap, stop_mode, eps, stats_out);
+    FinishArgs f{};
+    f.st = st; f.n = n; f.cap = cap; f.stop_mode = stop_mode; f.eps = eps; f.stats_out = stats_out;
+    k_finalize<<<1, FT, 0, s>>>(partial, nblocks, f);
     note_launch();
     return cudaGetLastError();
 }

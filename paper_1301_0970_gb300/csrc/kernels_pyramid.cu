@@ -101,13 +101,15 @@ __global__ void k_prolong(const float *__restrict__ uc, int cx, int cy, int cz, 
     }
 }
 
-// ---- UROI: exact ellipsoidal dilation in two passes -------------------
+// ---- UROI: exact ellipsoidal dilation in three passes -----------------
 // pass 1: per voxel, the distance |dx| (voxels) to the nearest union voxel of
-// its x-row within rx, 255 if none.  pass 2: a voxel is in the UROI if for
-// some row offset (dy, dz) that row holds a union voxel within the x extent
-// the ellipsoid allows at (dy, dz).  The extents are computed on the host
-// with the same double expression as the definition, so the decision equals
-// the brute-force test voxel by voxel.
+// its x-row within rx, 255 if none.  pass 2: per voxel (x, y, z') and per
+// z offset dz, bit dz+rz says that some row (y+dy, z') holds a union voxel
+// within the x extent the ellipsoid allows at (dy, dz).  pass 3: voxel
+// (x, y, z) is in the UROI if bit dz+rz of pass 2 at (x, y, z+dz) is set for
+// some dz.  The extents are computed on the host with the same double
+// expression as the definition, so the decision equals the brute-force test
+// voxel by voxel.
 constexpr int kMaxUroiRadius = 15;
 struct UroiTable {
     int rx, ry, rz;
@@ -130,24 +132,38 @@ __global__ void k_uroi_rows(const uint8_t *__restrict__ sbits, unsigned mask, in
     }
 }
 
-__global__ void k_uroi_dilate(const uint8_t *__restrict__ rowdist, UroiTable t, int nx, int ny,
-                              int nz, uint8_t *__restrict__ out) {
+__global__ void k_uroi_planes(const uint8_t *__restrict__ rowdist, UroiTable t, int nx, int ny, int nz,
+                              uint32_t *__restrict__ zbits) {
     const size_t N = (size_t)nx * ny * nz;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
-        uint8_t hit = 0;
-        for (int dz = -t.rz; dz <= t.rz && !hit; ++dz) {
+        const int y = (int)((i / nx) % ny);
+        uint32_t b = 0;
+        for (int dy = -t.ry; dy <= t.ry; ++dy) {
+            const int yy = y + dy;
+            if (yy < 0 || yy >= ny) continue;
+            const int r = __ldg(rowdist + i + (ptrdiff_t)dy * nx);
+            if (r == 255) continue;
+            for (int dz = -t.rz; dz <= t.rz; ++dz)
+                if (r <= t.ext[dz + t.rz][dy + t.ry]) b |= 1u << (dz + t.rz);
+        }
+        zbits[i] = b;
+    }
+}
+
+__global__ void k_uroi_dilate(const uint32_t *__restrict__ zbits, int rz, int nx, int ny, int nz,
+                              uint8_t *__restrict__ out) {
+    const size_t N = (size_t)nx * ny * nz, nxy = (size_t)nx * ny;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int z = (int)(i / nxy);
+        uint32_t hit = 0;
+        for (int dz = -rz; dz <= rz; ++dz) {
             const int zz = z + dz;
             if (zz < 0 || zz >= nz) continue;
-            for (int dy = -t.ry; dy <= t.ry; ++dy) {
-                const int yy = y + dy;
-                if (yy < 0 || yy >= ny) continue;
-                const int e = t.ext[dz + t.rz][dy + t.ry];
-                if (e >= 0 && (int)__ldg(rowdist + vox(x, yy, zz, nx, ny)) <= e) { hit = 1; break; }
-            }
+            hit |= (__ldg(zbits + i + (ptrdiff_t)dz * (ptrdiff_t)nxy) >> (dz + rz)) & 1u;
         }
-        out[i] = hit;
+        out[i] = (uint8_t)hit;
     }
 }
 
@@ -209,6 +225,13 @@ __global__ void k_sum_rows4(const double *__restrict__ partial, int rows, double
     }
 }
 
+__global__ void k_make_texels(const float *__restrict__ I0, const uint8_t *__restrict__ bits, size_t n,
+                              float2 *__restrict__ tex) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        tex[i] = make_float2(__ldg(I0 + i), __uint_as_float((unsigned)__ldg(bits + i)));
+}
+
 template <typename T>
 __device__ __forceinline__ float to_f32(T v);
 template <>
@@ -253,8 +276,10 @@ cudaError_t launch_prolong(const float *uc, int cx, int cy, int cz, int nx, int 
     return cudaGetLastError();
 }
 
+// scratch: 5 N bytes (row distances, then per-voxel z masks at offset N
+// rounded up to 4 bytes).
 cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, const double *spacing,
-                        double margin, uint8_t *rowdist, uint8_t *out, cudaStream_t s) {
+                        double margin, uint8_t *scratch, uint8_t *out, cudaStream_t s) {
     const size_t N = (size_t)nx * ny * nz;
     if (k <= 0) {
         k_fill_u8<<<flat_grid(N), 256, 0, s>>>(out, N, 1); note_launch();
@@ -279,10 +304,15 @@ cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, con
             t.ext[dz + t.rz][dy + t.ry] = (int8_t)e;
         }
     const unsigned mask = (k >= 8) ? 0xffu : ((1u << k) - 1u);
+    uint8_t *rowdist = scratch;
+    uint32_t *zbits = reinterpret_cast<uint32_t *>(scratch + (N + 3) / 4 * 4);
     k_uroi_rows<<<flat_grid(N), 256, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist); note_launch();
-    k_uroi_dilate<<<flat_grid(N), 256, 0, s>>>(rowdist, t, nx, ny, nz, out); note_launch();
+    k_uroi_planes<<<flat_grid(N), 256, 0, s>>>(rowdist, t, nx, ny, nz, zbits); note_launch();
+    k_uroi_dilate<<<flat_grid(N), 256, 0, s>>>(zbits, t.rz, nx, ny, nz, out); note_launch();
     return cudaGetLastError();
 }
+
+size_t uroi_scratch_bytes(size_t n) { return (n + 3) / 4 * 4 + 4 * n; }
 
 // sums: device [k][4]; tmp_a, tmp_b: N bytes each; partial: sign_partial_rows(N) x 4 doubles.
 cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int nx, int ny,
@@ -303,6 +333,12 @@ cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int n
 }
 
 size_t sign_partial_rows(size_t n) { return flat_grid(n, 152 * 4); }
+
+cudaError_t launch_make_texels(const float *I0, const uint8_t *bits, size_t n, float2 *tex, cudaStream_t s) {
+    k_make_texels<<<flat_grid(n), 256, 0, s>>>(I0, bits, n, tex);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_convert_image(const void *in, int dtype, size_t n, float *out, cudaStream_t s) {
     if (dtype == CGDIR_F16) {

@@ -121,123 +121,212 @@ __global__ void __launch_bounds__(NT) k_smooth(const float *__restrict__ in,
 }
 
 // ---- TMA-fed version ---------------------------------------------------
+// A CTA (32 x 8 threads) filters NC components (NC = 1: one component per
+// CTA; NC = 3: the three components of a DVF, needed by the composite-update
+// epilogue) of a 32 x 16 column; each thread owns two adjacent output rows.
+// Per input plane one TMA box (x from x0 - ML, ML = R rounded up to 4 so the
+// start is 16-byte aligned; y from y0 - R) lands in a 4-stage ring.
+// x pass: each task filters 4 adjacent outputs of one row from 16-byte
+// shared loads; y pass: two rows from 2R+2 loads; z pass: a (2R+1)-deep
+// register ring whose slots are fixed at compile time by unrolling the
+// plane loop 2R+1 times.  One barrier per plane.
+//
+// COMPOSE (NC = 3): the z-pass result is the smoothed du at (x, y, z); the
+// epilogue applies Algorithm A step 3 there, u_new = du + u(x + du), so the
+// smoothed du never goes back to memory.
 constexpr int kStages = 4;
+constexpr int SY = 16;                 // output rows per CTA (2 per thread)
 
-// Box of one plane: x from x0 - ML (ML = R rounded up to 4, so the start is a
-// 16-byte multiple) over TX + 2 ML columns, y from y0 - R over TY + 2R rows.
-// Each stage starts on a 128-byte boundary.
-template <int R>
-struct SmoothSmem {
+template <int R, int NC>
+struct SmoothGeom {
     static constexpr int ML = (R + 3) / 4 * 4;
     static constexpr int BXW = TX + 2 * ML;
-    static constexpr int BY = TY + 2 * R;
-    static constexpr int STAGE = (3 * BY * BXW + 31) / 32 * 32;   // floats per stage (3 components)
+    static constexpr int BY = SY + 2 * R;
+    static constexpr int STAGE = (NC * BY * BXW + 31) / 32 * 32;   // floats per stage
+    static constexpr int NV = (4 + R + ML + 3) / 4;                // float4 per x task
+    static constexpr int XB = NC * BY * TX;                          // floats per X buffer
     static constexpr size_t bytes() {
-        return sizeof(float) * (kStages * STAGE + 2 * 3 * BY * TX) + kStages * sizeof(uint64_t) + 128;
+        return sizeof(float) * ((size_t)kStages * STAGE + 2 * XB) + kStages * sizeof(uint64_t) + 128;
     }
 };
 
-template <int R>
+__device__ __forceinline__ float trilinear_at(const float *__restrict__ f, size_t b0, int ddx, int ddy,
+                                              int ddz, float wx, float wy, float wz) {
+    const float c000 = __ldg(f + b0), c100 = __ldg(f + b0 + ddx), c010 = __ldg(f + b0 + ddy),
+                c110 = __ldg(f + b0 + ddy + ddx), c001 = __ldg(f + b0 + ddz), c101 = __ldg(f + b0 + ddz + ddx),
+                c011 = __ldg(f + b0 + ddz + ddy), c111 = __ldg(f + b0 + ddz + ddy + ddx);
+    const float e00 = fmaf(wx, c100 - c000, c000), e10 = fmaf(wx, c110 - c010, c010);
+    const float e01 = fmaf(wx, c101 - c001, c001), e11 = fmaf(wx, c111 - c011, c011);
+    const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
+    return fmaf(wz, f1 - f0, f0);
+}
+
+template <int R, int NC, bool COMPOSE>
 __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUtensorMap tin,
+                                                   const float *__restrict__ ucomp, int mode,
                                                    float *__restrict__ out, int ncomp, Taps taps,
                                                    int nx, int ny, int nz, int zchunk,
                                                    const int *stop_flag, int *err) {
     if (stop_flag && *stop_flag) return;
-    constexpr int BY = SmoothSmem<R>::BY, STAGE = SmoothSmem<R>::STAGE, K = 2 * R + 1;
-    constexpr int ML = SmoothSmem<R>::ML, BXW = SmoothSmem<R>::BXW;
+    using G = SmoothGeom<R, NC>;
+    constexpr int BY = G::BY, BXW = G::BXW, ML = G::ML, STAGE = G::STAGE, NV = G::NV, K = 2 * R + 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stage = reinterpret_cast<float *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *Xb = stage + kStages * STAGE;                       // [2][3][BY][TX]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Xb + 2 * 3 * BY * TX);
+    float *Xb = stage + kStages * STAGE;                            // [2][NC][BY][TX]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Xb + 2 * G::XB);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const size_t N = (size_t)nx * ny * nz;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
-    const int P = (ze - zb) + 2 * R;                           // input planes
-    const int x = x0 + tx, y = y0 + ty;
-    const bool act = x < nx && y < ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * SY;
+    const int nchunks = (nz + zchunk - 1) / zchunk;
+    const int chunk = (int)blockIdx.z % nchunks;
+    const int comp = NC == 1 ? (int)blockIdx.z / nchunks : 0;      // component of an NC=1 CTA
+    const int zb = chunk * zchunk, ze = min(zb + zchunk, nz);
+    const int P = (ze - zb) + 2 * R;
+    const int x = x0 + tx, ya = y0 + 2 * ty;                        // rows ya, ya + 1
+    const bool acta = x < nx && ya < ny, actb = x < nx && ya + 1 < ny;
     const bool xin = (x0 - R >= 0) && (x0 + TX + R <= nx);
-    const uint32_t tx_bytes = (uint32_t)(ncomp * BY * BXW * sizeof(float));
+    const uint32_t tx_bytes = (uint32_t)(NC * BY * BXW * sizeof(float));
+    (void)ncomp;
 
     float w[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) w[j] = taps.w[j];
-    float ring[3][K];
+    float ring[NC][2][K];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int j = 0; j < K; ++j) ring[c][j] = 0.f;
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < K; ++j) ring[c][h][j] = 0.f;
 
     auto issue = [&](int q) {
-        const int s = q % kStages;
+        const int sidx = q % kStages;
         const int z = clampi(zb - R + q, 0, nz - 1);
-        mbar_expect_tx(&bar[s], tx_bytes);
-        tma_load_4d(stage + s * STAGE, &tin, x0 - ML, y0 - R, z, 0, &bar[s]);
+        mbar_expect_tx(&bar[sidx], tx_bytes);
+        tma_load_4d(stage + sidx * STAGE, &tin, x0 - ML, y0 - R, z, comp, &bar[sidx]);
     };
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        for (int q = 0; q < kStages; ++q) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
+    int issued = 0;
     if (tid == 0)
-        for (int q = 0; q < kStages && q < P; ++q) issue(q);
+        for (; issued < kStages && issued < P; ++issued) issue(issued);
 
-    int t = 0;
-    for (; t < P; ++t) {
-        const int s = t % kStages;
-        const bool ok = mbar_wait_bounded(&bar[s], (uint32_t)((t / kStages) & 1));
-        const float *S = stage + s * STAGE;
-        float *X = Xb + (t & 1) * 3 * BY * TX;
-        // x pass over every (clamped) row of the box
-        for (int p = tid; p < BY * TX; p += NT) {
-            const int hy = p / TX, xx = p % TX;
-            const int ly = clampi(y0 - R + hy, 0, ny - 1) - (y0 - R);
+    bool aborted = false;
+    int tw = 0;                         // plane being waited for
+    for (int t0 = 0; t0 < P && !aborted; t0 += K) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (c >= ncomp) break;
-                const float *row = S + (c * BY + ly) * BXW;
-                float acc = 0.f;
+        for (int r = 0; r < K; ++r) {
+            const int t = t0 + r;
+            if (t >= P) break;
+            tw = t;
+            const int sidx = t % kStages;
+            const bool ok = mbar_wait_bounded(&bar[sidx], (uint32_t)((t / kStages) & 1));
+            const float *S = stage + sidx * STAGE;
+            float *X = Xb + (t & 1) * G::XB;
+            // x pass: NC * BY rows x TX/4 groups of 4 outputs
+            for (int task = tid; task < NC * BY * (TX / 4); task += NT) {
+                const int g = task & (TX / 4 - 1);
+                const int row = task >> 3;                          // c * BY + hy
+                const int c = NC == 1 ? 0 : row / BY;
+                const int hy = NC == 1 ? row : row - c * BY;
+                const int ly = clampi(y0 - R + hy, 0, ny - 1) - (y0 - R);
+                const float *src = S + (c * BY + ly) * BXW;
+                float o[4];
                 if (xin) {
+                    float v[4 * NV];
 #pragma unroll
-                    for (int j = 0; j < K; ++j) acc = fmaf(w[j], row[xx + j + ML - R], acc);
+                    for (int q = 0; q < NV; ++q) {
+                        const float4 f = reinterpret_cast<const float4 *>(src + 4 * g)[q];
+                        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int j = 0; j < K; ++j) acc = fmaf(w[j], v[q + j + ML - R], acc);
+                        o[q] = acc;
+                    }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < K; ++j)
-                        acc = fmaf(w[j], row[clampi(x0 + xx + j - R, 0, nx - 1) - x0 + ML], acc);
+                    for (int q = 0; q < 4; ++q) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int j = 0; j < K; ++j)
+                            acc = fmaf(w[j], src[clampi(x0 + 4 * g + q + j - R, 0, nx - 1) - x0 + ML], acc);
+                        o[q] = acc;
+                    }
                 }
-                X[(c * BY + hy) * TX + xx] = acc;
+                reinterpret_cast<float4 *>(X + row * TX)[g] = make_float4(o[0], o[1], o[2], o[3]);
             }
-        }
-        if (__syncthreads_or(!ok)) break;
-        if (tid == 0 && t + kStages < P) {
-            fence_proxy_async();
-            issue(t + kStages);
-        }
-        // y pass, z ring, output
+            if (__syncthreads_or(!ok)) { aborted = true; break; }
+            if (tid == 0 && issued < P) {
+                fence_proxy_async();
+                issue(issued);
+                ++issued;
+            }
+            // y pass into the ring slot of this plane, z pass for plane t - 2R
+            float res[NC][2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (c >= ncomp) break;
-            float acc = 0.f;
+            for (int c = 0; c < NC; ++c) {
+                const float *col = X + (c * BY + 2 * ty) * TX + tx;
+                float yin[K + 1];
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc = fmaf(w[j], X[(c * BY + ty + j) * TX + tx], acc);
+                for (int j = 0; j <= K; ++j) yin[j] = col[j * TX];
+                float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-            for (int j = 0; j < K - 1; ++j) ring[c][j] = ring[c][j + 1];
-            ring[c][K - 1] = acc;
-            if (t >= 2 * R && act) {
-                float o = 0.f;
+                for (int j = 0; j < K; ++j) { a0 = fmaf(w[j], yin[j], a0); a1 = fmaf(w[j], yin[j + 1], a1); }
+                ring[c][0][r] = a0;
+                ring[c][1][r] = a1;
+                float o0 = 0.f, o1 = 0.f;
 #pragma unroll
-                for (int j = 0; j < K; ++j) o = fmaf(w[j], ring[c][j], o);
-                out[c * N + vox(x, y, zb + t - 2 * R, nx, ny)] = o;
+                for (int j = 0; j < K; ++j) {
+                    o0 = fmaf(w[j], ring[c][0][(r + 1 + j) % K], o0);
+                    o1 = fmaf(w[j], ring[c][1][(r + 1 + j) % K], o1);
+                }
+                res[c][0] = o0;
+                res[c][1] = o1;
+            }
+            if (t >= 2 * R) {
+                const int zo = zb + t - 2 * R;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int y = ya + h;
+                    if (!(h == 0 ? acta : actb)) continue;
+                    const size_t i = ((size_t)zo * ny + y) * nx + x;
+                    if (COMPOSE) {
+                        const float dx = res[0][h], dy = res[NC > 1 ? 1 : 0][h], dz = res[NC > 2 ? 2 : 0][h];
+                        float ax, ay, az;
+                        if (mode == CGDIR_ADDITIVE) {
+                            ax = __ldg(ucomp + i); ay = __ldg(ucomp + N + i); az = __ldg(ucomp + 2 * N + i);
+                        } else {
+                            const Corners cc = corners((float)x + dx, (float)y + dy, (float)zo + dz, nx, ny, nz);
+                            const int ddx = cc.x1 - cc.x0, ddy = (cc.y1 - cc.y0) * nx, ddz = (cc.z1 - cc.z0) * nx * ny;
+                            const size_t b0 = ((size_t)cc.z0 * ny + cc.y0) * nx + cc.x0;
+                            ax = trilinear_at(ucomp, b0, ddx, ddy, ddz, cc.wx, cc.wy, cc.wz);
+                            ay = trilinear_at(ucomp + N, b0, ddx, ddy, ddz, cc.wx, cc.wy, cc.wz);
+                            az = trilinear_at(ucomp + 2 * N, b0, ddx, ddy, ddz, cc.wx, cc.wy, cc.wz);
+                        }
+                        out[i] = dx + ax;
+                        out[N + i] = dy + ay;
+                        out[2 * N + i] = dz + az;
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) out[(size_t)(comp + c) * N + i] = res[c][h];
+                    }
+                }
             }
         }
     }
-    if (t < P) {
+    if (aborted) {
         // a wait ran out: record it, drain the loads still in flight (bounded), leave
         if (tid == 0) {
             atomicExch(err, 1);
-            for (int q = t; q < P && q < t + kStages; ++q)
+            for (int q = tw; q < issued; ++q)
                 mbar_wait_bounded(&bar[q % kStages], (uint32_t)((q / kStages) & 1));
         }
         __syncthreads();
@@ -285,14 +374,10 @@ __global__ void k_compose(const float *__restrict__ u, const float *__restrict__
     }
 }
 
-int smooth_zchunk(int nx, int ny, int nz) {
-    const long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
-    const long target = 152L * 8;
-    long chunks = (target + tiles - 1) / tiles;
-    if (chunks < 1) chunks = 1;
-    int zc = (int)((nz + chunks - 1) / chunks);
-    if (zc < 8) zc = 8;
-    return zc > nz ? nz : zc;
+// z chunk of the smoothing kernels: about two waves of resident CTAs (4 per
+// SM for one component per CTA, 2 for the three-component compose variant).
+int smooth_zchunk(int nx, int ny, int nz, int rows, int comp_ctas, int resident) {
+    return pick_zchunk(nz, (long)((nx + TX - 1) / TX) * ((ny + rows - 1) / rows) * comp_ctas, resident, 2);
 }
 
 unsigned flat_grid(size_t n) {
@@ -303,14 +388,58 @@ unsigned flat_grid(size_t n) {
 
 }  // namespace
 
-template <int R>
-static cudaError_t smooth_tma_r(const CUtensorMap &m, float *out, int ncomp, const Taps &t, int nx,
-                                int ny, int nz, int zc, const int *stop_flag, int *err, dim3 grid,
-                                dim3 block, cudaStream_t s) {
-    const size_t smem = SmoothSmem<R>::bytes();
-    cudaError_t e = ensure_smem((const void *)k_smooth_tma<R>, smem);
+template <int R, int NC, bool COMPOSE>
+static cudaError_t smooth_tma_r(const float *in, const float *ucomp, int mode, float *out, int ncomp,
+                                const Taps &t, int nx, int ny, int nz, const int *stop_flag, int *err,
+                                cudaStream_t s, bool *launched) {
+    using G = SmoothGeom<R, NC>;
+    CUtensorMap m;
+    const uint64_t dims[4] = {(uint64_t)nx, (uint64_t)ny, (uint64_t)nz, (uint64_t)ncomp};
+    const uint32_t box[4] = {(uint32_t)G::BXW, (uint32_t)G::BY, 1u, (uint32_t)NC};
+    *launched = false;
+    if (!encode_tensor_map(&m, in, 4, dims, box, 4)) return cudaSuccess;
+    const int zc = smooth_zchunk(nx, ny, nz, SY, NC == 1 ? ncomp : 1, NC == 1 ? 4 : 2);
+    const int nchunks = (nz + zc - 1) / zc;
+    dim3 grid((nx + TX - 1) / TX, (ny + SY - 1) / SY, nchunks * (NC == 1 ? ncomp : 1)), block(TX, TY);
+    const size_t smem = G::bytes();
+    cudaError_t e = ensure_smem((const void *)k_smooth_tma<R, NC, COMPOSE>, smem);
     if (e != cudaSuccess) return e;
-    k_smooth_tma<R><<<grid, block, smem, s>>>(m, out, ncomp, t, nx, ny, nz, zc, stop_flag, err);
+    k_smooth_tma<R, NC, COMPOSE><<<grid, block, smem, s>>>(m, ucomp, mode, out, ncomp, t, nx, ny, nz, zc,
+                                                          stop_flag, err);
+    *launched = true;
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int NC, bool COMPOSE>
+static cudaError_t smooth_tma(const float *in, const float *ucomp, int mode, float *out, int ncomp,
+                              const Taps &t, int nx, int ny, int nz, const int *stop_flag, int *err,
+                              cudaStream_t s, bool *launched) {
+    switch (t.r) {
+        case 1: return smooth_tma_r<1, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
+        case 2: return smooth_tma_r<2, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
+        case 3: return smooth_tma_r<3, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
+        case 4: return smooth_tma_r<4, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
+        case 5: return smooth_tma_r<5, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
+        case 6: return smooth_tma_r<6, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
+        default: *launched = false; return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t smooth_plain(const float *in, int ncomp, const Taps &t, int nx, int ny, int nz,
+                                float *out, const int *stop_flag, cudaStream_t s) {
+    const int zc = smooth_zchunk(nx, ny, nz, TY, 1, 4);
+    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + zc - 1) / zc), block(TX, TY);
+    switch (t.r) {
+        case 1: k_smooth<1><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
+        case 2: k_smooth<2><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
+        case 3: k_smooth<3><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
+        case 4: k_smooth<4><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
+        case 5: k_smooth<5><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
+        case 6: k_smooth<6><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
+        default: return cudaErrorInvalidValue;
+    }
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -323,39 +452,27 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
         note_launch();
         return cudaGetLastError();
     }
-    const int zc = smooth_zchunk(nx, ny, nz);
-    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + zc - 1) / zc), block(TX, TY);
     if (err != nullptr) {
-        CUtensorMap m;
-        const uint64_t dims[4] = {(uint64_t)nx, (uint64_t)ny, (uint64_t)nz, (uint64_t)ncomp};
-        const uint32_t ml = (uint32_t)((t.r + 3) / 4 * 4);
-        const uint32_t box[4] = {(uint32_t)TX + 2 * ml, (uint32_t)(TY + 2 * t.r), 1u, (uint32_t)ncomp};
-        if (encode_tensor_map(&m, in, 4, dims, box, 4)) {
-            cudaError_t e;
-            switch (t.r) {
-                case 1: e = smooth_tma_r<1>(m, out, ncomp, t, nx, ny, nz, zc, stop_flag, err, grid, block, s); break;
-                case 2: e = smooth_tma_r<2>(m, out, ncomp, t, nx, ny, nz, zc, stop_flag, err, grid, block, s); break;
-                case 3: e = smooth_tma_r<3>(m, out, ncomp, t, nx, ny, nz, zc, stop_flag, err, grid, block, s); break;
-                case 4: e = smooth_tma_r<4>(m, out, ncomp, t, nx, ny, nz, zc, stop_flag, err, grid, block, s); break;
-                case 5: e = smooth_tma_r<5>(m, out, ncomp, t, nx, ny, nz, zc, stop_flag, err, grid, block, s); break;
-                case 6: e = smooth_tma_r<6>(m, out, ncomp, t, nx, ny, nz, zc, stop_flag, err, grid, block, s); break;
-                default: return cudaErrorInvalidValue;
-            }
-            note_launch();
-            return e;
-        }
+        bool launched = false;
+        cudaError_t e = smooth_tma<1, false>(in, nullptr, 0, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched);
+        if (e != cudaSuccess || launched) return e;
     }
-    switch (t.r) {
-        case 1: k_smooth<1><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
-        case 2: k_smooth<2><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
-        case 3: k_smooth<3><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
-        case 4: k_smooth<4><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
-        case 5: k_smooth<5><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
-        case 6: k_smooth<6><<<grid, block, 0, s>>>(in, out, ncomp, t, nx, ny, nz, zc, stop_flag); break;
-        default: return cudaErrorInvalidValue;
+    return smooth_plain(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+}
+
+cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
+                                  int nz, float *out, float *tmp, const int *stop_flag, cudaStream_t s,
+                                  int *err) {
+    const Taps t = gauss_taps(sigma);
+    if (t.r > 0 && err != nullptr) {
+        bool launched = false;
+        cudaError_t e = smooth_tma<3, true>(du, u, mode, out, 3, t, nx, ny, nz, stop_flag, err, s, &launched);
+        if (e != cudaSuccess || launched) return e;
     }
-    note_launch();
-    return cudaGetLastError();
+    // unfused: smooth du into tmp, then compose
+    cudaError_t e = launch_smooth(du, 3, sigma, nx, ny, nz, tmp, stop_flag, s, err);
+    if (e != cudaSuccess) return e;
+    return launch_compose(u, tmp, mode, nx, ny, nz, out, stop_flag, s);
 }
 
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,

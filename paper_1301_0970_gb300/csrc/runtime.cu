@@ -3,8 +3,8 @@
 // a fixed sequence of kernel launches on the context's stream.
 //
 // The per-iteration sequence at a level (u stays in one buffer):
-//   force(u -> du) ; finalize(delta^n, stop test) ; smooth(du -> du2) ;
-//   compose(u, du2 -> du) ; smooth(du -> u)
+//   force(u -> du) ; finalize(delta^n, stop test) ;
+//   smooth+compose(du, u -> du2) ; smooth(du2 -> u)
 // and after the level's cap a metric pass gives delta^cap.  The stopping
 // decision is taken on the device (finalize sets the level's stop flag and
 // every later kernel of the level returns at once), so a level never waits
@@ -76,6 +76,28 @@ struct cgdir_ctx {
 namespace cgdir {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int sm_count() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cache[dev] = n;
+    return n;
+}
+
+int pick_zchunk(int nz, long xy_ctas, int resident_per_sm, int waves) {
+    const long target = (long)waves * resident_per_sm * sm_count();
+    long chunks = (target + xy_ctas - 1) / (xy_ctas > 0 ? xy_ctas : 1);
+    if (chunks < 1) chunks = 1;
+    if (chunks > nz) chunks = nz;
+    return (int)((nz + chunks - 1) / chunks);
+}
 
 cudaError_t ensure_smem(const void *func, size_t bytes) {
     static std::mutex mu;
@@ -398,6 +420,14 @@ static int force_impl(cgdir_ctx *ctx, const ForceArgs &a, double *stats_host) {
     void *part = nullptr, *st = nullptr;
     ForceArgs b = a;
     const int zc = force_default_zchunk(a.nx, a.ny, a.nz);
+    if (b.contour && b.k > 0 && !ctx->plain_kernels && b.mtex == nullptr) {
+        // the TMA kernel gathers interleaved {I0, bits} texels
+        const size_t N = (size_t)a.nx * a.ny * a.nz;
+        void *tex = nullptr;
+        TRY(ws_get(ctx, "force_tex", N * sizeof(float2), &tex));
+        CK(launch_make_texels(a.I0, a.mbits, N, (float2 *)tex, ctx->stream));
+        b.mtex = (const float2 *)tex;
+    }
     if (stats_host) {
         TRY(ws_get(ctx, "partial", force_partial_count(a.nx, a.ny, a.nz, zc) * kPartialStride * sizeof(double), &part));
         TRY(ws_get(ctx, "stats", 4 * sizeof(double), &st));
@@ -478,17 +508,23 @@ int cgdir_iterate(cgdir_ctx *ctx, const float *I0, const float *T0, const uint8_
     TRY(fill_force_args(ctx, a, k, lambda, sign, offset, use_contour));
     DeviceGuard g(ctx->device);
     const size_t N = (size_t)nx * ny * nz;
-    void *t1 = nullptr, *t2 = nullptr;
+    void *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
     TRY(ws_get(ctx, "iter_a", 3 * N * sizeof(float), &t1));
     TRY(ws_get(ctx, "iter_b", 3 * N * sizeof(float), &t2));
-    float *du = (float *)t1, *dus = du_out ? du_out : (float *)t2;
+    TRY(ws_get(ctx, "iter_c", 3 * N * sizeof(float), &t3));
+    float *du = (float *)t1, *un = (float *)t2;
     a.I0 = I0; a.T0 = T0; a.mbits = mbits; a.sbits = sbits; a.uroi = uroi; a.u = u_in; a.du = du;
     a.warped = nullptr; a.stop_flag = nullptr;
     a.nx = nx; a.ny = ny; a.nz = nz;
     TRY(force_impl(ctx, a, stats_host));
-    CK(launch_smooth(du, 3, sigma_fluid, nx, ny, nz, dus, nullptr, ctx->stream, kerr(ctx)));
-    CK(launch_compose(u_in, dus, compose_mode, nx, ny, nz, du, nullptr, ctx->stream));
-    CK(launch_smooth(du, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx)));
+    if (du_out) {   // the smoothed du is wanted: steps 2 and 3 separately
+        CK(launch_smooth(du, 3, sigma_fluid, nx, ny, nz, du_out, nullptr, ctx->stream, kerr(ctx)));
+        CK(launch_compose(u_in, du_out, compose_mode, nx, ny, nz, un, nullptr, ctx->stream));
+    } else {
+        CK(launch_smooth_compose(du, u_in, compose_mode, sigma_fluid, nx, ny, nz, un, (float *)t3, nullptr,
+                                 ctx->stream, kerr(ctx)));
+    }
+    CK(launch_smooth(un, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx)));
     return CGDIR_OK;
 }
 
@@ -525,7 +561,7 @@ int cgdir_uroi(cgdir_ctx *ctx, const uint8_t *sbits, int k, int nx, int ny, int 
         return fail(ctx, CGDIR_EINVAL, "uroi: bad arguments");
     DeviceGuard g(ctx->device);
     void *rd = nullptr;
-    TRY(ws_get(ctx, "rowdist", (size_t)nx * ny * nz, &rd));
+    TRY(ws_get(ctx, "rowdist", uroi_scratch_bytes((size_t)nx * ny * nz), &rd));
     const double sp1[3] = {1, 1, 1};
     cudaError_t e = launch_uroi(sbits, k, nx, ny, nz, spacing ? spacing : sp1, margin, (uint8_t *)rd, out,
                                 ctx->stream);
@@ -665,6 +701,8 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     void *p_img, *p_bits, *p_fields, *p_part, *p_state, *p_rowdist;
     TRY(ws_get(ctx, "reg_img", 2 * Ntot * sizeof(float), &p_img));
     TRY(ws_get(ctx, "reg_bits", 3 * Ntot, &p_bits));
+    void *p_tex = nullptr;
+    TRY(ws_get(ctx, "reg_tex", Ntot * sizeof(float2), &p_tex));
     TRY(ws_get(ctx, "reg_fields", 4 * 3 * Nf * sizeof(float), &p_fields));
     size_t np = 0;
     for (int l = 0; l < L; ++l) {
@@ -674,9 +712,9 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
         np = std::max(np, std::max(a, b));
     }
     TRY(ws_get(ctx, "reg_partial", np * kPartialStride * sizeof(double), &p_part));
-    const size_t state_bytes = (size_t)L * hcap * sizeof(double) + 4 * CGDIR_MAX_LEVELS * sizeof(int);
+    const size_t state_bytes = (size_t)L * hcap * sizeof(double) + 5 * CGDIR_MAX_LEVELS * sizeof(int);
     TRY(ws_get(ctx, "reg_state", state_bytes, &p_state));
-    TRY(ws_get(ctx, "rowdist", Nf, &p_rowdist));
+    TRY(ws_get(ctx, "rowdist", uroi_scratch_bytes(Nf), &p_rowdist));
     void *p_stage = nullptr;
     const bool need_stage = (S->where == CGDIR_HOST && S->dtype != CGDIR_F32) ||
                             (M->where == CGDIR_HOST && M->dtype != CGDIR_F32) ||
@@ -699,6 +737,7 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     int *meta = (int *)((char *)p_state + (size_t)L * hcap * sizeof(double));
     int *hist_len = meta, *iters_run = meta + CGDIR_MAX_LEVELS, *reason = meta + 2 * CGDIR_MAX_LEVELS,
         *flags = meta + 3 * CGDIR_MAX_LEVELS;
+    unsigned *done = (unsigned *)(meta + 4 * CGDIR_MAX_LEVELS);   // per-level completion counters
 
     // ---- ingest images (finest level)
     auto ingest = [&](const cgdir_volume *v, float *dst) -> int {
@@ -769,6 +808,10 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
             CK(launch_restrict_bits(MB[l + 1], d[0], d[1], d[2], MB[l], s));
         }
         for (int l = 0; l < L; ++l) {
+            if (((P->contour_level_mask >> l) & 1u) && k > 0 && !ctx->plain_kernels) {
+                ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
+                CK(launch_make_texels(I[l], MB[l], Nl[l], (float2 *)p_tex + off[l], s));
+            }
             const double f = (double)(1 << (L - 1 - l));
             const double sp[3] = {P->spacing_mm[0] * f, P->spacing_mm[1] * f, P->spacing_mm[2] * f};
             ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
@@ -796,29 +839,34 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
             st.hist_cap = hcap;
             ForceArgs a = base;
             a.I0 = I[l]; a.T0 = T[l]; a.mbits = MB[l]; a.sbits = SB[l]; a.uroi = UR[l];
+            a.mtex = ctx->plain_kernels ? nullptr : (const float2 *)p_tex + off[l];
             a.u = ucur; a.du = du; a.warped = nullptr; a.partial = partial; a.stop_flag = flags + l;
             a.nx = lx; a.ny = ly; a.nz = lz;
             a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
             const int zc = force_default_zchunk(lx, ly, lz);
             const int cap = P->iters[l];
             const unsigned m = ctx->prof_mask;
+            a.fin.done = done + l;
+            a.fin.st = st;
+            a.fin.cap = cap;
+            a.fin.stop_mode = P->stop_mode;
+            a.fin.eps = P->eps;
+            a.fin.stats_out = nullptr;
             for (int n = 0; n < cap; ++n) {
                 int nb = 0;
+                a.fin.n = n;   // the force kernel's last CTA reduces delta^n and runs the stop test
                 { ProfScope ps(pl, m, s, CGDIR_K_FORCE, l); CK(launch_force(a, zc, &nb, s, kerr(ctx))); }
-                { ProfScope ps(pl, m, s, CGDIR_K_FINALIZE, l);
-                  CK(launch_finalize(partial, nb, st, n, cap, P->stop_mode, P->eps, nullptr, s)); }
-                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_DU, l);
-                  CK(launch_smooth(du, 3, P->sigma_fluid, lx, ly, lz, du2, flags + l, s, kerr(ctx))); }
-                { ProfScope ps(pl, m, s, CGDIR_K_COMPOSE, l);
-                  CK(launch_compose(ucur, du2, P->compose_mode, lx, ly, lz, du, flags + l, s)); }
-                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_U, l);
-                  CK(launch_smooth(du, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx))); }
+                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3
+                  CK(launch_smooth_compose(du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, du2, uoth,
+                                           flags + l, s, kerr(ctx))); }
+                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_U, l);    // step 4
+                  CK(launch_smooth(du2, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx))); }
             }
             int nb = 0;
+            FinishArgs fm = a.fin;
+            fm.n = cap;
             { ProfScope ps(pl, m, s, CGDIR_K_METRIC, l);
-              CK(launch_metric(I[l], T[l], ucur, UR[l], lx, ly, lz, partial, flags + l, &nb, s)); }
-            { ProfScope ps(pl, m, s, CGDIR_K_FINALIZE, l);
-              CK(launch_finalize(partial, nb, st, cap, cap, P->stop_mode, P->eps, nullptr, s)); }
+              CK(launch_metric(I[l], T[l], ucur, UR[l], lx, ly, lz, partial, flags + l, &nb, s, &fm)); }
         }
         return CGDIR_OK;
     };
