@@ -286,6 +286,26 @@ int cgdir_rms_id(cgdir_ctx *ctx, const float *I0, const float *T0, const float *
                  const uint8_t *uroi, int nx, int ny, int nz, double *rms_host,
                  long long *count_host);
 
+/* RMS-ID over the UROI, like cgdir_rms_id, for callers that cannot allocate
+   device memory: hosts that own every byte of it through their own pool (a
+   framework's caching allocator, a planning system with a fixed device
+   budget) or loops where allocation is forbidden.  The paper has no
+   counterpart; this is a service entry point of the library.
+   It takes no context and allocates nothing: its scratch (per-CTA partial
+   sums, a completion counter, the result) is a fixed array in the library's
+   device memory, which every GPU that loads the library holds until the
+   process exits.  Limit: nx*ny*nz <= 67,108,864 voxels; larger volumes are
+   rejected with CGDIR_EINVAL.  Device pointers as in cgdir_rms_id (uroi may be
+   NULL = whole volume); stream = cudaStream_t (NULL = legacy default stream).
+   Blocking: *rms_host (and *count_host if not NULL) are written on return.
+   The first call on a device looks up the array's device address (with that
+   device current); make that first call before any stream capture.  All calls
+   share the one array: calls whose work overlaps on the GPU (two streams or
+   threads at once) race and give undefined results.  Errors: EINVAL, ECUDA. */
+int cgdir_rms_id_noalloc(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
+                         int nx, int ny, int nz, void *stream, double *rms_host,
+                         long long *count_host);
+
 /* ---- instrumentation (not part of the paper's method) ------------------ */
 
 /* Number of CUDA kernels this library has launched in the process so far

@@ -101,6 +101,8 @@ _SIGNATURES = {
                                 POINTER(c_int8)]),
     "cgdir_rms_id": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int,
                              c_int, POINTER(c_double), POINTER(c_longlong)]),
+    "cgdir_rms_id_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                     c_void_p, POINTER(c_double), POINTER(c_longlong)]),
 }
 
 _lib = None
