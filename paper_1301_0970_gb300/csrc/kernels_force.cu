@@ -90,34 +90,31 @@ __device__ int stop_test(const double *d, int n, int mode, double eps) {
 }
 
 // Fixed-order sum of the per-CTA partials, RMS-ID into the level history and
-// the stop decision (kernel 5).  Run by one CTA of blockDim >= 1 (any shape).
+// the stop decision (kernel 5).  Run by one whole CTA (any shape, blockDim a
+// multiple of 32, at most 1024 threads): each thread sums a fixed stride of
+// partials, then warp shuffles and warp 0 combine them in a fixed order.
 __device__ void finalize_block(const double *__restrict__ partial, int nblocks, const FinishArgs &f) {
-    constexpr int FT = 256;
-    __shared__ double ss[FT], sc[FT], sx[FT];
+    __shared__ double ws[32], wc[32], wm[32];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nt = blockDim.x * blockDim.y;
-    if (tid < FT) {
-        double s = 0.0, c = 0.0, m = 0.0;
-        for (int b = tid; b < nblocks; b += FT) {
-            s += __ldcg(partial + (size_t)b * kPartialStride + 0);
-            c += __ldcg(partial + (size_t)b * kPartialStride + 1);
-            m = fmax(m, __ldcg(partial + (size_t)b * kPartialStride + 2));
-        }
-        ss[tid] = s; sc[tid] = c; sx[tid] = m;
+    double s = 0.0, c = 0.0, m = 0.0;
+    for (int b = tid; b < nblocks; b += nt) {
+        s += __ldcg(partial + (size_t)b * kPartialStride + 0);
+        c += __ldcg(partial + (size_t)b * kPartialStride + 1);
+        m = fmax(m, __ldcg(partial + (size_t)b * kPartialStride + 2));
     }
-    (void)nt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((tid & 31) == 0) { ws[tid >> 5] = s; wc[tid >> 5] = c; wm[tid >> 5] = m; }
     __syncthreads();
-    for (int h = FT / 2; h > 0; h >>= 1) {
-        if (tid < h) {
-            ss[tid] += ss[tid + h];
-            sc[tid] += sc[tid + h];
-            sx[tid] = fmax(sx[tid], sx[tid + h]);
-        }
-        __syncthreads();
-    }
     if (tid == 0) {
-        const double S = ss[0], C = sc[0];
-        if (f.stats_out) { f.stats_out[0] = S; f.stats_out[1] = C; f.stats_out[2] = sx[0]; }
+        double S = 0.0, C = 0.0, M = 0.0;
+        for (int w = 0; w < nt / 32; ++w) { S += ws[w]; C += wc[w]; M = fmax(M, wm[w]); }
+        if (f.stats_out) { f.stats_out[0] = S; f.stats_out[1] = C; f.stats_out[2] = M; }
         const LevelState &st = f.st;
         if (st.hist) {
             const double d = C > 0 ? sqrt(S / C) : 0.0;
@@ -278,7 +275,7 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
 
 
 // ---- TMA-fed version -------------------------------------------------------
-constexpr int kFStages = 3;
+constexpr int kFStages = 5;
 constexpr int UBX = TX + 8;           // DVF box width: x0-4 .. x0+35
 constexpr int UBY = TY + 2;           // DVF box height: y0-1 .. y0+8
 constexpr int U_BYTES = 3 * UBY * UBX * 4;                 // 4800
@@ -343,6 +340,21 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
     if (tid == 0)
         for (; issued < kFStages && issued < P; ++issued) issue(issued);
 
+    // halo points of this thread (the same in every plane): offset of the
+    // DVF value in a stage (-1 = none) and the clamped voxel coordinates
+    constexpr int PPT = (HP + NT - 1) / NT;
+    int hp_u[PPT];
+    float hp_gx[PPT], hp_gy[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int p = tid + q * NT;
+        const int hx = p % HX, hy = p / HX;
+        const int gx = clampi(x0 - 1 + hx, 0, nx - 1), gy = clampi(y0 - 1 + hy, 0, ny - 1);
+        hp_u[q] = p < HP ? (gy - (y0 - 1)) * UBX + (gx - (x0 - 4)) : -1;
+        hp_gx[q] = (float)gx;
+        hp_gy[q] = (float)gy;
+    }
+    const float fxmax = (float)(nx - 1), fymax = (float)(ny - 1), fzmax = (float)(nz - 1);
     float ssd = 0.f;
     int cnt = 0;
     float mx = 0.f;
@@ -355,17 +367,17 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
             const float *U = reinterpret_cast<const float *>(stages + sidx * STAGE_BYTES);
             float *W = ring + (t % kRing) * nv * HP;
             uint16_t *Sg = state + (t % kRing) * HP;
-            const int gz = clampi(zb - 1 + t, 0, nz - 1);
-            for (int p = tid; p < HP; p += NT) {
-                const int hx = p % HX, hy = p / HX;
-                const int gx = clampi(x0 - 1 + hx, 0, nx - 1), gy = clampi(y0 - 1 + hy, 0, ny - 1);
-                const int lx = gx - (x0 - 4), ly = gy - (y0 - 1);
-                const float ux = U[(0 * UBY + ly) * UBX + lx];
-                const float uy = U[(1 * UBY + ly) * UBX + lx];
-                const float uz = U[(2 * UBY + ly) * UBX + lx];
-                const float px = fminf(fmaxf((float)gx + ux, 0.f), (float)(nx - 1));
-                const float py = fminf(fmaxf((float)gy + uy, 0.f), (float)(ny - 1));
-                const float pz = fminf(fmaxf((float)gz + uz, 0.f), (float)(nz - 1));
+            const float gzf = (float)clampi(zb - 1 + t, 0, nz - 1);
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                if (hp_u[q] < 0) continue;
+                const int p = tid + q * NT;
+                const float ux = U[hp_u[q]];
+                const float uy = U[UBY * UBX + hp_u[q]];
+                const float uz = U[2 * UBY * UBX + hp_u[q]];
+                const float px = fminf(fmaxf(hp_gx[q] + ux, 0.f), fxmax);
+                const float py = fminf(fmaxf(hp_gy[q] + uy, 0.f), fymax);
+                const float pz = fminf(fmaxf(gzf + uz, 0.f), fzmax);
                 const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
                 const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
                 const float wx = px - fx, wy = py - fy, wz = pz - fz;
@@ -470,18 +482,17 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
                                    s4 = Sc[cidx + HX], s5 = Sm[cidx], s6 = Sp[cidx];
                     const unsigned A = (s0 & s1 & s2 & s3 & s4 & s5 & s6) >> 8;      // inside at every corner
                     const unsigned O = (s0 | s1 | s2 | s3 | s4 | s5 | s6) & 0xffu;   // inside at some corner
+                    const unsigned mixed = O & ~A;                                   // needs the stored P_j
 #pragma unroll
                     for (int j = 0; j < kMaxMasks; ++j) {
                         if (j < a.k) {
                             const float hs = a.half_sign[j];
                             const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
                             float aj, rj;
-                            if (!((O >> j) & 1u)) {
-                                aj = gn;
-                                rj = r0 + hs * inside;
-                            } else if ((A >> j) & 1u) {
-                                aj = gn + hs * gn;
-                                rj = r0 + hs * (inside - (w0 + off));
+                            if (!((mixed >> j) & 1u)) {
+                                const float b = (float)((A >> j) & 1u);     // P_j = b (I0~ + offset) on the stencil
+                                aj = fmaf(hs * b, gn, gn);
+                                rj = fmaf(hs, inside - b * (w0 + off), r0);
                             } else {
                                 const float *Pjm = Pm + (1 + j) * HP, *Pjc = Pc + (1 + j) * HP,
                                             *Pjp = Pp + (1 + j) * HP;

@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(NT) k_smooth(const float *__restrict__ in,
 // COMPOSE (NC = 3): the z-pass result is the smoothed du at (x, y, z); the
 // epilogue applies Algorithm A step 3 there, u_new = du + u(x + du), so the
 // smoothed du never goes back to memory.
-constexpr int kStages = 4;
 constexpr int SY = 16;                 // output rows per CTA (2 per thread)
 
 template <int R, int NC>
@@ -142,11 +141,14 @@ struct SmoothGeom {
     static constexpr int ML = (R + 3) / 4 * 4;
     static constexpr int BXW = TX + 2 * ML;
     static constexpr int BY = SY + 2 * R;
+    static constexpr int ST = NC == 1 ? 8 : 6;                      // pipeline stages
     static constexpr int STAGE = (NC * BY * BXW + 31) / 32 * 32;   // floats per stage
     static constexpr int NV = (4 + R + ML + 3) / 4;                // float4 per x task
     static constexpr int XB = NC * BY * TX;                          // floats per X buffer
+    static constexpr int NTASK = NC * BY * (TX / 4);                 // x-pass tasks per plane
+    static constexpr int TPT = (NTASK + NT - 1) / NT;                // tasks per thread
     static constexpr size_t bytes() {
-        return sizeof(float) * ((size_t)kStages * STAGE + 2 * XB) + kStages * sizeof(uint64_t) + 128;
+        return sizeof(float) * ((size_t)ST * STAGE + 2 * XB) + ST * sizeof(uint64_t) + 128;
     }
 };
 
@@ -170,14 +172,15 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
     if (stop_flag && *stop_flag) return;
     using G = SmoothGeom<R, NC>;
     constexpr int BY = G::BY, BXW = G::BXW, ML = G::ML, STAGE = G::STAGE, NV = G::NV, K = 2 * R + 1;
+    constexpr int ST = G::ST, TPT = G::TPT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *stage = reinterpret_cast<float *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *Xb = stage + kStages * STAGE;                            // [2][NC][BY][TX]
+    float *Xb = stage + ST * STAGE;                                 // [2][NC][BY][TX]
     uint64_t *bar = reinterpret_cast<uint64_t *>(Xb + 2 * G::XB);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const size_t N = (size_t)nx * ny * nz;
+    const size_t N = (size_t)nx * ny * nz, nxy = (size_t)nx * ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * SY;
     const int nchunks = (nz + zchunk - 1) / zchunk;
     const int chunk = (int)blockIdx.z % nchunks;
@@ -190,78 +193,91 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
     const uint32_t tx_bytes = (uint32_t)(NC * BY * BXW * sizeof(float));
     (void)ncomp;
 
-    float w[K];
+    float2 w2[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) w[j] = taps.w[j];
-    float ring[NC][2][K];
+    for (int j = 0; j < K; ++j) w2[j] = make_float2(taps.w[j], taps.w[j]);
+    float2 ring[NC][K];                                             // {row ya, row ya+1}
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < K; ++j) ring[c][j] = make_float2(0.f, 0.f);
+
+    // x-pass tasks of this thread (the same in every plane): row offset in a
+    // stage, first column of its 4 outputs, destination offset in X
+    int t_row[TPT], t_g4[TPT], t_dst[TPT];
 #pragma unroll
-            for (int j = 0; j < K; ++j) ring[c][h][j] = 0.f;
+    for (int q = 0; q < TPT; ++q) {
+        const int task = tid + q * NT;
+        const int g = task & (TX / 4 - 1), row = task >> 3;         // row = c * BY + hy
+        const int c = NC == 1 ? 0 : row / BY, hy = row - c * BY;
+        const int ly = clampi(y0 - R + hy, 0, ny - 1) - (y0 - R);
+        t_row[q] = task < G::NTASK ? (c * BY + ly) * BXW : -1;
+        t_g4[q] = 4 * g;
+        t_dst[q] = row * TX + 4 * g;
+    }
+    float *outp[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) outp[c] = out + (size_t)(comp + c) * N + (size_t)ya * nx + x;
 
     auto issue = [&](int q) {
-        const int sidx = q % kStages;
+        const int sidx = q % ST;
         const int z = clampi(zb - R + q, 0, nz - 1);
         mbar_expect_tx(&bar[sidx], tx_bytes);
         tma_load_4d(stage + sidx * STAGE, &tin, x0 - ML, y0 - R, z, comp, &bar[sidx]);
     };
     if (tid == 0) {
-        for (int q = 0; q < kStages; ++q) mbar_init(&bar[q], 1);
+        for (int q = 0; q < ST; ++q) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
     int issued = 0;
     if (tid == 0)
-        for (; issued < kStages && issued < P; ++issued) issue(issued);
+        for (; issued < ST && issued < P; ++issued) issue(issued);
 
     bool aborted = false;
     int tw = 0;                         // plane being waited for
+    int sidx = 0;                       // its stage
+    uint32_t par = 0;                   // and the phase parity of that stage
     for (int t0 = 0; t0 < P && !aborted; t0 += K) {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
             const int t = t0 + r;
             if (t >= P) break;
             tw = t;
-            const int sidx = t % kStages;
-            const bool ok = mbar_wait_bounded(&bar[sidx], (uint32_t)((t / kStages) & 1));
+            const bool ok = mbar_wait_bounded(&bar[sidx], par);
             const float *S = stage + sidx * STAGE;
             float *X = Xb + (t & 1) * G::XB;
-            // x pass: NC * BY rows x TX/4 groups of 4 outputs
-            for (int task = tid; task < NC * BY * (TX / 4); task += NT) {
-                const int g = task & (TX / 4 - 1);
-                const int row = task >> 3;                          // c * BY + hy
-                const int c = NC == 1 ? 0 : row / BY;
-                const int hy = NC == 1 ? row : row - c * BY;
-                const int ly = clampi(y0 - R + hy, 0, ny - 1) - (y0 - R);
-                const float *src = S + (c * BY + ly) * BXW;
-                float o[4];
+            // x pass: 4 adjacent outputs per task, paired FMAs
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+                if (t_row[q] < 0) continue;
+                const float *src = S + t_row[q];
+                float2 o01 = make_float2(0.f, 0.f), o23 = make_float2(0.f, 0.f);
                 if (xin) {
                     float v[4 * NV];
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        const float4 f = reinterpret_cast<const float4 *>(src + 4 * g)[q];
-                        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+                    for (int h = 0; h < NV; ++h) {
+                        const float4 f = reinterpret_cast<const float4 *>(src + t_g4[q])[h];
+                        v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float acc = 0.f;
-#pragma unroll
-                        for (int j = 0; j < K; ++j) acc = fmaf(w[j], v[q + j + ML - R], acc);
-                        o[q] = acc;
+                    for (int j = 0; j < K; ++j) {
+                        o01 = __ffma2_rn(w2[j], make_float2(v[j + ML - R], v[j + 1 + ML - R]), o01);
+                        o23 = __ffma2_rn(w2[j], make_float2(v[j + 2 + ML - R], v[j + 3 + ML - R]), o23);
                     }
                 } else {
+                    const int gx = x0 + t_g4[q] - R;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float acc = 0.f;
-#pragma unroll
-                        for (int j = 0; j < K; ++j)
-                            acc = fmaf(w[j], src[clampi(x0 + 4 * g + q + j - R, 0, nx - 1) - x0 + ML], acc);
-                        o[q] = acc;
+                    for (int j = 0; j < K; ++j) {
+                        const float a0 = src[clampi(gx + j, 0, nx - 1) - x0 + ML];
+                        const float a1 = src[clampi(gx + j + 1, 0, nx - 1) - x0 + ML];
+                        const float a2 = src[clampi(gx + j + 2, 0, nx - 1) - x0 + ML];
+                        const float a3 = src[clampi(gx + j + 3, 0, nx - 1) - x0 + ML];
+                        o01 = __ffma2_rn(w2[j], make_float2(a0, a1), o01);
+                        o23 = __ffma2_rn(w2[j], make_float2(a2, a3), o23);
                     }
                 }
-                reinterpret_cast<float4 *>(X + row * TX)[g] = make_float4(o[0], o[1], o[2], o[3]);
+                reinterpret_cast<float4 *>(X + t_dst[q])[0] = make_float4(o01.x, o01.y, o23.x, o23.y);
             }
             if (__syncthreads_or(!ok)) { aborted = true; break; }
             if (tid == 0 && issued < P) {
@@ -269,37 +285,37 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
                 issue(issued);
                 ++issued;
             }
+            if (++sidx == ST) { sidx = 0; par ^= 1u; }
             // y pass into the ring slot of this plane, z pass for plane t - 2R
-            float res[NC][2];
+            float2 res[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const float *col = X + (c * BY + 2 * ty) * TX + tx;
                 float yin[K + 1];
 #pragma unroll
                 for (int j = 0; j <= K; ++j) yin[j] = col[j * TX];
-                float a0 = 0.f, a1 = 0.f;
+                float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < K; ++j) { a0 = fmaf(w[j], yin[j], a0); a1 = fmaf(w[j], yin[j + 1], a1); }
-                ring[c][0][r] = a0;
-                ring[c][1][r] = a1;
-                float o0 = 0.f, o1 = 0.f;
+                for (int j = 0; j < K; ++j) a = __ffma2_rn(w2[j], make_float2(yin[j], yin[j + 1]), a);
+                ring[c][r] = a;
+                float2 o = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    o0 = fmaf(w[j], ring[c][0][(r + 1 + j) % K], o0);
-                    o1 = fmaf(w[j], ring[c][1][(r + 1 + j) % K], o1);
-                }
-                res[c][0] = o0;
-                res[c][1] = o1;
+                for (int j = 0; j < K; ++j) o = __ffma2_rn(w2[j], ring[c][(r + 1 + j) % K], o);
+                res[c] = o;
             }
             if (t >= 2 * R) {
                 const int zo = zb + t - 2 * R;
+                const size_t zoff = (size_t)zo * nxy;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int y = ya + h;
                     if (!(h == 0 ? acta : actb)) continue;
-                    const size_t i = ((size_t)zo * ny + y) * nx + x;
+                    const size_t off = zoff + (size_t)h * nx;
                     if (COMPOSE) {
-                        const float dx = res[0][h], dy = res[NC > 1 ? 1 : 0][h], dz = res[NC > 2 ? 2 : 0][h];
+                        const int y = ya + h;
+                        const size_t i = off + (size_t)ya * nx + x;
+                        const float dx = h ? res[0].y : res[0].x;
+                        const float dy = NC > 1 ? (h ? res[NC > 1 ? 1 : 0].y : res[NC > 1 ? 1 : 0].x) : 0.f;
+                        const float dz = NC > 2 ? (h ? res[NC > 2 ? 2 : 0].y : res[NC > 2 ? 2 : 0].x) : 0.f;
                         float ax, ay, az;
                         if (mode == CGDIR_ADDITIVE) {
                             ax = __ldg(ucomp + i); ay = __ldg(ucomp + N + i); az = __ldg(ucomp + 2 * N + i);
@@ -311,12 +327,12 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
                             ay = trilinear_at(ucomp + N, b0, ddx, ddy, ddz, cc.wx, cc.wy, cc.wz);
                             az = trilinear_at(ucomp + 2 * N, b0, ddx, ddy, ddz, cc.wx, cc.wy, cc.wz);
                         }
-                        out[i] = dx + ax;
-                        out[N + i] = dy + ay;
-                        out[2 * N + i] = dz + az;
+                        outp[0][off] = dx + ax;
+                        outp[0][N + off] = dy + ay;
+                        outp[0][2 * N + off] = dz + az;
                     } else {
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) out[(size_t)(comp + c) * N + i] = res[c][h];
+                        for (int c = 0; c < NC; ++c) outp[c][off] = h ? res[c].y : res[c].x;
                     }
                 }
             }
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
         if (tid == 0) {
             atomicExch(err, 1);
             for (int q = tw; q < issued; ++q)
-                mbar_wait_bounded(&bar[q % kStages], (uint32_t)((q / kStages) & 1));
+                mbar_wait_bounded(&bar[q % ST], (uint32_t)((q / ST) & 1));
         }
         __syncthreads();
     }
