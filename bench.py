@@ -61,6 +61,28 @@ def dist_env():
     return world, rank, local
 
 
+def replica_case_index(rank: int) -> int:
+    """Replicas only: every rank registers its own case (seeded by its rank);
+    no data crosses ranks."""
+    return rank
+
+
+def reduce_max(value: float, device=None) -> float:
+    """Max over ranks of a per-rank time (the only collective of a run)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, vox_iters_per_step: int, steps: int, max_total_ms: float) -> float:
+    """voxel-iterations of all ranks / the slowest rank's time."""
+    return world * vox_iters_per_step * steps / (max_total_ms / 1e3)
+
+
 def workload_config(case, n_gpus):
     nz, ny, nx = case.shape
     return {"workload": f"{WORKLOAD['name']}: {nx}x{ny}x{nz} float32 CT, {case.k} uint8 structure "
@@ -173,18 +195,21 @@ def measured_peaks():
 
 
 def force_traffic_record(case):
-    """dram bytes per launch of the force kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "force_headneck256_traffic.json")
+    """DRAM bytes per launch of the force kernel from the committed ncu
+    summary (profiles/force_headneck256.md), if it was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "force_headneck256.md")
     src = os.path.join(ROOT, "paper_1301_0970_gb300", "csrc", "kernels_force.cu")
     if not os.path.exists(path):
         return None
-    with open(path) as f:
-        rec = json.load(f)
+    sha, traffic = None, None
+    for line in open(path):
+        if line.startswith("- kernels_force.cu sha1:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("- dram bytes per launch (full size):"):
+            traffic = float(line.split(":", 1)[1].strip())
     h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    if rec.get("kernels_force_sha1") != h:
-        return None
-    return float(rec["dram_bytes_per_launch_full_size"])
+    return traffic if (sha == h and traffic) else None
 
 
 # --------------------------------------------------------------------------- #
@@ -226,7 +251,7 @@ def run_cgdir(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case = phantom.make_case(WORKLOAD["name"], index=rank)
+    case = phantom.make_case(WORKLOAD["name"], index=replica_case_index(rank))
     L, iters = WORKLOAD["levels"], WORKLOAD["iters"]
     vox_iters = phantom.voxel_iters(case.shape, L, iters)
     N = int(np.prod(case.shape))
@@ -269,11 +294,8 @@ def run_cgdir(args):
     total_ms = sum(step_ms)
     prof = ctx.profile_read()
     ctx.profile([])
-    tot = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
-    max_total_ms = float(tot.item())
-    value = world * vox_iters * args.steps / (max_total_ms / 1e3)
+    max_total_ms = reduce_max(total_ms, dev)
+    value = whole_job_value(world, vox_iters, args.steps, max_total_ms)
 
     # ---- one profiled step with every kernel class timed (breakdown only)
     ctx.profile(list(range(7)))
@@ -298,14 +320,12 @@ def run_cgdir(args):
             t0 = time.perf_counter()
             _, st = ctx.register(Sh, Mh, SMh, MMh, dvf_out=dvf_h, **kw)
             et.append(time.perf_counter() - t0)
-        t = torch.tensor([sum(et)], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = reduce_max(sum(et), dev)
         h2d = 2 * N * 4 + 2 * case.k * N
         d2h = 3 * N * 4 + L * (max(iters) + 1) * 8 + 4 * 8 * 4
-        e2e = {"value": world * vox_iters * args.steps / float(t.item()), "unit": UNIT,
+        e2e = {"value": whole_job_value(world, vox_iters, args.steps, 1e3 * t_max), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": 1e3 * float(t.item()) / args.steps}
+               "ms_per_step": 1e3 * t_max / args.steps}
 
     # ---- roofline of the dominant kernel: force at the finest level
     fine = [p for p in prof if p["kernel"] == "force" and p["level"] == L - 1]
