@@ -66,6 +66,7 @@ extern "C" {
 #define CGDIR_F32   0        /* image storage types                             */
 #define CGDIR_F16   1
 #define CGDIR_BF16  2
+#define CGDIR_STORAGE_AUTO (-1)   /* pyramid images keep the input type       */
 
 #define CGDIR_HOST    0      /* where a buffer lives                            */
 #define CGDIR_DEVICE  1
@@ -135,6 +136,13 @@ typedef struct {
     const float  *init_dvf;           /* NULL, or a full-resolution DVF that
                                          replaces the coarse levels (Sec. 4)    */
     int           init_dvf_where;     /* CGDIR_HOST or CGDIR_DEVICE             */
+    int           storage_dtype;      /* type of the pyramid's images: CGDIR_F32,
+                                         CGDIR_F16, CGDIR_BF16 (inputs converted
+                                         at ingest, round to nearest even), or
+                                         CGDIR_STORAGE_AUTO = the input type (F32
+                                         if static and moving differ).  All force,
+                                         DVF and smoothing arithmetic is FP32
+                                         whatever the storage.                  */
 } cgdir_params;
 
 typedef struct {

@@ -21,6 +21,7 @@ from . import build as _build
 # ---- constants (include/cgdir.h) ------------------------------------------
 CGDIR_OK, CGDIR_EINVAL, CGDIR_ENOMEM, CGDIR_ECUDA, CGDIR_ETIMEDOUT, CGDIR_ECANCELED, CGDIR_EBUSY = range(7)
 CGDIR_F32, CGDIR_F16, CGDIR_BF16 = 0, 1, 2
+CGDIR_STORAGE_AUTO = -1
 CGDIR_HOST, CGDIR_DEVICE = 0, 1
 CGDIR_STOP_FIXED, CGDIR_STOP_WINDOW10, CGDIR_STOP_PAPER_LITERAL = 0, 1, 2
 CGDIR_COMPOSE, CGDIR_ADDITIVE = 0, 1
@@ -48,7 +49,7 @@ class cgdir_params(ctypes.Structure):
                 ("contour_level_mask", c_uint), ("stop_mode", c_int), ("eps", c_double),
                 ("spacing_mm", c_double * 3), ("margin_mm", c_double),
                 ("intensity_offset", c_float), ("compose_mode", c_int),
-                ("init_dvf", c_void_p), ("init_dvf_where", c_int)]
+                ("init_dvf", c_void_p), ("init_dvf_where", c_int), ("storage_dtype", c_int)]
 
 
 class cgdir_level_stats(ctypes.Structure):
@@ -254,7 +255,7 @@ class Context:
                  stop_mode: int = CGDIR_STOP_WINDOW10, eps: float = 1e-4,
                  spacing_mm=(1.97, 1.97, 2.5), margin_mm: float = 10.0,
                  intensity_offset: float = 1000.0, compose_mode: int = CGDIR_COMPOSE,
-                 init_dvf=None, dvf_out=None):
+                 init_dvf=None, dvf_out=None, storage_dtype: int = CGDIR_STORAGE_AUTO):
         """Algorithm A on (static, moving) [nz,ny,nx] tensors (CUDA or CPU;
         float32/16/bf16) with k-long lists (or [k,nz,ny,nx] tensors) of uint8
         masks.  Returns (dvf [3,nz,ny,nx] float32, stats list coarse->fine)."""
@@ -292,6 +293,7 @@ class Context:
         p.margin_mm = margin_mm
         p.intensity_offset = intensity_offset
         p.compose_mode = compose_mode
+        p.storage_dtype = storage_dtype
         if init_dvf is not None:
             p.init_dvf = c_void_p(_ptr(init_dvf))
             p.init_dvf_where = CGDIR_DEVICE if init_dvf.is_cuda else CGDIR_HOST

@@ -8,6 +8,7 @@
 #include <stddef.h>
 
 #include "cgdir.h"
+#include "imgtype.cuh"
 
 namespace cgdir {
 
@@ -80,10 +81,11 @@ struct FinishArgs {
 };
 
 struct ForceArgs {
-    const float *I0, *T0;
+    const void *I0, *T0;      // images of type img_dtype (CGDIR_F32 / F16 / BF16)
+    int img_dtype;
     const uint8_t *mbits, *sbits, *uroi;
-    const float2 *mtex;       // moving texels {I0, mask bits as uint32}; used by the TMA
-                              // kernel when the contour terms are on (null otherwise)
+    const void *mtex;         // moving texels (see imgtype.cuh); used by the TMA kernel
+                              // when the contour terms are on (null otherwise)
     const float *u;
     float *du, *warped;
     double *partial;          // [gridDim.x*gridDim.y*gridDim.z][kPartialStride] or null
@@ -114,9 +116,10 @@ cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaS
                          int *err = nullptr);
 size_t force_partial_count(int nx, int ny, int nz, int zchunk);
 int force_default_zchunk(int nx, int ny, int nz);
-cudaError_t launch_metric(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
-                          int nx, int ny, int nz, double *partial, const int *stop_flag,
-                          int *nblocks_out, cudaStream_t s, const FinishArgs *fin = nullptr);
+cudaError_t launch_metric(const void *I0, const void *T0, int img_dtype, const float *u,
+                          const uint8_t *uroi, int nx, int ny, int nz, double *partial,
+                          const int *stop_flag, int *nblocks_out, cudaStream_t s,
+                          const FinishArgs *fin = nullptr);
 size_t metric_partial_count(int nx, int ny, int nz);
 cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
                             int stop_mode, double eps, double *stats_out, cudaStream_t s);
@@ -137,7 +140,7 @@ cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, 
 
 cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint8_t *bits,
                               cudaStream_t s);
-cudaError_t launch_restrict_image(const float *in, int nx, int ny, int nz, float *out,
+cudaError_t launch_restrict_image(const void *in, int dtype, int nx, int ny, int nz, void *out,
                                   cudaStream_t s);
 cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint8_t *out,
                                  cudaStream_t s);
@@ -146,12 +149,15 @@ cudaError_t launch_prolong(const float *uc, int cx, int cy, int cz, int nx, int 
 cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, const double *spacing,
                         double margin, uint8_t *scratch, uint8_t *out, cudaStream_t s);
 size_t uroi_scratch_bytes(size_t n);
-cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int nx, int ny, int nz,
+cudaError_t launch_sign_sums(const void *T0, int dtype, const uint8_t *sbits, int k, int nx, int ny, int nz,
                              uint8_t *tmp_a, uint8_t *tmp_b, double *partial,
                              double *sums /* [k][4] */, cudaStream_t s);
 size_t sign_partial_rows(size_t n);
-cudaError_t launch_convert_image(const void *in, int dtype, size_t n, float *out, cudaStream_t s);
-// Interleave the moving image with its mask bits: tex[v] = {I0[v], bits[v]}.
-cudaError_t launch_make_texels(const float *I0, const uint8_t *bits, size_t n, float2 *tex, cudaStream_t s);
+// Convert n image values from in_dtype to out_dtype (round to nearest even).
+cudaError_t launch_convert_image(const void *in, int in_dtype, size_t n, void *out, int out_dtype,
+                                 cudaStream_t s);
+// Interleave the moving image with its mask bits into texels (imgtype.cuh).
+cudaError_t launch_make_texels(const void *I0, int dtype, const uint8_t *bits, size_t n, void *tex,
+                               cudaStream_t s);
 
 }  // namespace cgdir

@@ -148,9 +148,10 @@ __device__ void finish_if_last(const double *partial, int nblocks, const FinishA
 
 // Interpolate I0~ and the k structure sums P_i at the halo points of plane zz.
 // slot layout: [1 + k][HP].
-template <bool CONTOUR>
+template <bool CONTOUR, typename IT>
 __device__ __forceinline__ void force_plane(const ForceArgs &a, int zz, float *slot, int x0, int y0,
                                             int tid) {
+    const IT *I0 = static_cast<const IT *>(a.I0);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const size_t N = (size_t)nx * ny * nz;
     const int gz = clampi(zz, 0, nz - 1);
@@ -172,7 +173,7 @@ __device__ __forceinline__ void force_plane(const ForceArgs &a, int zz, float *s
             const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
                             ((q & 4) ? c.wz : 1.f - c.wz);
             const size_t ci = vox(cx, cy, cz, nx, ny);
-            const float v = __ldg(a.I0 + ci);
+            const float v = ld_img<IT>(I0 + ci);
             acc = fmaf(w, v, acc);
             if (CONTOUR) {
                 const unsigned b = __ldg(a.mbits + ci);
@@ -191,7 +192,7 @@ __device__ __forceinline__ void force_plane(const ForceArgs &a, int zz, float *s
     }
 }
 
-template <bool CONTOUR>
+template <bool CONTOUR, typename IT>
 __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
     if (a.stop_flag && *a.stop_flag) return;
     extern __shared__ float sm[];
@@ -205,8 +206,8 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
     const bool act = x < nx && y < ny;
     const int c = (ty + 1) * HX + (tx + 1);
 
-    force_plane<CONTOUR>(a, zb - 1, sm, x0, y0, tid);
-    force_plane<CONTOUR>(a, zb, sm + plane, x0, y0, tid);
+    force_plane<CONTOUR, IT>(a, zb - 1, sm, x0, y0, tid);
+    force_plane<CONTOUR, IT>(a, zb, sm + plane, x0, y0, tid);
     float ssd = 0.f;
     int cnt = 0;
     float mx = 0.f;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
         const int r = z - zb;
         float *Pm = sm + (r % 3) * plane, *Pc = sm + ((r + 1) % 3) * plane,
               *Pp = sm + ((r + 2) % 3) * plane;
-        force_plane<CONTOUR>(a, z + 1, Pp, x0, y0, tid);
+        force_plane<CONTOUR, IT>(a, z + 1, Pp, x0, y0, tid);
         __syncthreads();
         if (act) {
             const size_t i = vox(x, y, z, nx, ny);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
             const float gx = 0.5f * (Pc[c + 1] - Pc[c - 1]);
             const float gy = 0.5f * (Pc[c + HX] - Pc[c - HX]);
             const float gz = 0.5f * (Pp[c] - Pm[c]);
-            const float T = __ldg(a.T0 + i);
+            const float T = ld_img<IT>(static_cast<const IT *>(a.T0) + i);
             const float r0 = T - w0;
             if (a.warped) a.warped[i] = w0;
             const float g2 = gx * gx + gy * gy + gz * gz;
@@ -294,9 +295,10 @@ __host__ __device__ constexpr size_t force2_smem_bytes(int nv) {
            kFStages * 8;
 }
 
-template <bool CONTOUR>
+template <bool CONTOUR, typename IT>
 __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceMaps maps, ForceArgs a,
                                                   int zchunk, int *err) {
+    using TT = typename TexOf<IT>::type;
     if (a.stop_flag && *a.stop_flag) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
     const bool act = x < nx && y < ny;
     const int cidx = (ty + 1) * HX + (tx + 1);
     const float off = a.offset;
-    const uint32_t tx_bytes = (uint32_t)(U_BYTES + TX * TY * 4 + (CONTOUR ? TX * TY : 0) +
+    const uint32_t tx_bytes = (uint32_t)(U_BYTES + TX * TY * sizeof(IT) + (CONTOUR ? TX * TY : 0) +
                                          (a.uroi ? TX * TY : 0));
 
     auto issue = [&](int q) {
@@ -386,21 +388,20 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
                 float c000, c100, c010, c110, c001, c101, c011, c111;
                 unsigned m000 = 0, m100 = 0, m010 = 0, m110 = 0, m001 = 0, m101 = 0, m011 = 0, m111 = 0;
                 if (CONTOUR) {
-                    const float2 *q0 = a.mtex + b0;
-                    const float2 t000 = __ldg(q0), t100 = __ldg(q0 + dx), t010 = __ldg(q0 + dy),
-                                 t110 = __ldg(q0 + dy + dx), t001 = __ldg(q0 + dz), t101 = __ldg(q0 + dz + dx),
-                                 t011 = __ldg(q0 + dz + dy), t111 = __ldg(q0 + dz + dy + dx);
-                    c000 = t000.x; c100 = t100.x; c010 = t010.x; c110 = t110.x;
-                    c001 = t001.x; c101 = t101.x; c011 = t011.x; c111 = t111.x;
-                    m000 = __float_as_uint(t000.y); m100 = __float_as_uint(t100.y);
-                    m010 = __float_as_uint(t010.y); m110 = __float_as_uint(t110.y);
-                    m001 = __float_as_uint(t001.y); m101 = __float_as_uint(t101.y);
-                    m011 = __float_as_uint(t011.y); m111 = __float_as_uint(t111.y);
+                    const TT *q0 = static_cast<const TT *>(a.mtex) + b0;
+                    tex_unpack<IT>(__ldg(q0), c000, m000);
+                    tex_unpack<IT>(__ldg(q0 + dx), c100, m100);
+                    tex_unpack<IT>(__ldg(q0 + dy), c010, m010);
+                    tex_unpack<IT>(__ldg(q0 + dy + dx), c110, m110);
+                    tex_unpack<IT>(__ldg(q0 + dz), c001, m001);
+                    tex_unpack<IT>(__ldg(q0 + dz + dx), c101, m101);
+                    tex_unpack<IT>(__ldg(q0 + dz + dy), c011, m011);
+                    tex_unpack<IT>(__ldg(q0 + dz + dy + dx), c111, m111);
                 } else {
-                    const float *q0 = a.I0 + b0;
-                    c000 = __ldg(q0); c100 = __ldg(q0 + dx); c010 = __ldg(q0 + dy); c110 = __ldg(q0 + dy + dx);
-                    c001 = __ldg(q0 + dz); c101 = __ldg(q0 + dz + dx); c011 = __ldg(q0 + dz + dy);
-                    c111 = __ldg(q0 + dz + dy + dx);
+                    const IT *q0 = static_cast<const IT *>(a.I0) + b0;
+                    c000 = ld_img<IT>(q0); c100 = ld_img<IT>(q0 + dx); c010 = ld_img<IT>(q0 + dy);
+                    c110 = ld_img<IT>(q0 + dy + dx); c001 = ld_img<IT>(q0 + dz); c101 = ld_img<IT>(q0 + dz + dx);
+                    c011 = ld_img<IT>(q0 + dz + dy); c111 = ld_img<IT>(q0 + dz + dy + dx);
                 }
                 const float e00 = fmaf(wx, c100 - c000, c000), e10 = fmaf(wx, c110 - c010, c010);
                 const float e01 = fmaf(wx, c101 - c001, c001), e11 = fmaf(wx, c111 - c011, c011);
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
             const float gxv = 0.5f * (Pc[cidx + 1] - Pc[cidx - 1]);
             const float gyv = 0.5f * (Pc[cidx + HX] - Pc[cidx - HX]);
             const float gzv = 0.5f * (Pp[cidx] - Pm[cidx]);
-            const float T = reinterpret_cast<const float *>(st + T_OFF)[ty * TX + tx];
+            const float T = to_f<IT>(reinterpret_cast<const IT *>(st + T_OFF)[ty * TX + tx]);
             const float r0 = T - w0;
             if (a.warped) a.warped[i] = w0;
             const float g2 = gxv * gxv + gyv * gyv + gzv * gzv;
@@ -539,8 +540,9 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
 // Metric-only pass: I0~ at every voxel and the UROI partial sums (the warp
 // of Algorithm A step 5 after a level's last update).
 constexpr int MT = 256;
-__global__ void __launch_bounds__(MT) k_metric(const float *__restrict__ I0,
-                                               const float *__restrict__ T0,
+template <typename IT>
+__global__ void __launch_bounds__(MT) k_metric(const IT *__restrict__ I0,
+                                               const IT *__restrict__ T0,
                                                const float *__restrict__ u,
                                                const uint8_t *__restrict__ uroi, int nx, int ny,
                                                int nz, double *partial, const int *stop_flag,
@@ -560,9 +562,9 @@ __global__ void __launch_bounds__(MT) k_metric(const float *__restrict__ I0,
             const int cx = (q & 1) ? c.x1 : c.x0, cy = (q & 2) ? c.y1 : c.y0, cz = (q & 4) ? c.z1 : c.z0;
             const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
                             ((q & 4) ? c.wz : 1.f - c.wz);
-            acc = fmaf(w, __ldg(I0 + vox(cx, cy, cz, nx, ny)), acc);
+            acc = fmaf(w, ld_img<IT>(I0 + vox(cx, cy, cz, nx, ny)), acc);
         }
-        const float r = __ldg(T0 + i) - acc;
+        const float r = ld_img<IT>(T0 + i) - acc;
         ssd = fmaf(r, r, ssd);
         cnt += 1;
     }
@@ -611,12 +613,10 @@ size_t force_partial_count(int nx, int ny, int nz, int zchunk) {
     return (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zchunk - 1) / zchunk);
 }
 
-cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s, int *err) {
-    if (zchunk <= 0) zchunk = force_default_zchunk(a.nx, a.ny, a.nz);
-    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
-    dim3 block(TX, TY);
+template <typename IT>
+static cudaError_t launch_force_t(const ForceArgs &a, int zchunk, dim3 grid, dim3 block, cudaStream_t s,
+                                  int *err) {
     const bool contour = a.contour && a.k > 0;
-    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     const size_t N = (size_t)a.nx * a.ny * a.nz;
     if (err != nullptr && N < (size_t)1 << 31 && (!contour || a.mtex != nullptr)) {
         ForceMaps m;
@@ -624,33 +624,42 @@ cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaS
         const uint64_t d3[3] = {(uint64_t)a.nx, (uint64_t)a.ny, (uint64_t)a.nz};
         const uint32_t ubox[4] = {UBX, UBY, 1, 3}, tbox[3] = {TX, TY, 1};
         bool ok = encode_tensor_map(&m.u, a.u, 4, du4, ubox, 4) &&
-                  encode_tensor_map(&m.t0, a.T0, 3, d3, tbox, 4);
+                  encode_tensor_map(&m.t0, a.T0, 3, d3, tbox, (int)sizeof(IT));
         if (ok && contour) ok = encode_tensor_map(&m.sb, a.sbits, 3, d3, tbox, 1);
         if (ok && a.uroi) ok = encode_tensor_map(&m.ur, a.uroi, 3, d3, tbox, 1);
         if (ok) {
             const size_t smem = force2_smem_bytes(contour ? 1 + a.k : 1);
             cudaError_t e;
             if (contour) {
-                e = ensure_smem((const void *)k_force_tma<true>, smem);
-                if (e == cudaSuccess) k_force_tma<true><<<grid, block, smem, s>>>(m, a, zchunk, err);
+                e = ensure_smem((const void *)k_force_tma<true, IT>, smem);
+                if (e == cudaSuccess) k_force_tma<true, IT><<<grid, block, smem, s>>>(m, a, zchunk, err);
             } else {
-                e = ensure_smem((const void *)k_force_tma<false>, smem);
-                if (e == cudaSuccess) k_force_tma<false><<<grid, block, smem, s>>>(m, a, zchunk, err);
+                e = ensure_smem((const void *)k_force_tma<false, IT>, smem);
+                if (e == cudaSuccess) k_force_tma<false, IT><<<grid, block, smem, s>>>(m, a, zchunk, err);
             }
             note_launch();
             return e != cudaSuccess ? e : cudaGetLastError();
         }
     }
     const size_t smem = 3u * (1 + (contour ? a.k : 0)) * HP * sizeof(float);
-    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     if (contour) {
-        ensure_smem((const void *)k_force<true>, smem);
-        k_force<true><<<grid, block, smem, s>>>(a, zchunk);
+        ensure_smem((const void *)k_force<true, IT>, smem);
+        k_force<true, IT><<<grid, block, smem, s>>>(a, zchunk);
     } else {
-        k_force<false><<<grid, block, smem, s>>>(a, zchunk);
+        k_force<false, IT><<<grid, block, smem, s>>>(a, zchunk);
     }
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaStream_t s, int *err) {
+    if (zchunk <= 0) zchunk = force_default_zchunk(a.nx, a.ny, a.nz);
+    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
+    dim3 block(TX, TY);
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    if (a.img_dtype == CGDIR_F16) return launch_force_t<__half>(a, zchunk, grid, block, s, err);
+    if (a.img_dtype == CGDIR_BF16) return launch_force_t<__nv_bfloat16>(a, zchunk, grid, block, s, err);
+    return launch_force_t<float>(a, zchunk, grid, block, s, err);
 }
 
 // At most 16 voxels per thread, so each thread's FP32 partial sum stays short.
@@ -662,14 +671,22 @@ static int metric_grid(int nx, int ny, int nz) {
 
 size_t metric_partial_count(int nx, int ny, int nz) { return (size_t)metric_grid(nx, ny, nz); }
 
-cudaError_t launch_metric(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
-                          int nx, int ny, int nz, double *partial, const int *stop_flag,
-                          int *nblocks_out, cudaStream_t s, const FinishArgs *fin) {
+cudaError_t launch_metric(const void *I0, const void *T0, int img_dtype, const float *u,
+                          const uint8_t *uroi, int nx, int ny, int nz, double *partial,
+                          const int *stop_flag, int *nblocks_out, cudaStream_t s, const FinishArgs *fin) {
     const int g = metric_grid(nx, ny, nz);
     if (nblocks_out) *nblocks_out = g;
     FinishArgs f{};
     if (fin) f = *fin;
-    k_metric<<<g, MT, 0, s>>>(I0, T0, u, uroi, nx, ny, nz, partial, stop_flag, f);
+    if (img_dtype == CGDIR_F16)
+        k_metric<__half><<<g, MT, 0, s>>>((const __half *)I0, (const __half *)T0, u, uroi, nx, ny, nz, partial,
+                                          stop_flag, f);
+    else if (img_dtype == CGDIR_BF16)
+        k_metric<__nv_bfloat16><<<g, MT, 0, s>>>((const __nv_bfloat16 *)I0, (const __nv_bfloat16 *)T0, u, uroi,
+                                                 nx, ny, nz, partial, stop_flag, f);
+    else
+        k_metric<float><<<g, MT, 0, s>>>((const float *)I0, (const float *)T0, u, uroi, nx, ny, nz, partial,
+                                         stop_flag, f);
     note_launch();
     return cudaGetLastError();
 }

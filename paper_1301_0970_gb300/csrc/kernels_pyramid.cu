@@ -33,9 +33,11 @@ __global__ void k_pack(MaskPtrs m, int k, size_t n, uint8_t *__restrict__ bits) 
     }
 }
 
-// 2x2x2 box mean, source indices clamped (odd sizes replicate the border).
-__global__ void k_restrict_image(const float *__restrict__ in, int nx, int ny, int nz,
-                                 float *__restrict__ out) {
+// 2x2x2 box mean, source indices clamped (odd sizes replicate the border),
+// accumulated in float32 and stored in the image type.
+template <typename IT>
+__global__ void k_restrict_image(const IT *__restrict__ in, int nx, int ny, int nz,
+                                 IT *__restrict__ out) {
     const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
     const size_t Nc = (size_t)cx * cy * cz;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < Nc;
@@ -46,9 +48,9 @@ __global__ void k_restrict_image(const float *__restrict__ in, int nx, int ny, i
         for (int q = 0; q < 8; ++q) {
             const int x = min(2 * X + (q & 1), nx - 1), y = min(2 * Y + ((q >> 1) & 1), ny - 1),
                       z = min(2 * Z + ((q >> 2) & 1), nz - 1);
-            s += __ldg(in + vox(x, y, z, nx, ny));
+            s += ld_img<IT>(in + vox(x, y, z, nx, ny));
         }
-        out[i] = s * 0.125f;
+        out[i] = from_f<IT>(s * 0.125f);
     }
 }
 
@@ -194,7 +196,8 @@ __global__ void k_dilate_axis(const uint8_t *__restrict__ in, int axis, int nx, 
 
 constexpr int ST = 256;
 // Per block: {sum T0 inside j, count inside, sum T0 in shell, count shell}.
-__global__ void __launch_bounds__(ST) k_sign_partial(const float *__restrict__ T0,
+template <typename IT>
+__global__ void __launch_bounds__(ST) k_sign_partial(const IT *__restrict__ T0,
                                                      const uint8_t *__restrict__ sbits,
                                                      const uint8_t *__restrict__ dil, int j,
                                                      size_t n, double *__restrict__ partial) {
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(ST) k_sign_partial(const float *__restrict__ T
     for (size_t i = (size_t)blockIdx.x * ST + threadIdx.x; i < n; i += (size_t)gridDim.x * ST) {
         const bool in = (__ldg(sbits + i) >> j) & 1u;
         const bool sh = !in && ((__ldg(dil + i) >> j) & 1u);
-        const double t = (double)__ldg(T0 + i);
+        const double t = (double)ld_img<IT>(T0 + i);
         if (in) { a += t; b += 1.0; }
         if (sh) { c += t; d += 1.0; }
     }
@@ -225,25 +228,26 @@ __global__ void k_sum_rows4(const double *__restrict__ partial, int rows, double
     }
 }
 
-__global__ void k_make_texels(const float *__restrict__ I0, const uint8_t *__restrict__ bits, size_t n,
-                              float2 *__restrict__ tex) {
+__global__ void k_make_texels_f32(const float *__restrict__ I0, const uint8_t *__restrict__ bits, size_t n,
+                                  float2 *__restrict__ tex) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
         tex[i] = make_float2(__ldg(I0 + i), __uint_as_float((unsigned)__ldg(bits + i)));
 }
 
-template <typename T>
-__device__ __forceinline__ float to_f32(T v);
-template <>
-__device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
-template <>
-__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <typename T>
-__global__ void k_convert(const T *__restrict__ in, size_t n, float *__restrict__ out) {
+// 16-bit images: low half = the value's bits, bits 16..23 = the mask bits.
+__global__ void k_make_texels_16(const unsigned short *__restrict__ I0, const uint8_t *__restrict__ bits,
+                                 size_t n, uint32_t *__restrict__ tex) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
-        out[i] = to_f32<T>(in[i]);
+        tex[i] = (uint32_t)__ldg(I0 + i) | ((uint32_t)__ldg(bits + i) << 16);
+}
+
+template <typename IN, typename OUT>
+__global__ void k_convert(const IN *__restrict__ in, size_t n, OUT *__restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = from_f<OUT>(to_f<IN>(in[i]));
 }
 
 }  // namespace
@@ -256,10 +260,17 @@ cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_restrict_image(const float *in, int nx, int ny, int nz, float *out,
+cudaError_t launch_restrict_image(const void *in, int dtype, int nx, int ny, int nz, void *out,
                                   cudaStream_t s) {
     const size_t Nc = (size_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
-    k_restrict_image<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out); note_launch();
+    if (dtype == CGDIR_F16)
+        k_restrict_image<__half><<<flat_grid(Nc), 256, 0, s>>>((const __half *)in, nx, ny, nz, (__half *)out);
+    else if (dtype == CGDIR_BF16)
+        k_restrict_image<__nv_bfloat16><<<flat_grid(Nc), 256, 0, s>>>((const __nv_bfloat16 *)in, nx, ny, nz,
+                                                                      (__nv_bfloat16 *)out);
+    else
+        k_restrict_image<float><<<flat_grid(Nc), 256, 0, s>>>((const float *)in, nx, ny, nz, (float *)out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -315,7 +326,7 @@ cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, con
 size_t uroi_scratch_bytes(size_t n) { return (n + 3) / 4 * 4 + 4 * n; }
 
 // sums: device [k][4]; tmp_a, tmp_b: N bytes each; partial: sign_partial_rows(N) x 4 doubles.
-cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int nx, int ny,
+cudaError_t launch_sign_sums(const void *T0, int dtype, const uint8_t *sbits, int k, int nx, int ny,
                                 int nz, uint8_t *tmp_a, uint8_t *tmp_b, double *partial,
                                 double *sums, cudaStream_t s) {
     const size_t N = (size_t)nx * ny * nz;
@@ -326,7 +337,13 @@ cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int n
     note_launch(3);
     const unsigned gp = flat_grid(N, 152 * 4);
     for (int j = 0; j < k; ++j) {
-        k_sign_partial<<<gp, ST, 0, s>>>(T0, sbits, tmp_a, j, N, partial); note_launch();
+        if (dtype == CGDIR_F16)
+            k_sign_partial<__half><<<gp, ST, 0, s>>>((const __half *)T0, sbits, tmp_a, j, N, partial);
+        else if (dtype == CGDIR_BF16)
+            k_sign_partial<__nv_bfloat16><<<gp, ST, 0, s>>>((const __nv_bfloat16 *)T0, sbits, tmp_a, j, N, partial);
+        else
+            k_sign_partial<float><<<gp, ST, 0, s>>>((const float *)T0, sbits, tmp_a, j, N, partial);
+        note_launch();
         k_sum_rows4<<<1, 32, 0, s>>>(partial, (int)gp, sums + 4 * j); note_launch();
     }
     return cudaGetLastError();
@@ -334,20 +351,30 @@ cudaError_t launch_sign_sums(const float *T0, const uint8_t *sbits, int k, int n
 
 size_t sign_partial_rows(size_t n) { return flat_grid(n, 152 * 4); }
 
-cudaError_t launch_make_texels(const float *I0, const uint8_t *bits, size_t n, float2 *tex, cudaStream_t s) {
-    k_make_texels<<<flat_grid(n), 256, 0, s>>>(I0, bits, n, tex);
+cudaError_t launch_make_texels(const void *I0, int dtype, const uint8_t *bits, size_t n, void *tex,
+                               cudaStream_t s) {
+    if (dtype == CGDIR_F32)
+        k_make_texels_f32<<<flat_grid(n), 256, 0, s>>>((const float *)I0, bits, n, (float2 *)tex);
+    else
+        k_make_texels_16<<<flat_grid(n), 256, 0, s>>>((const unsigned short *)I0, bits, n, (uint32_t *)tex);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert_image(const void *in, int dtype, size_t n, float *out, cudaStream_t s) {
-    if (dtype == CGDIR_F16) {
-        k_convert<__half><<<flat_grid(n), 256, 0, s>>>((const __half *)in, n, out);
-    } else if (dtype == CGDIR_BF16) {
-        k_convert<__nv_bfloat16><<<flat_grid(n), 256, 0, s>>>((const __nv_bfloat16 *)in, n, out);
-    } else {
-        return cudaMemcpyAsync(out, in, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    }
+cudaError_t launch_convert_image(const void *in, int in_dtype, size_t n, void *out, int out_dtype,
+                                 cudaStream_t s) {
+    if (in_dtype == out_dtype)
+        return cudaMemcpyAsync(out, in, n * img_elem_size(in_dtype), cudaMemcpyDeviceToDevice, s);
+    const unsigned g = flat_grid(n);
+#define CGDIR_CONV(IN, OUT) k_convert<IN, OUT><<<g, 256, 0, s>>>((const IN *)in, n, (OUT *)out)
+    if (in_dtype == CGDIR_F32 && out_dtype == CGDIR_F16) CGDIR_CONV(float, __half);
+    else if (in_dtype == CGDIR_F32 && out_dtype == CGDIR_BF16) CGDIR_CONV(float, __nv_bfloat16);
+    else if (in_dtype == CGDIR_F16 && out_dtype == CGDIR_F32) CGDIR_CONV(__half, float);
+    else if (in_dtype == CGDIR_BF16 && out_dtype == CGDIR_F32) CGDIR_CONV(__nv_bfloat16, float);
+    else if (in_dtype == CGDIR_F16 && out_dtype == CGDIR_BF16) CGDIR_CONV(__half, __nv_bfloat16);
+    else if (in_dtype == CGDIR_BF16 && out_dtype == CGDIR_F16) CGDIR_CONV(__nv_bfloat16, __half);
+    else return cudaErrorInvalidValue;
+#undef CGDIR_CONV
     note_launch();
     return cudaGetLastError();
 }

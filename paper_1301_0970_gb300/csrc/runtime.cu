@@ -293,6 +293,7 @@ void cgdir_default_params(cgdir_params *p) {
     p->compose_mode = CGDIR_COMPOSE;
     p->init_dvf = nullptr;
     p->init_dvf_where = CGDIR_DEVICE;
+    p->storage_dtype = CGDIR_STORAGE_AUTO;
 }
 
 const char *cgdir_strerror(int s) {
@@ -424,9 +425,9 @@ static int force_impl(cgdir_ctx *ctx, const ForceArgs &a, double *stats_host) {
         // the TMA kernel gathers interleaved {I0, bits} texels
         const size_t N = (size_t)a.nx * a.ny * a.nz;
         void *tex = nullptr;
-        TRY(ws_get(ctx, "force_tex", N * sizeof(float2), &tex));
-        CK(launch_make_texels(a.I0, a.mbits, N, (float2 *)tex, ctx->stream));
-        b.mtex = (const float2 *)tex;
+        TRY(ws_get(ctx, "force_tex", N * tex_elem_size(a.img_dtype), &tex));
+        CK(launch_make_texels(a.I0, a.img_dtype, a.mbits, N, tex, ctx->stream));
+        b.mtex = tex;
     }
     if (stats_host) {
         TRY(ws_get(ctx, "partial", force_partial_count(a.nx, a.ny, a.nz, zc) * kPartialStride * sizeof(double), &part));
@@ -532,7 +533,7 @@ int cgdir_restrict_image(cgdir_ctx *ctx, const float *in, int nx, int ny, int nz
     if (!ctx) return CGDIR_EINVAL;
     if (!in || !out || !dims_ok(nx, ny, nz)) return fail(ctx, CGDIR_EINVAL, "restrict_image: bad arguments");
     DeviceGuard g(ctx->device);
-    CK(launch_restrict_image(in, nx, ny, nz, out, ctx->stream));
+    CK(launch_restrict_image(in, CGDIR_F32, nx, ny, nz, out, ctx->stream));
     return CGDIR_OK;
 }
 
@@ -571,8 +572,8 @@ int cgdir_uroi(cgdir_ctx *ctx, const uint8_t *sbits, int k, int nx, int ny, int 
     return CGDIR_OK;
 }
 
-int cgdir_auto_sign(cgdir_ctx *ctx, const float *T0, const uint8_t *sbits, int k, int nx, int ny,
-                    int nz, int8_t *sign_host) {
+static int auto_sign_impl(cgdir_ctx *ctx, const void *T0, int dtype, const uint8_t *sbits, int k, int nx,
+                          int ny, int nz, int8_t *sign_host) {
     if (!ctx) return CGDIR_EINVAL;
     if (!T0 || !dims_ok(nx, ny, nz) || k < 0 || k > kMaxMasks || (k > 0 && (!sbits || !sign_host)))
         return fail(ctx, CGDIR_EINVAL, "auto_sign: bad arguments");
@@ -584,7 +585,7 @@ int cgdir_auto_sign(cgdir_ctx *ctx, const float *T0, const uint8_t *sbits, int k
     TRY(ws_get(ctx, "sign_b", N, &tb));
     TRY(ws_get(ctx, "sign_part", sign_partial_rows(N) * 4 * sizeof(double), &part));
     TRY(ws_get(ctx, "sign_sums", kMaxMasks * 4 * sizeof(double), &sums));
-    CK(launch_sign_sums(T0, sbits, k, nx, ny, nz, (uint8_t *)ta, (uint8_t *)tb, (double *)part,
+    CK(launch_sign_sums(T0, dtype, sbits, k, nx, ny, nz, (uint8_t *)ta, (uint8_t *)tb, (double *)part,
                         (double *)sums, ctx->stream));
     double h[kMaxMasks * 4];
     CK(cudaMemcpyAsync(h, sums, k * 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -594,6 +595,11 @@ int cgdir_auto_sign(cgdir_ctx *ctx, const float *T0, const uint8_t *sbits, int k
         sign_host[j] = (cin == 0 || csh == 0) ? 1 : ((sin_ / cin >= ssh / csh) ? 1 : -1);
     }
     return CGDIR_OK;
+}
+
+int cgdir_auto_sign(cgdir_ctx *ctx, const float *T0, const uint8_t *sbits, int k, int nx, int ny,
+                    int nz, int8_t *sign_host) {
+    return auto_sign_impl(ctx, T0, CGDIR_F32, sbits, k, nx, ny, nz, sign_host);
 }
 
 int cgdir_rms_id(cgdir_ctx *ctx, const float *I0, const float *T0, const float *u,
@@ -607,7 +613,7 @@ int cgdir_rms_id(cgdir_ctx *ctx, const float *I0, const float *T0, const float *
     TRY(ws_get(ctx, "partial_m", metric_partial_count(nx, ny, nz) * kPartialStride * sizeof(double), &part));
     TRY(ws_get(ctx, "stats", 4 * sizeof(double), &st));
     int nb = 0;
-    CK(launch_metric(I0, T0, u, uroi, nx, ny, nz, (double *)part, nullptr, &nb, ctx->stream));
+    CK(launch_metric(I0, T0, CGDIR_F32, u, uroi, nx, ny, nz, (double *)part, nullptr, &nb, ctx->stream));
     LevelState ls{};
     CK(launch_finalize((double *)part, nb, ls, 0, 0, CGDIR_STOP_FIXED, 0.0, (double *)st, ctx->stream));
     double h[3];
@@ -673,6 +679,8 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
         return fail(ctx, CGDIR_EINVAL, "register: bad dvf_where");
     if (P->init_dvf && P->init_dvf_where != CGDIR_HOST && P->init_dvf_where != CGDIR_DEVICE)
         return fail(ctx, CGDIR_EINVAL, "register: bad init_dvf_where");
+    if (P->storage_dtype < CGDIR_STORAGE_AUTO || P->storage_dtype > CGDIR_BF16)
+        return fail(ctx, CGDIR_EINVAL, "register: bad storage_dtype");
     ForceArgs base{};
     {
         int8_t tmp_sign[kMaxMasks];
@@ -699,10 +707,13 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
 
     // ---- workspace
     void *p_img, *p_bits, *p_fields, *p_part, *p_state, *p_rowdist;
-    TRY(ws_get(ctx, "reg_img", 2 * Ntot * sizeof(float), &p_img));
+    // image storage type of the pyramid (float32, or 16-bit to halve the image bytes)
+    const int sdt = P->storage_dtype >= 0 ? P->storage_dtype : (S->dtype == M->dtype ? S->dtype : CGDIR_F32);
+    const size_t esz = img_elem_size(sdt), tsz = tex_elem_size(sdt);
+    TRY(ws_get(ctx, "reg_img", 2 * Ntot * esz, &p_img));
     TRY(ws_get(ctx, "reg_bits", 3 * Ntot, &p_bits));
     void *p_tex = nullptr;
-    TRY(ws_get(ctx, "reg_tex", Ntot * sizeof(float2), &p_tex));
+    TRY(ws_get(ctx, "reg_tex", Ntot * tsz, &p_tex));
     TRY(ws_get(ctx, "reg_fields", 4 * 3 * Nf * sizeof(float), &p_fields));
     size_t np = 0;
     for (int l = 0; l < L; ++l) {
@@ -716,17 +727,17 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     TRY(ws_get(ctx, "reg_state", state_bytes, &p_state));
     TRY(ws_get(ctx, "rowdist", uroi_scratch_bytes(Nf), &p_rowdist));
     void *p_stage = nullptr;
-    const bool need_stage = (S->where == CGDIR_HOST && S->dtype != CGDIR_F32) ||
-                            (M->where == CGDIR_HOST && M->dtype != CGDIR_F32) ||
+    const bool need_stage = (S->where == CGDIR_HOST && S->dtype != sdt) ||
+                            (M->where == CGDIR_HOST && M->dtype != sdt) ||
                             (k > 0 && (SM->where == CGDIR_HOST || MM->where == CGDIR_HOST));
-    if (need_stage) TRY(ws_get(ctx, "reg_stage", std::max(Nf * 2, (size_t)k * Nf), &p_stage));
+    if (need_stage) TRY(ws_get(ctx, "reg_stage", std::max(Nf * 4, (size_t)k * Nf), &p_stage));
     // (re-fetch: a later ws_get may have reallocated an earlier name only if
     //  the same name was requested twice, which it is not)
-    float *T[CGDIR_MAX_LEVELS], *I[CGDIR_MAX_LEVELS];
+    char *T[CGDIR_MAX_LEVELS], *I[CGDIR_MAX_LEVELS];          // images of type sdt
     uint8_t *SB[CGDIR_MAX_LEVELS], *MB[CGDIR_MAX_LEVELS], *UR[CGDIR_MAX_LEVELS];
     for (int l = 0; l < L; ++l) {
-        T[l] = (float *)p_img + off[l];
-        I[l] = (float *)p_img + Ntot + off[l];
+        T[l] = (char *)p_img + off[l] * esz;
+        I[l] = (char *)p_img + (Ntot + off[l]) * esz;
         SB[l] = (uint8_t *)p_bits + off[l];
         MB[l] = (uint8_t *)p_bits + Ntot + off[l];
         UR[l] = (uint8_t *)p_bits + 2 * Ntot + off[l];
@@ -740,16 +751,16 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     unsigned *done = (unsigned *)(meta + 4 * CGDIR_MAX_LEVELS);   // per-level completion counters
 
     // ---- ingest images (finest level)
-    auto ingest = [&](const cgdir_volume *v, float *dst) -> int {
+    auto ingest = [&](const cgdir_volume *v, void *dst) -> int {
         const size_t bytes = Nf * elem_size(v->dtype);
-        if (v->dtype == CGDIR_F32) {
+        if (v->dtype == sdt) {
             CK(cudaMemcpyAsync(dst, v->data, bytes,
                                v->where == CGDIR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
         } else if (v->where == CGDIR_HOST) {
             CK(cudaMemcpyAsync(p_stage, v->data, bytes, cudaMemcpyHostToDevice, s));
-            CK(launch_convert_image(p_stage, v->dtype, Nf, dst, s));
+            CK(launch_convert_image(p_stage, v->dtype, Nf, dst, sdt, s));
         } else {
-            CK(launch_convert_image(v->data, v->dtype, Nf, dst, s));
+            CK(launch_convert_image(v->data, v->dtype, Nf, dst, sdt, s));
         }
         return CGDIR_OK;
     };
@@ -783,7 +794,7 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     }
     if (need_auto) {
         int8_t autos[kMaxMasks];
-        TRY(cgdir_auto_sign(ctx, T[L - 1], SB[L - 1], k, nx, ny, nz, autos));
+        TRY(auto_sign_impl(ctx, T[L - 1], sdt, SB[L - 1], k, nx, ny, nz, autos));
         for (int j = 0; j < k; ++j)
             if (sign[j] == 0) sign[j] = autos[j];
     }
@@ -802,15 +813,15 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
         for (int l = L - 2; l >= 0; --l) {
             const int *d = dims[l + 1];
             ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
-            CK(launch_restrict_image(T[l + 1], d[0], d[1], d[2], T[l], s));
-            CK(launch_restrict_image(I[l + 1], d[0], d[1], d[2], I[l], s));
+            CK(launch_restrict_image(T[l + 1], sdt, d[0], d[1], d[2], T[l], s));
+            CK(launch_restrict_image(I[l + 1], sdt, d[0], d[1], d[2], I[l], s));
             CK(launch_restrict_bits(SB[l + 1], d[0], d[1], d[2], SB[l], s));
             CK(launch_restrict_bits(MB[l + 1], d[0], d[1], d[2], MB[l], s));
         }
         for (int l = 0; l < L; ++l) {
             if (((P->contour_level_mask >> l) & 1u) && k > 0 && !ctx->plain_kernels) {
                 ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
-                CK(launch_make_texels(I[l], MB[l], Nl[l], (float2 *)p_tex + off[l], s));
+                CK(launch_make_texels(I[l], sdt, MB[l], Nl[l], (char *)p_tex + off[l] * tsz, s));
             }
             const double f = (double)(1 << (L - 1 - l));
             const double sp[3] = {P->spacing_mm[0] * f, P->spacing_mm[1] * f, P->spacing_mm[2] * f};
@@ -838,8 +849,8 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
             st.stop_flag = flags + l;
             st.hist_cap = hcap;
             ForceArgs a = base;
-            a.I0 = I[l]; a.T0 = T[l]; a.mbits = MB[l]; a.sbits = SB[l]; a.uroi = UR[l];
-            a.mtex = ctx->plain_kernels ? nullptr : (const float2 *)p_tex + off[l];
+            a.I0 = I[l]; a.T0 = T[l]; a.img_dtype = sdt; a.mbits = MB[l]; a.sbits = SB[l]; a.uroi = UR[l];
+            a.mtex = ctx->plain_kernels ? nullptr : (const void *)((char *)p_tex + off[l] * tsz);
             a.u = ucur; a.du = du; a.warped = nullptr; a.partial = partial; a.stop_flag = flags + l;
             a.nx = lx; a.ny = ly; a.nz = lz;
             a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
@@ -866,7 +877,7 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
             FinishArgs fm = a.fin;
             fm.n = cap;
             { ProfScope ps(pl, m, s, CGDIR_K_METRIC, l);
-              CK(launch_metric(I[l], T[l], ucur, UR[l], lx, ly, lz, partial, flags + l, &nb, s, &fm)); }
+              CK(launch_metric(I[l], T[l], sdt, ucur, UR[l], lx, ly, lz, partial, flags + l, &nb, s, &fm)); }
         }
         return CGDIR_OK;
     };
@@ -875,10 +886,10 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     if (ctx->use_graphs) {
         char key[1024];
         int len = std::snprintf(key, sizeof key, "%d %d %d|%d|%d %d %.9g %.9g %d %u %d %.17g %.17g %.17g %.17g "
-                                "%.17g %.9g %d %d %llu %u|", nx, ny, nz, L, k, first, P->sigma_fluid, P->sigma_diff,
+                                "%.17g %.9g %d %d %llu %u %d|", nx, ny, nz, L, k, first, P->sigma_fluid, P->sigma_diff,
                                 P->compose_mode, P->contour_level_mask, P->stop_mode, P->eps, P->spacing_mm[0],
                                 P->spacing_mm[1], P->spacing_mm[2], P->margin_mm, P->intensity_offset,
-                                (int)ctx->plain_kernels, maxcap, ctx->ws_generation, ctx->prof_mask);
+                                (int)ctx->plain_kernels, maxcap, ctx->ws_generation, ctx->prof_mask, sdt);
         std::string skey(key, (size_t)len);
         for (int l = 0; l < L; ++l) skey += std::to_string(P->iters[l]) + ",";
         for (int j = 0; j < k; ++j) {

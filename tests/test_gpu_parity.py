@@ -447,3 +447,44 @@ def test_profile_reports_every_kernel_class():
     force = {p["level"]: p["launches"] for p in prof if p["kernel"] == "force"}
     assert force == {0: 3, 1: 2}
     assert all(p["total_ms"] > 0 for p in prof)
+
+
+# ------------------------------------------------- 16-bit image storage (FP32 math)
+@pytest.mark.parametrize("storage", [cg.CGDIR_F16, cg.CGDIR_BF16])
+@pytest.mark.parametrize("kernels", ["tma", "plain"])
+@pytest.mark.parametrize("shape", [(20, 48, 48), (13, 30, 37)])
+def test_half_storage_registration_within_a_tenth_of_a_voxel(storage, kernels, shape):
+    """Images stored in FP16 / BF16, all arithmetic FP32: with FP16 storage the
+    final DVF stays within 0.1 voxel RMS of the FP64 oracle run on the FP32
+    images.  BF16 keeps 8 mantissa bits, a 4 HU step at -1000 HU next to
+    15-20 HU contrasts, so its bound is 0.25 voxel."""
+    c = phantom.make_case("phantom64", shape=shape)
+    ctx = make_context(kernels)
+    try:
+        dvf, st = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                               [dev(m) for m in c.moving_masks], levels=2, iters=[30, 20], lam=c.lam,
+                               sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED, storage_dtype=storage)
+        got = host(dvf)
+    finally:
+        ctx.close()
+    ref, _ = oracle.register(c.static, c.moving, c.static_masks, c.moving_masks, levels=2,
+                             iters=[30, 20], lam=c.lam, sign=c.signs)
+    assert dvf_rms(got, ref) <= (0.1 if storage == cg.CGDIR_F16 else 0.25)
+    assert [s["iters_run"] for s in st] == [30, 20]
+
+
+@pytest.mark.parametrize("dtype,code", [(torch.float16, cg.CGDIR_F16), (torch.bfloat16, cg.CGDIR_BF16)])
+def test_half_inputs_equal_on_device_conversion(dtype, code):
+    c = phantom.make_case("phantom64", shape=(16, 40, 48))
+    kw = dict(levels=2, iters=[5, 5], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as ctx:
+        a, _ = ctx.register(dev(c.static).to(dtype), dev(c.moving).to(dtype),
+                            [dev(m) for m in c.static_masks], [dev(m) for m in c.moving_masks], **kw)
+        a = a.cpu()
+        b, _ = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                            [dev(m) for m in c.moving_masks], storage_dtype=code, **kw)
+        b = b.cpu()
+        f, _ = ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
+                            [dev(m) for m in c.moving_masks], storage_dtype=cg.CGDIR_F32, **kw)
+    assert torch.equal(a, b)
+    assert float((a - f.cpu()).abs().max()) > 0       # the storage type is really in effect
