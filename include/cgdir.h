@@ -213,6 +213,57 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *static_img, const cgdir_v
                    const cgdir_params *params, float *dvf_out, int dvf_where,
                    cgdir_level_stats *stats_out);
 
+/* ---- many registrations at once (not in the paper: an execution mode) --- */
+
+/* Register `count` (1..1024) independent cases in one call.  Arrays of
+   `count` entries: statics, movings, params (each case its own parameters,
+   shapes and mask counts); static_masks / moving_masks may be NULL (no masks
+   for any case); dvf_outs[i] receives case i as cgdir_register would write
+   it (dvf_where applies to all).  The device parts of all cases are one
+   CUDA graph with a concurrent branch per case, so small cases share the GPU
+   instead of running one after another.  stats_out: host array holding
+   params[0].levels + ... + params[count-1].levels entries, case after case
+   (may be NULL).  Results are bitwise those of cgdir_register per case.
+   Blocking.  Errors as cgdir_register; EBUSY if a slot it needs is serving
+   a submitted request. */
+int cgdir_register_batch(cgdir_ctx *ctx, int count, const cgdir_volume *statics,
+                         const cgdir_volume *movings, const cgdir_masks *static_masks,
+                         const cgdir_masks *moving_masks, const cgdir_params *params,
+                         float *const *dvf_outs, int dvf_where, cgdir_level_stats *stats_out);
+
+/* ---- serving: asynchronous requests (not in the paper) ------------------
+ * cgdir_submit queues one registration and returns at once with a ticket;
+ * each request in flight has its own device buffers and CUDA stream (a
+ * "slot"), so requests that arrive while others run overlap on the device.
+ * At most cgdir_set_max_inflight(n) requests (default 8) are in flight; a
+ * submit beyond that, or one whose new buffers would exceed the context's
+ * mem_budget_bytes, returns EBUSY and queues nothing (retry after a
+ * release).  Inputs must stay valid until the request completes; dvf_out
+ * is written by the time cgdir_wait / cgdir_poll return CGDIR_OK (a
+ * pageable host dvf_out is copied by that call, pinned or device memory by
+ * the request's stream).  A result is the same, bit for bit, whether the
+ * request ran alone or among others.  The context's stream is not used. */
+int cgdir_set_max_inflight(cgdir_ctx *ctx, int n);            /* 1..256 */
+int cgdir_submit(cgdir_ctx *ctx, const cgdir_volume *static_img, const cgdir_volume *moving_img,
+                 const cgdir_masks *static_masks, const cgdir_masks *moving_masks,
+                 const cgdir_params *params, float *dvf_out, int dvf_where, long long *ticket);
+/* CGDIR_OK once the request has completed (dvf_out written), EBUSY while it
+   runs, EINVAL for an unknown or released ticket, ETIMEDOUT / ECUDA if a
+   kernel of the request failed. */
+int cgdir_poll(cgdir_ctx *ctx, long long ticket);
+/* Poll until completion or until timeout_ms (< 0: no limit) has passed:
+   then ETIMEDOUT, and the request is still in flight. */
+int cgdir_wait(cgdir_ctx *ctx, long long ticket, int timeout_ms);
+/* Free the request's slot and fill stats_out (`levels` entries, may be
+   NULL; its rms_id arrays stay valid until the slot is reused).  EBUSY if
+   the request has not completed. */
+int cgdir_release(cgdir_ctx *ctx, long long ticket, cgdir_level_stats *stats_out);
+/* Stop a request early: its remaining kernels return at once (a request
+   whose device part has not begun yet runs to the end).  Blocks until the
+   slot is idle, then frees it; dvf_out then holds an unspecified partial
+   result (a pageable host dvf_out is left untouched). */
+int cgdir_cancel(cgdir_ctx *ctx, long long ticket);
+
 /* ---- primitives of the iteration (device pointers, ctx's stream) -------- *
  * These expose each step of the hot path on caller-owned device buffers, so
  * that a caller can run its own loop and so that each step can be checked on

@@ -80,6 +80,17 @@ _SIGNATURES = {
     "cgdir_register": (c_int, [c_void_p, POINTER(cgdir_volume), POINTER(cgdir_volume),
                                POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
                                c_void_p, c_int, POINTER(cgdir_level_stats)]),
+    "cgdir_register_batch": (c_int, [c_void_p, c_int, POINTER(cgdir_volume), POINTER(cgdir_volume),
+                                     POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
+                                     POINTER(c_void_p), c_int, POINTER(cgdir_level_stats)]),
+    "cgdir_set_max_inflight": (c_int, [c_void_p, c_int]),
+    "cgdir_submit": (c_int, [c_void_p, POINTER(cgdir_volume), POINTER(cgdir_volume),
+                             POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
+                             c_void_p, c_int, POINTER(c_longlong)]),
+    "cgdir_poll": (c_int, [c_void_p, c_longlong]),
+    "cgdir_wait": (c_int, [c_void_p, c_longlong, c_int]),
+    "cgdir_release": (c_int, [c_void_p, c_longlong, POINTER(cgdir_level_stats)]),
+    "cgdir_cancel": (c_int, [c_void_p, c_longlong]),
     "cgdir_pack_masks": (c_int, [c_void_p, POINTER(c_void_p), c_int, c_size_t, c_void_p]),
     "cgdir_warp": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     "cgdir_force": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
@@ -179,6 +190,79 @@ def _dtype_code(t) -> int:
     return {torch.float32: CGDIR_F32, torch.float16: CGDIR_F16, torch.bfloat16: CGDIR_BF16}[t.dtype]
 
 
+def _stats_list(stats, first: int, n: int):
+    out = []
+    for i in range(first, first + n):
+        s = stats[i]
+        hist = [s.rms_id[j] for j in range(s.hist_len)] if s.hist_len else []
+        out.append({"level": s.level, "shape": (s.nz, s.ny, s.nx), "iters_run": s.iters_run,
+                    "stop_reason": s.stop_reason, "rms_id": hist})
+    return out
+
+
+class Request:
+    """The C arguments of one registration (Algorithm A), kept alive while it
+    runs.  Images are [nz,ny,nx] tensors (CUDA or CPU; float32/16/bf16),
+    masks k-long lists (or [k,nz,ny,nx] tensors) of uint8 tensors."""
+
+    def __init__(self, static, moving, static_masks=None, moving_masks=None, *,
+                 levels: int = 2, iters: Sequence[int] = (100, 50), sigma_fluid: float = 1.0,
+                 sigma_diff: float = 1.0, lam: Optional[Sequence[float]] = None,
+                 sign: Optional[Sequence[int]] = None, contour_level_mask: Optional[int] = None,
+                 stop_mode: int = CGDIR_STOP_WINDOW10, eps: float = 1e-4,
+                 spacing_mm=(1.97, 1.97, 2.5), margin_mm: float = 10.0,
+                 intensity_offset: float = 1000.0, compose_mode: int = CGDIR_COMPOSE,
+                 init_dvf=None, dvf_out=None, storage_dtype: int = CGDIR_STORAGE_AUTO):
+        torch = _torch()
+        nx, ny, nz = _dims(static)
+        sm = list(static_masks) if static_masks is not None else []
+        mm = list(moving_masks) if moving_masks is not None else []
+        k = len(sm)
+        for m in sm + mm:
+            if m.dtype != torch.uint8 or not m.is_contiguous():
+                raise ValueError("masks must be contiguous uint8 tensors")
+        self.levels = int(levels)
+        self.ticket = -1
+        self.S = cgdir_volume(nx, ny, nz, _dtype_code(static),
+                              CGDIR_DEVICE if static.is_cuda else CGDIR_HOST, c_void_p(_ptr(static)))
+        self.M = cgdir_volume(*_dims(moving), _dtype_code(moving),
+                              CGDIR_DEVICE if moving.is_cuda else CGDIR_HOST, c_void_p(_ptr(moving)))
+        sptr = (c_void_p * max(k, 1))(*[c_void_p(_ptr(m)) for m in sm])
+        mptr = (c_void_p * max(len(mm), 1))(*[c_void_p(_ptr(m)) for m in mm])
+        self.SM = cgdir_masks(nx, ny, nz, CGDIR_DEVICE if (k and sm[0].is_cuda) else CGDIR_HOST,
+                              ctypes.cast(sptr, POINTER(c_void_p)), k)
+        self.MM = cgdir_masks(nx, ny, nz, CGDIR_DEVICE if (mm and mm[0].is_cuda) else CGDIR_HOST,
+                              ctypes.cast(mptr, POINTER(c_void_p)), len(mm))
+        it = (c_int * max(self.levels, 1))(*[int(v) for v in iters])
+        p = cgdir_params()
+        load().cgdir_default_params(ctypes.byref(p))
+        p.levels = self.levels
+        p.iters = ctypes.cast(it, POINTER(c_int))
+        p.sigma_fluid, p.sigma_diff = sigma_fluid, sigma_diff
+        lam_a = (c_float * max(k, 1))(*([float(v) for v in lam] if lam is not None else [1e-3] * k))
+        p.lambda_ = ctypes.cast(lam_a, POINTER(c_float))
+        sg_a = (c_int8 * max(k, 1))(*([int(v) for v in sign] if sign is not None else [0] * k))
+        p.sign = ctypes.cast(sg_a, POINTER(c_int8))
+        p.contour_level_mask = (1 << (self.levels - 1)) if contour_level_mask is None else contour_level_mask
+        p.stop_mode, p.eps = stop_mode, eps
+        p.spacing_mm = (c_double * 3)(*spacing_mm)
+        p.margin_mm = margin_mm
+        p.intensity_offset = intensity_offset
+        p.compose_mode = compose_mode
+        p.storage_dtype = storage_dtype
+        if init_dvf is not None:
+            p.init_dvf = c_void_p(_ptr(init_dvf))
+            p.init_dvf_where = CGDIR_DEVICE if init_dvf.is_cuda else CGDIR_HOST
+        if dvf_out is None:
+            dvf_out = torch.empty((3, nz, ny, nx), dtype=torch.float32,
+                                  device=static.device if static.is_cuda else "cpu")
+        self.p = p
+        self.dvf = dvf_out
+        self.dvf_where = CGDIR_DEVICE if dvf_out.is_cuda else CGDIR_HOST
+        # everything the C structures point into
+        self._keep = (static, moving, sm, mm, sptr, mptr, it, lam_a, sg_a, init_dvf)
+
+
 class Context:
     """One device + one stream (default: torch's current stream on `device`)."""
 
@@ -248,69 +332,86 @@ class Context:
                 for i in range(n)]
 
     # ---- whole registration ------------------------------------------------
-    def register(self, static, moving, static_masks=None, moving_masks=None, *,
-                 levels: int = 2, iters: Sequence[int] = (100, 50), sigma_fluid: float = 1.0,
-                 sigma_diff: float = 1.0, lam: Optional[Sequence[float]] = None,
-                 sign: Optional[Sequence[int]] = None, contour_level_mask: Optional[int] = None,
-                 stop_mode: int = CGDIR_STOP_WINDOW10, eps: float = 1e-4,
-                 spacing_mm=(1.97, 1.97, 2.5), margin_mm: float = 10.0,
-                 intensity_offset: float = 1000.0, compose_mode: int = CGDIR_COMPOSE,
-                 init_dvf=None, dvf_out=None, storage_dtype: int = CGDIR_STORAGE_AUTO):
+    def register(self, static, moving, static_masks=None, moving_masks=None, **kw):
         """Algorithm A on (static, moving) [nz,ny,nx] tensors (CUDA or CPU;
         float32/16/bf16) with k-long lists (or [k,nz,ny,nx] tensors) of uint8
-        masks.  Returns (dvf [3,nz,ny,nx] float32, stats list coarse->fine)."""
-        torch = _torch()
-        nx, ny, nz = _dims(static)
-        sm = list(static_masks) if static_masks is not None else []
-        mm = list(moving_masks) if moving_masks is not None else []
-        k = len(sm)
-        S = cgdir_volume(nx, ny, nz, _dtype_code(static), CGDIR_DEVICE if static.is_cuda else CGDIR_HOST,
-                         c_void_p(_ptr(static)))
-        M = cgdir_volume(*_dims(moving), _dtype_code(moving),
-                         CGDIR_DEVICE if moving.is_cuda else CGDIR_HOST, c_void_p(_ptr(moving)))
-        for m in sm + mm:
-            if m.dtype != torch.uint8 or not m.is_contiguous():
-                raise ValueError("masks must be contiguous uint8 tensors")
-        sptr = (c_void_p * max(k, 1))(*[c_void_p(_ptr(m)) for m in sm])
-        mptr = (c_void_p * max(len(mm), 1))(*[c_void_p(_ptr(m)) for m in mm])
-        SMk = cgdir_masks(nx, ny, nz, CGDIR_DEVICE if (k and sm[0].is_cuda) else CGDIR_HOST,
-                          ctypes.cast(sptr, POINTER(c_void_p)), k)
-        MMk = cgdir_masks(nx, ny, nz, CGDIR_DEVICE if (mm and mm[0].is_cuda) else CGDIR_HOST,
-                          ctypes.cast(mptr, POINTER(c_void_p)), len(mm))
-        it = (c_int * levels)(*[int(v) for v in iters])
-        p = cgdir_params()
-        load().cgdir_default_params(ctypes.byref(p))
-        p.levels = levels
-        p.iters = ctypes.cast(it, POINTER(c_int))
-        p.sigma_fluid, p.sigma_diff = sigma_fluid, sigma_diff
-        lam_a = (c_float * max(k, 1))(*([float(v) for v in lam] if lam is not None else [1e-3] * k))
-        p.lambda_ = ctypes.cast(lam_a, POINTER(c_float))
-        sg_a = (c_int8 * max(k, 1))(*([int(v) for v in sign] if sign is not None else [0] * k))
-        p.sign = ctypes.cast(sg_a, POINTER(c_int8))
-        p.contour_level_mask = (1 << (levels - 1)) if contour_level_mask is None else contour_level_mask
-        p.stop_mode, p.eps = stop_mode, eps
-        p.spacing_mm = (c_double * 3)(*spacing_mm)
-        p.margin_mm = margin_mm
-        p.intensity_offset = intensity_offset
-        p.compose_mode = compose_mode
-        p.storage_dtype = storage_dtype
-        if init_dvf is not None:
-            p.init_dvf = c_void_p(_ptr(init_dvf))
-            p.init_dvf_where = CGDIR_DEVICE if init_dvf.is_cuda else CGDIR_HOST
-        if dvf_out is None:
-            dvf_out = torch.empty((3, nz, ny, nx), dtype=torch.float32,
-                                  device=static.device if static.is_cuda else "cpu")
-        stats = (cgdir_level_stats * levels)()
-        st = load().cgdir_register(self._h, ctypes.byref(S), ctypes.byref(M), ctypes.byref(SMk),
-                                   ctypes.byref(MMk), ctypes.byref(p), c_void_p(_ptr(dvf_out)),
-                                   CGDIR_DEVICE if dvf_out.is_cuda else CGDIR_HOST, stats)
+        masks.  Keyword arguments: see `Request`.  Returns (dvf [3,nz,ny,nx]
+        float32, stats list coarse->fine)."""
+        r = Request(static, moving, static_masks, moving_masks, **kw)
+        stats = (cgdir_level_stats * r.levels)()
+        st = load().cgdir_register(self._h, ctypes.byref(r.S), ctypes.byref(r.M), ctypes.byref(r.SM),
+                                   ctypes.byref(r.MM), ctypes.byref(r.p), c_void_p(_ptr(r.dvf)),
+                                   r.dvf_where, stats)
         self._check(st, "cgdir_register")
-        out = []
-        for s in stats:
-            hist = [s.rms_id[i] for i in range(s.hist_len)] if s.hist_len else []
-            out.append({"level": s.level, "shape": (s.nz, s.ny, s.nx), "iters_run": s.iters_run,
-                        "stop_reason": s.stop_reason, "rms_id": hist})
-        return dvf_out, out
+        return r.dvf, _stats_list(stats, 0, r.levels)
+
+    def register_batch(self, cases):
+        """Register every case of `cases` (dicts with static, moving,
+        static_masks, moving_masks and any `Request` keyword) in one call: one
+        CUDA graph with a concurrent branch per case.  All dvf outputs must be
+        on the same side (all CUDA or all host).  Returns a list of
+        (dvf, stats) per case."""
+        reqs = [Request(c["static"], c["moving"], c.get("static_masks"), c.get("moving_masks"),
+                        **{k: v for k, v in c.items()
+                           if k not in ("static", "moving", "static_masks", "moving_masks")})
+                for c in cases]
+        n = len(reqs)
+        if n == 0:
+            return []
+        where = {r.dvf_where for r in reqs}
+        if len(where) != 1:
+            raise ValueError("register_batch: dvf outputs must all be on the device or all on the host")
+        Sa = (cgdir_volume * n)(*[r.S for r in reqs])
+        Ma = (cgdir_volume * n)(*[r.M for r in reqs])
+        SMa = (cgdir_masks * n)(*[r.SM for r in reqs])
+        MMa = (cgdir_masks * n)(*[r.MM for r in reqs])
+        Pa = (cgdir_params * n)(*[r.p for r in reqs])
+        outs = (c_void_p * n)(*[c_void_p(_ptr(r.dvf)) for r in reqs])
+        total = sum(r.levels for r in reqs)
+        stats = (cgdir_level_stats * total)()
+        st = load().cgdir_register_batch(self._h, n, Sa, Ma, SMa, MMa, Pa, outs, where.pop(), stats)
+        self._check(st, "cgdir_register_batch")
+        res, o = [], 0
+        for r in reqs:
+            res.append((r.dvf, _stats_list(stats, o, r.levels)))
+            o += r.levels
+        return res
+
+    # ---- serving ---------------------------------------------------------------
+    def set_max_inflight(self, n: int):
+        self._check(load().cgdir_set_max_inflight(self._h, int(n)), "cgdir_set_max_inflight")
+
+    def submit(self, static, moving, static_masks=None, moving_masks=None, **kw) -> "Request":
+        """Queue one registration; returns its `Request` at once.  Raises
+        CgdirError with code CGDIR_EBUSY when no slot or budget is free."""
+        r = Request(static, moving, static_masks, moving_masks, **kw)
+        t = c_longlong()
+        st = load().cgdir_submit(self._h, ctypes.byref(r.S), ctypes.byref(r.M), ctypes.byref(r.SM),
+                                 ctypes.byref(r.MM), ctypes.byref(r.p), c_void_p(_ptr(r.dvf)),
+                                 r.dvf_where, ctypes.byref(t))
+        self._check(st, "cgdir_submit")
+        r.ticket = int(t.value)
+        return r
+
+    def poll(self, req: "Request") -> bool:
+        st = load().cgdir_poll(self._h, req.ticket)
+        if st == CGDIR_EBUSY:
+            return False
+        self._check(st, "cgdir_poll")
+        return True
+
+    def wait(self, req: "Request", timeout_ms: int = -1):
+        """Wait for `req`, free its slot and return (dvf, stats).  On timeout
+        raises CgdirError(CGDIR_ETIMEDOUT) and the request stays in flight."""
+        self._check(load().cgdir_wait(self._h, req.ticket, int(timeout_ms)), "cgdir_wait")
+        stats = (cgdir_level_stats * req.levels)()
+        self._check(load().cgdir_release(self._h, req.ticket, stats), "cgdir_release")
+        req.ticket = -1
+        return req.dvf, _stats_list(stats, 0, req.levels)
+
+    def cancel(self, req: "Request"):
+        self._check(load().cgdir_cancel(self._h, req.ticket), "cgdir_cancel")
+        req.ticket = -1
 
     # ---- primitives ------------------------------------------------------------
     def pack_masks(self, masks, out=None):

@@ -30,7 +30,7 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.hpp")) + \
         [os.path.join(ROOT, "include", "cgdir.h"), os.path.abspath(__file__)]
 
 

@@ -1,77 +1,16 @@
-// Runtime and C ABI of the CG-DIR library (include/cgdir.h): contexts,
-// device workspace, the image pyramid, and Algorithm A (Sec. 2.2) driven as
-// a fixed sequence of kernel launches on the context's stream.
-//
-// The per-iteration sequence at a level (u stays in one buffer):
-//   force(u -> du) ; finalize(delta^n, stop test) ;
-//   smooth+compose(du, u -> du2) ; smooth(du2 -> u)
-// and after the level's cap a metric pass gives delta^cap.  The stopping
-// decision is taken on the device (finalize sets the level's stop flag and
-// every later kernel of the level returns at once), so a level never waits
-// for the host.
-#include "cgdir_internal.cuh"
+// Contexts, device workspace and the per-step primitives of the C ABI
+// (include/cgdir.h).  The registration pipeline (Algorithm A, Sec. 2.2:
+// single, batched and served) is in register.cu.
+#include "runtime_internal.hpp"
 
 #include <algorithm>
-#include <atomic>
-#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <map>
 #include <mutex>
-#include <string>
-#include <vector>
 
 using namespace cgdir;
-
-struct WsBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-};
-
-struct ProfPending {
-    int cls, level;
-    cudaEvent_t a, b;
-};
-
-// Event pairs recorded around profiled launches, with the events they use.
-struct ProfList {
-    std::vector<ProfPending> recs;
-    std::vector<cudaEvent_t> pool;
-    void release() {
-        for (cudaEvent_t e : pool) cudaEventDestroy(e);
-        pool.clear();
-        recs.clear();
-    }
-};
-
-// One instantiated CUDA graph of the device part of a registration.
-struct GraphEntry {
-    cudaGraphExec_t exec = nullptr;
-    ProfList prof;
-    unsigned long long launches = 0;
-};
-
-struct cgdir_ctx {
-    unsigned prof_mask = 0;
-    ProfList eager;
-    std::map<std::pair<int, int>, std::pair<long long, double>> prof;
-    bool use_graphs = true;
-    unsigned long long ws_generation = 0;
-    std::map<std::string, GraphEntry> graphs;
-    int device = 0;
-    bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
-    int *err_word = nullptr;      // device word set by a kernel whose bounded wait ran out
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
-    bool own_stream = false;
-    size_t budget = 0;
-    size_t in_use = 0;
-    std::string err;
-    std::map<std::string, WsBuf> ws;
-    std::vector<double> h_hist;
-    std::vector<int> h_meta;
-};
+using namespace cgdir::rt;
 
 namespace cgdir {
 static std::atomic<unsigned long long> g_launches{0};
@@ -112,34 +51,43 @@ cudaError_t ensure_smem(const void *func, size_t bytes) {
     if (e == cudaSuccess) have = bytes;
     return e;
 }
-}  // namespace cgdir
 
-namespace {
+namespace rt {
 
-// Event pair around one launch of class `cls` when that class is profiled.
-struct ProfScope {
-    ProfList *list = nullptr;
-    cudaStream_t stream;
-    int idx = -1;
-    ProfScope(ProfList *l, unsigned mask, cudaStream_t s, int cls, int level) : stream(s) {
-        if (!(mask & (1u << cls))) return;
-        const size_t need = 2 * (l->recs.size() + 1);
-        while (l->pool.size() < need) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
-            l->pool.push_back(e);
-        }
-        ProfPending p{cls, level, l->pool[need - 2], l->pool[need - 1]};
-        // External: inside a stream capture this becomes an event-record node
-        cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal);
-        l->recs.push_back(p);
-        list = l;
-        idx = (int)l->recs.size() - 1;
+unsigned long long launches_now() { return g_launches.load(); }
+void launches_sub(unsigned long long n) { g_launches.fetch_sub(n); }
+
+void ProfList::release() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    recs.clear();
+}
+
+size_t WsSet::bytes() const {
+    size_t b = 0;
+    for (const auto &kv : bufs) b += kv.second.cap;
+    return b;
+}
+
+ProfScope::ProfScope(ProfList *l, unsigned mask, cudaStream_t s, int cls, int level) : stream(s) {
+    if (!(mask & (1u << cls))) return;
+    const size_t need = 2 * (l->recs.size() + 1);
+    while (l->pool.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+        l->pool.push_back(e);
     }
-    ~ProfScope() {
-        if (idx >= 0) cudaEventRecordWithFlags(list->recs[idx].b, stream, cudaEventRecordExternal);
-    }
-};
+    ProfPending p{cls, level, l->pool[need - 2], l->pool[need - 1]};
+    // External: inside a stream capture this becomes an event-record node
+    cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal);
+    l->recs.push_back(p);
+    list = l;
+    idx = (int)l->recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (idx >= 0) cudaEventRecordWithFlags(list->recs[idx].b, stream, cudaEventRecordExternal);
+}
 
 // After the stream has drained: fold the recorded pairs into the totals.
 void prof_collect(cgdir_ctx *ctx, const ProfList &l) {
@@ -155,50 +103,32 @@ void prof_collect(cgdir_ctx *ctx, const ProfList &l) {
     }
 }
 
-void drop_graphs(cgdir_ctx *ctx) {
-    for (auto &kv : ctx->graphs) {
+void drop_graphs(WsSet &ws) {
+    for (auto &kv : ws.graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         kv.second.prof.release();
     }
-    ctx->graphs.clear();
+    ws.graphs.clear();
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int d) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != d) cudaSetDevice(d);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+DeviceGuard::DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) cudaSetDevice(d);
+}
+DeviceGuard::~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
 
 int fail(cgdir_ctx *c, int code, const std::string &msg) {
     if (c) c->err = msg;
     return code;
 }
 
-#define CK(expr)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (expr);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(ctx, CGDIR_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-#define TRY(expr)                 \
-    do {                          \
-        int r_ = (expr);          \
-        if (r_ != CGDIR_OK) return r_; \
-    } while (0)
-
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Grow-only named device buffers.  Growing frees the old buffer after the
-// stream has drained, so callers must re-fetch pointers after any ws_get.
-int ws_get(cgdir_ctx *ctx, const char *name, size_t bytes, void **out) {
-    WsBuf &b = ctx->ws[name];
+int ws_get(cgdir_ctx *ctx, WsSet &ws, cudaStream_t sync, const char *name, size_t bytes, void **out) {
+    WsBuf &b = ws.bufs[name];
     if (bytes == 0) bytes = 256;
     if (b.p && b.cap >= bytes) { *out = b.p; return CGDIR_OK; }
     const size_t cap = round_up(bytes, (size_t)1 << 21);
@@ -206,13 +136,13 @@ int ws_get(cgdir_ctx *ctx, const char *name, size_t bytes, void **out) {
     if (ctx->budget && after > ctx->budget)
         return fail(ctx, CGDIR_ENOMEM, std::string("device budget exceeded growing '") + name + "'");
     if (b.p) {
-        cudaStreamSynchronize(ctx->stream);
-        drop_graphs(ctx);              // cached graphs hold the old address
+        cudaStreamSynchronize(sync);
+        drop_graphs(ws);               // cached graphs hold the old address
         cudaFree(b.p);
         ctx->in_use -= b.cap;
         b = WsBuf{};
     }
-    ++ctx->ws_generation;
+    ++ws.generation;
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, cap);
     if (e != cudaSuccess) {
@@ -224,6 +154,16 @@ int ws_get(cgdir_ctx *ctx, const char *name, size_t bytes, void **out) {
     ctx->in_use += cap;
     *out = p;
     return CGDIR_OK;
+}
+
+void ws_release(cgdir_ctx *ctx, WsSet &ws) {
+    drop_graphs(ws);
+    for (auto &kv : ws.bufs)
+        if (kv.second.p) {
+            cudaFree(kv.second.p);
+            ctx->in_use -= kv.second.cap;
+        }
+    ws.bufs.clear();
 }
 
 bool dims_ok(int nx, int ny, int nz) { return nx >= 1 && ny >= 1 && nz >= 1; }
@@ -267,7 +207,8 @@ int fill_force_args(cgdir_ctx *ctx, ForceArgs &a, int k, const float *lambda, co
     return CGDIR_OK;
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace cgdir
 
 // ======================================================================
 extern "C" {
@@ -387,10 +328,20 @@ void cgdir_destroy(cgdir_ctx *ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    for (auto &kv : ctx->ws)
-        if (kv.second.p) cudaFree(kv.second.p);
-    drop_graphs(ctx);
+    for (auto &sl : ctx->slots) {
+        if (sl->stream) cudaStreamSynchronize(sl->stream);
+        ws_release(ctx, sl->ws);
+        if (sl->own_stream && sl->stream) cudaStreamDestroy(sl->stream);
+        if (sl->done) cudaEventDestroy(sl->done);
+        if (sl->ready) cudaEventDestroy(sl->ready);
+        if (sl->h_hist) cudaFreeHost(sl->h_hist);
+        if (sl->h_meta) cudaFreeHost(sl->h_meta);
+    }
+    ctx->slots.clear();
+    drop_graphs(ctx->batch);
+    ws_release(ctx, ctx->ws);
     ctx->eager.release();
+    for (cudaStream_t b : ctx->branch_streams) cudaStreamDestroy(b);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->err_word) cudaFree(ctx->err_word);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -572,8 +523,10 @@ int cgdir_uroi(cgdir_ctx *ctx, const uint8_t *sbits, int k, int nx, int ny, int 
     return CGDIR_OK;
 }
 
-static int auto_sign_impl(cgdir_ctx *ctx, const void *T0, int dtype, const uint8_t *sbits, int k, int nx,
-                          int ny, int nz, int8_t *sign_host) {
+}  // extern "C"
+
+int cgdir::rt::auto_sign_impl(cgdir_ctx *ctx, const void *T0, int dtype, const uint8_t *sbits, int k, int nx,
+                              int ny, int nz, int8_t *sign_host) {
     if (!ctx) return CGDIR_EINVAL;
     if (!T0 || !dims_ok(nx, ny, nz) || k < 0 || k > kMaxMasks || (k > 0 && (!sbits || !sign_host)))
         return fail(ctx, CGDIR_EINVAL, "auto_sign: bad arguments");
@@ -596,6 +549,8 @@ static int auto_sign_impl(cgdir_ctx *ctx, const void *T0, int dtype, const uint8
     }
     return CGDIR_OK;
 }
+
+extern "C" {
 
 int cgdir_auto_sign(cgdir_ctx *ctx, const float *T0, const uint8_t *sbits, int k, int nx, int ny,
                     int nz, int8_t *sign_host) {
@@ -621,344 +576,6 @@ int cgdir_rms_id(cgdir_ctx *ctx, const float *I0, const float *T0, const float *
     CK(cudaStreamSynchronize(ctx->stream));
     *rms_host = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
     if (count_host) *count_host = (long long)h[1];
-    return CGDIR_OK;
-}
-
-// ------------------------------------------------------------ registration
-int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
-                   const cgdir_masks *SM, const cgdir_masks *MM, const cgdir_params *P,
-                   float *dvf_out, int dvf_where, cgdir_level_stats *stats_out) {
-    if (!ctx) return CGDIR_EINVAL;
-    ctx->err.clear();
-    // ---- validation
-    if (!S || !M || !P || !dvf_out) return fail(ctx, CGDIR_EINVAL, "register: null argument");
-    if (!S->data || !M->data) return fail(ctx, CGDIR_EINVAL, "register: null image data");
-    const int nx = S->nx, ny = S->ny, nz = S->nz;
-    if (!dims_ok(nx, ny, nz)) return fail(ctx, CGDIR_EINVAL, "register: image dimensions must be >= 1");
-    if (M->nx != nx || M->ny != ny || M->nz != nz)
-        return fail(ctx, CGDIR_EINVAL, "register: static and moving images differ in size");
-    for (const cgdir_volume *v : {S, M}) {
-        if (v->dtype != CGDIR_F32 && v->dtype != CGDIR_F16 && v->dtype != CGDIR_BF16)
-            return fail(ctx, CGDIR_EINVAL, "register: unknown image dtype");
-        if (v->where != CGDIR_HOST && v->where != CGDIR_DEVICE)
-            return fail(ctx, CGDIR_EINVAL, "register: image 'where' must be HOST or DEVICE");
-    }
-    const int k = SM ? SM->count : 0;
-    if ((MM ? MM->count : 0) != k) return fail(ctx, CGDIR_EINVAL, "register: static and moving mask counts differ");
-    if (k < 0 || k > kMaxMasks) return fail(ctx, CGDIR_EINVAL, "register: mask count must be 0..8");
-    for (const cgdir_masks *m : {SM, MM}) {
-        if (k == 0) break;
-        if (m->nx != nx || m->ny != ny || m->nz != nz)
-            return fail(ctx, CGDIR_EINVAL, "register: masks must have the image size");
-        if (m->where != CGDIR_HOST && m->where != CGDIR_DEVICE)
-            return fail(ctx, CGDIR_EINVAL, "register: mask 'where' must be HOST or DEVICE");
-        if (!m->data) return fail(ctx, CGDIR_EINVAL, "register: null mask array");
-        for (int j = 0; j < k; ++j)
-            if (!m->data[j]) return fail(ctx, CGDIR_EINVAL, "register: null mask pointer");
-    }
-    const int L = P->levels;
-    if (L < 1 || L > CGDIR_MAX_LEVELS || !P->iters) return fail(ctx, CGDIR_EINVAL, "register: levels must be 1..8 with iters");
-    int maxcap = 0;
-    for (int l = 0; l < L; ++l) {
-        if (P->iters[l] < 0 || P->iters[l] > 1000000) return fail(ctx, CGDIR_EINVAL, "register: iters must be 0..1e6");
-        if (P->iters[l] > maxcap) maxcap = P->iters[l];
-    }
-    if (!sigma_ok(P->sigma_fluid) || !sigma_ok(P->sigma_diff))
-        return fail(ctx, CGDIR_EINVAL, "register: sigma must be in [0, 2]");
-    if (P->stop_mode < CGDIR_STOP_FIXED || P->stop_mode > CGDIR_STOP_PAPER_LITERAL || !std::isfinite(P->eps))
-        return fail(ctx, CGDIR_EINVAL, "register: bad stop mode or eps");
-    if (P->compose_mode != CGDIR_COMPOSE && P->compose_mode != CGDIR_ADDITIVE)
-        return fail(ctx, CGDIR_EINVAL, "register: bad compose mode");
-    for (int a = 0; a < 3; ++a)
-        if (!(P->spacing_mm[a] > 0) || !std::isfinite(P->spacing_mm[a]))
-            return fail(ctx, CGDIR_EINVAL, "register: spacing must be > 0");
-    if (!(P->margin_mm >= 0) || !std::isfinite(P->margin_mm)) return fail(ctx, CGDIR_EINVAL, "register: margin must be >= 0");
-    if (k > 0 && P->margin_mm / std::fmin(P->spacing_mm[0], std::fmin(P->spacing_mm[1], P->spacing_mm[2])) > 15.0)
-        return fail(ctx, CGDIR_EINVAL, "register: UROI margin must be <= 15 voxels");
-    if (dvf_where != CGDIR_HOST && dvf_where != CGDIR_DEVICE)
-        return fail(ctx, CGDIR_EINVAL, "register: bad dvf_where");
-    if (P->init_dvf && P->init_dvf_where != CGDIR_HOST && P->init_dvf_where != CGDIR_DEVICE)
-        return fail(ctx, CGDIR_EINVAL, "register: bad init_dvf_where");
-    if (P->storage_dtype < CGDIR_STORAGE_AUTO || P->storage_dtype > CGDIR_BF16)
-        return fail(ctx, CGDIR_EINVAL, "register: bad storage_dtype");
-    ForceArgs base{};
-    {
-        int8_t tmp_sign[kMaxMasks];
-        for (int j = 0; j < kMaxMasks; ++j) tmp_sign[j] = 1;
-        TRY(fill_force_args(ctx, base, k, P->lambda, tmp_sign, P->intensity_offset, 1));
-    }
-
-    DeviceGuard g(ctx->device);
-    cudaStream_t s = ctx->stream;
-
-    // ---- sizes
-    int dims[CGDIR_MAX_LEVELS][3];
-    size_t Nl[CGDIR_MAX_LEVELS], off[CGDIR_MAX_LEVELS + 1];
-    dims[L - 1][0] = nx; dims[L - 1][1] = ny; dims[L - 1][2] = nz;
-    for (int l = L - 2; l >= 0; --l)
-        for (int a = 0; a < 3; ++a) dims[l][a] = (dims[l + 1][a] + 1) / 2;
-    off[0] = 0;
-    for (int l = 0; l < L; ++l) {
-        Nl[l] = (size_t)dims[l][0] * dims[l][1] * dims[l][2];
-        off[l + 1] = off[l] + round_up(Nl[l], 64);
-    }
-    const size_t Nf = Nl[L - 1], Ntot = off[L];
-    const int hcap = maxcap + 1;
-
-    // ---- workspace
-    void *p_img, *p_bits, *p_fields, *p_part, *p_state, *p_rowdist;
-    // image storage type of the pyramid (float32, or 16-bit to halve the image bytes)
-    const int sdt = P->storage_dtype >= 0 ? P->storage_dtype : (S->dtype == M->dtype ? S->dtype : CGDIR_F32);
-    const size_t esz = img_elem_size(sdt), tsz = tex_elem_size(sdt);
-    TRY(ws_get(ctx, "reg_img", 2 * Ntot * esz, &p_img));
-    TRY(ws_get(ctx, "reg_bits", 3 * Ntot, &p_bits));
-    void *p_tex = nullptr;
-    TRY(ws_get(ctx, "reg_tex", Ntot * tsz, &p_tex));
-    TRY(ws_get(ctx, "reg_fields", 4 * 3 * Nf * sizeof(float), &p_fields));
-    size_t np = 0;
-    for (int l = 0; l < L; ++l) {
-        const size_t a = force_partial_count(dims[l][0], dims[l][1], dims[l][2],
-                                             force_default_zchunk(dims[l][0], dims[l][1], dims[l][2]));
-        const size_t b = metric_partial_count(dims[l][0], dims[l][1], dims[l][2]);
-        np = std::max(np, std::max(a, b));
-    }
-    TRY(ws_get(ctx, "reg_partial", np * kPartialStride * sizeof(double), &p_part));
-    const size_t state_bytes = (size_t)L * hcap * sizeof(double) + 5 * CGDIR_MAX_LEVELS * sizeof(int);
-    TRY(ws_get(ctx, "reg_state", state_bytes, &p_state));
-    TRY(ws_get(ctx, "rowdist", uroi_scratch_bytes(Nf), &p_rowdist));
-    void *p_stage = nullptr;
-    const bool need_stage = (S->where == CGDIR_HOST && S->dtype != sdt) ||
-                            (M->where == CGDIR_HOST && M->dtype != sdt) ||
-                            (k > 0 && (SM->where == CGDIR_HOST || MM->where == CGDIR_HOST));
-    if (need_stage) TRY(ws_get(ctx, "reg_stage", std::max(Nf * 4, (size_t)k * Nf), &p_stage));
-    // (re-fetch: a later ws_get may have reallocated an earlier name only if
-    //  the same name was requested twice, which it is not)
-    char *T[CGDIR_MAX_LEVELS], *I[CGDIR_MAX_LEVELS];          // images of type sdt
-    uint8_t *SB[CGDIR_MAX_LEVELS], *MB[CGDIR_MAX_LEVELS], *UR[CGDIR_MAX_LEVELS];
-    for (int l = 0; l < L; ++l) {
-        T[l] = (char *)p_img + off[l] * esz;
-        I[l] = (char *)p_img + (Ntot + off[l]) * esz;
-        SB[l] = (uint8_t *)p_bits + off[l];
-        MB[l] = (uint8_t *)p_bits + Ntot + off[l];
-        UR[l] = (uint8_t *)p_bits + 2 * Ntot + off[l];
-    }
-    float *ua = (float *)p_fields, *ub = ua + 3 * Nf, *du = ub + 3 * Nf, *du2 = du + 3 * Nf;
-    double *partial = (double *)p_part;
-    double *hist = (double *)p_state;
-    int *meta = (int *)((char *)p_state + (size_t)L * hcap * sizeof(double));
-    int *hist_len = meta, *iters_run = meta + CGDIR_MAX_LEVELS, *reason = meta + 2 * CGDIR_MAX_LEVELS,
-        *flags = meta + 3 * CGDIR_MAX_LEVELS;
-    unsigned *done = (unsigned *)(meta + 4 * CGDIR_MAX_LEVELS);   // per-level completion counters
-
-    // ---- ingest images (finest level)
-    auto ingest = [&](const cgdir_volume *v, void *dst) -> int {
-        const size_t bytes = Nf * elem_size(v->dtype);
-        if (v->dtype == sdt) {
-            CK(cudaMemcpyAsync(dst, v->data, bytes,
-                               v->where == CGDIR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
-        } else if (v->where == CGDIR_HOST) {
-            CK(cudaMemcpyAsync(p_stage, v->data, bytes, cudaMemcpyHostToDevice, s));
-            CK(launch_convert_image(p_stage, v->dtype, Nf, dst, sdt, s));
-        } else {
-            CK(launch_convert_image(v->data, v->dtype, Nf, dst, sdt, s));
-        }
-        return CGDIR_OK;
-    };
-    TRY(ingest(S, T[L - 1]));
-    TRY(ingest(M, I[L - 1]));
-    // ---- masks
-    auto pack = [&](const cgdir_masks *m, uint8_t *dst) -> int {
-        if (k == 0) { CK(cudaMemsetAsync(dst, 0, Nf, s)); return CGDIR_OK; }
-        const uint8_t *ptrs[kMaxMasks];
-        if (m->where == CGDIR_HOST) {
-            for (int j = 0; j < k; ++j) {
-                CK(cudaMemcpyAsync((uint8_t *)p_stage + (size_t)j * Nf, m->data[j], Nf, cudaMemcpyHostToDevice, s));
-                ptrs[j] = (uint8_t *)p_stage + (size_t)j * Nf;
-            }
-        } else {
-            for (int j = 0; j < k; ++j) ptrs[j] = m->data[j];
-        }
-        CK(launch_pack_masks(ptrs, k, Nf, dst, s));
-        return CGDIR_OK;
-    };
-    TRY(pack(SM, SB[L - 1]));
-    TRY(pack(MM, MB[L - 1]));
-    // ---- signs (decided on the host before the device part is enqueued)
-    int8_t sign[kMaxMasks];
-    bool need_auto = false;
-    for (int j = 0; j < k; ++j) {
-        sign[j] = P->sign ? P->sign[j] : 0;
-        if (sign[j] > 0) sign[j] = 1;
-        else if (sign[j] < 0) sign[j] = -1;
-        else need_auto = true;
-    }
-    if (need_auto) {
-        int8_t autos[kMaxMasks];
-        TRY(auto_sign_impl(ctx, T[L - 1], sdt, SB[L - 1], k, nx, ny, nz, autos));
-        for (int j = 0; j < k; ++j)
-            if (sign[j] == 0) sign[j] = autos[j];
-    }
-    for (int j = 0; j < k; ++j) base.half_sign[j] = 0.5f * (float)sign[j];
-
-    const int first = P->init_dvf ? L - 1 : 0;
-    if (P->init_dvf)
-        CK(cudaMemcpyAsync(ua, P->init_dvf, 3 * Nf * sizeof(float),
-                           P->init_dvf_where == CGDIR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
-    float *ufinal = ((L - 1 - first) % 2 == 0) ? ua : ub;
-
-    // ---- the device part: pyramid, UROI, every level.  Its launches depend
-    // only on the context's workspace, so it is captured once per shape and
-    // parameter set into a CUDA graph and replayed.
-    auto enqueue = [&](ProfList *pl, cudaStream_t s) -> int {
-        for (int l = L - 2; l >= 0; --l) {
-            const int *d = dims[l + 1];
-            ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
-            CK(launch_restrict_image(T[l + 1], sdt, d[0], d[1], d[2], T[l], s));
-            CK(launch_restrict_image(I[l + 1], sdt, d[0], d[1], d[2], I[l], s));
-            CK(launch_restrict_bits(SB[l + 1], d[0], d[1], d[2], SB[l], s));
-            CK(launch_restrict_bits(MB[l + 1], d[0], d[1], d[2], MB[l], s));
-        }
-        for (int l = 0; l < L; ++l) {
-            if (((P->contour_level_mask >> l) & 1u) && k > 0 && !ctx->plain_kernels) {
-                ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
-                CK(launch_make_texels(I[l], sdt, MB[l], Nl[l], (char *)p_tex + off[l] * tsz, s));
-            }
-            const double f = (double)(1 << (L - 1 - l));
-            const double sp[3] = {P->spacing_mm[0] * f, P->spacing_mm[1] * f, P->spacing_mm[2] * f};
-            ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
-            CK(launch_uroi(SB[l], k, dims[l][0], dims[l][1], dims[l][2], sp, P->margin_mm,
-                           (uint8_t *)p_rowdist, UR[l], s));
-        }
-        CK(cudaMemsetAsync(p_state, 0, state_bytes, s));
-        float *ucur = ua, *uoth = ub;
-        for (int l = first; l < L; ++l) {
-            const int lx = dims[l][0], ly = dims[l][1], lz = dims[l][2];
-            const size_t N = Nl[l];
-            if (l == first) {
-                if (!P->init_dvf) CK(cudaMemsetAsync(ucur, 0, 3 * N * sizeof(float), s));
-            } else {
-                ProfScope ps(pl, ctx->prof_mask, s, CGDIR_K_SETUP, l);
-                CK(launch_prolong(ucur, dims[l - 1][0], dims[l - 1][1], dims[l - 1][2], lx, ly, lz, uoth, s));
-                std::swap(ucur, uoth);
-            }
-            LevelState st{};
-            st.hist = hist + (size_t)l * hcap;
-            st.hist_len = hist_len + l;
-            st.iters_run = iters_run + l;
-            st.stop_reason = reason + l;
-            st.stop_flag = flags + l;
-            st.hist_cap = hcap;
-            ForceArgs a = base;
-            a.I0 = I[l]; a.T0 = T[l]; a.img_dtype = sdt; a.mbits = MB[l]; a.sbits = SB[l]; a.uroi = UR[l];
-            a.mtex = ctx->plain_kernels ? nullptr : (const void *)((char *)p_tex + off[l] * tsz);
-            a.u = ucur; a.du = du; a.warped = nullptr; a.partial = partial; a.stop_flag = flags + l;
-            a.nx = lx; a.ny = ly; a.nz = lz;
-            a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
-            const int zc = force_default_zchunk(lx, ly, lz);
-            const int cap = P->iters[l];
-            const unsigned m = ctx->prof_mask;
-            a.fin.done = done + l;
-            a.fin.st = st;
-            a.fin.cap = cap;
-            a.fin.stop_mode = P->stop_mode;
-            a.fin.eps = P->eps;
-            a.fin.stats_out = nullptr;
-            for (int n = 0; n < cap; ++n) {
-                int nb = 0;
-                a.fin.n = n;   // the force kernel's last CTA reduces delta^n and runs the stop test
-                { ProfScope ps(pl, m, s, CGDIR_K_FORCE, l); CK(launch_force(a, zc, &nb, s, kerr(ctx))); }
-                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3
-                  CK(launch_smooth_compose(du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, du2, uoth,
-                                           flags + l, s, kerr(ctx))); }
-                { ProfScope ps(pl, m, s, CGDIR_K_SMOOTH_U, l);    // step 4
-                  CK(launch_smooth(du2, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx))); }
-            }
-            int nb = 0;
-            FinishArgs fm = a.fin;
-            fm.n = cap;
-            { ProfScope ps(pl, m, s, CGDIR_K_METRIC, l);
-              CK(launch_metric(I[l], T[l], sdt, ucur, UR[l], lx, ly, lz, partial, flags + l, &nb, s, &fm)); }
-        }
-        return CGDIR_OK;
-    };
-
-    const ProfList *used = nullptr;
-    if (ctx->use_graphs) {
-        char key[1024];
-        int len = std::snprintf(key, sizeof key, "%d %d %d|%d|%d %d %.9g %.9g %d %u %d %.17g %.17g %.17g %.17g "
-                                "%.17g %.9g %d %d %llu %u %d|", nx, ny, nz, L, k, first, P->sigma_fluid, P->sigma_diff,
-                                P->compose_mode, P->contour_level_mask, P->stop_mode, P->eps, P->spacing_mm[0],
-                                P->spacing_mm[1], P->spacing_mm[2], P->margin_mm, P->intensity_offset,
-                                (int)ctx->plain_kernels, maxcap, ctx->ws_generation, ctx->prof_mask, sdt);
-        std::string skey(key, (size_t)len);
-        for (int l = 0; l < L; ++l) skey += std::to_string(P->iters[l]) + ",";
-        for (int j = 0; j < k; ++j) {
-            char b[48];
-            std::snprintf(b, sizeof b, "%.9g:%d,", base.lambda[j], (int)sign[j]);
-            skey += b;
-        }
-        auto it = ctx->graphs.find(skey);
-        if (it == ctx->graphs.end()) {
-            GraphEntry ge;
-            const unsigned long long before = g_launches.load();
-            CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-            const int rc = enqueue(&ge.prof, ctx->cap_stream);
-            cudaGraph_t graph = nullptr;
-            const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
-            ge.launches = g_launches.load() - before;
-            g_launches.fetch_sub(ge.launches);        // captured, not yet launched
-            if (rc != CGDIR_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                ge.prof.release();
-                return rc;
-            }
-            if (ec != cudaSuccess) {
-                ge.prof.release();
-                return fail(ctx, CGDIR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-            }
-            const cudaError_t ei = cudaGraphInstantiate(&ge.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ei != cudaSuccess) {
-                ge.prof.release();
-                return fail(ctx, CGDIR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
-            }
-            it = ctx->graphs.emplace(skey, std::move(ge)).first;
-        }
-        CK(cudaGraphLaunch(it->second.exec, s));
-        note_launch((unsigned)it->second.launches);
-        used = &it->second.prof;
-    } else {
-        ctx->eager.recs.clear();
-        TRY(enqueue(&ctx->eager, s));
-        used = &ctx->eager;
-    }
-
-    // ---- outputs
-    CK(cudaMemcpyAsync(dvf_out, ufinal, 3 * Nf * sizeof(float),
-                       dvf_where == CGDIR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-    ctx->h_hist.assign((size_t)L * hcap, 0.0);
-    ctx->h_meta.assign(4 * CGDIR_MAX_LEVELS, 0);
-    CK(cudaMemcpyAsync(ctx->h_hist.data(), hist, (size_t)L * hcap * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->h_meta.data(), meta, 4 * CGDIR_MAX_LEVELS * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    CK(cudaGetLastError());
-    prof_collect(ctx, *used);
-    TRY(check_err_word(ctx));
-    if (stats_out) {
-        for (int l = 0; l < L; ++l) {
-            cgdir_level_stats &o = stats_out[l];
-            o.level = l;
-            o.nx = dims[l][0]; o.ny = dims[l][1]; o.nz = dims[l][2];
-            if (l < first) {
-                o.iters_run = 0; o.stop_reason = CGDIR_REASON_SKIPPED; o.hist_len = 0; o.rms_id = nullptr;
-                continue;
-            }
-            o.iters_run = ctx->h_meta[CGDIR_MAX_LEVELS + l];
-            o.stop_reason = ctx->h_meta[2 * CGDIR_MAX_LEVELS + l];
-            o.hist_len = ctx->h_meta[l];
-            o.rms_id = ctx->h_hist.data() + (size_t)l * hcap;
-        }
-    }
     return CGDIR_OK;
 }
 

@@ -1,0 +1,174 @@
+"""Batched and served registrations (execution modes around Algorithm A):
+each case's result must be the one cgdir_register gives for it alone, bit for
+bit, whether it runs in a batch graph, in a serving slot alone, or among
+other requests in flight; and the batched path must still match the FP64
+oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import phantom
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1301_0970_gb300 as cg  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def mix(n=6, scale=0.22):
+    """Uneven mix of small cases (2-8 masks, four CT shapes shrunk), each
+    with its own iteration caps and stopping rule."""
+    out = []
+    for i, c in enumerate(phantom.batch_mix_cases(n, seed=4100, scale=scale)):
+        kw = dict(levels=2, iters=[8 + i, 5 + (i % 3)], lam=c.lam, sign=c.signs,
+                  stop_mode=cg.CGDIR_STOP_WINDOW10 if i % 2 else cg.CGDIR_STOP_FIXED, eps=1e-3,
+                  contour_level_mask=3 if i % 3 == 0 else 2)
+        out.append((c, kw))
+    c = phantom.make_case("phantom64", shape=(9, 22, 26))       # a case without masks
+    out.append((c, dict(levels=2, iters=[6, 4], lam=[], sign=[], stop_mode=cg.CGDIR_STOP_FIXED)))
+    return out
+
+
+def case_dict(c, kw):
+    d = dict(static=dev(c.static), moving=dev(c.moving), **kw)
+    if kw.get("lam"):
+        d["static_masks"] = [dev(m) for m in c.static_masks]
+        d["moving_masks"] = [dev(m) for m in c.moving_masks]
+    return d
+
+
+def single(ctx, c, kw):
+    d = case_dict(c, kw)
+    return ctx.register(d.pop("static"), d.pop("moving"), d.pop("static_masks", None),
+                        d.pop("moving_masks", None), **d)
+
+
+def submit(ctx, c, kw, **extra):
+    d = case_dict(c, kw)
+    d.update(extra)
+    return ctx.submit(d.pop("static"), d.pop("moving"), d.pop("static_masks", None),
+                      d.pop("moving_masks", None), **d)
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return mix()
+
+
+@pytest.fixture(scope="module")
+def singles(cases):
+    with cg.Context(0) as ctx:
+        return [(d.cpu(), st) for d, st in (single(ctx, c, kw) for c, kw in cases)]
+
+
+@pytest.mark.parametrize("graphs", ["1", "0"])
+def test_batch_equals_single_bitwise(cases, singles, graphs, monkeypatch):
+    monkeypatch.setenv("CGDIR_GRAPHS", graphs)
+    with cg.Context(0) as ctx:
+        for _ in range(2):                     # the second call replays the cached batch graph
+            res = ctx.register_batch([case_dict(c, kw) for c, kw in cases])
+            for (d, st), (d1, st1) in zip(res, singles):
+                assert torch.equal(d.cpu(), d1)
+                assert st == st1
+
+
+def test_batch_matches_oracle(cases, singles):
+    """The batched results (== the single ones) against the FP64 oracle: DVF
+    within 0.05 voxel RMS, the same iteration counts."""
+    for (c, kw), (d, st) in list(zip(cases, singles))[:3]:
+        ref, rst = oracle.register(c.static, c.moving, c.static_masks, c.moving_masks,
+                                   levels=kw["levels"], iters=kw["iters"], lam=kw["lam"], sign=kw["sign"],
+                                   contour_mask=kw["contour_level_mask"], stop_mode=kw["stop_mode"],
+                                   eps=kw["eps"])
+        got = d.numpy().astype(np.float64)
+        assert float(np.sqrt(((got - ref) ** 2).sum(axis=0).mean())) <= 0.05
+        assert [s["iters_run"] for s in st] == [r["iters_run"] for r in rst]
+
+
+def test_served_alone_equals_served_in_mix(cases, singles):
+    with cg.Context(0) as ctx:
+        alone = []
+        for c, kw in cases:
+            r = submit(ctx, c, kw)
+            d, st = ctx.wait(r)
+            alone.append((d.cpu(), st))
+        ctx.set_max_inflight(len(cases))
+        reqs = [submit(ctx, c, kw) for c, kw in cases]
+        mixed = [ctx.wait(r) for r in reversed(reqs)][::-1]
+        for (a, sa), (m, sm), (s1, ss1) in zip(alone, mixed, singles):
+            assert torch.equal(a, s1) and torch.equal(m.cpu(), s1)
+            assert sa == sm == ss1
+
+
+def test_submit_refuses_when_every_slot_is_busy(cases):
+    c, kw = cases[0]
+    with cg.Context(0) as ctx:
+        ctx.set_max_inflight(2)
+        a, b = submit(ctx, c, kw), submit(ctx, c, kw)
+        with pytest.raises(cg.CgdirError) as e:
+            submit(ctx, c, kw)
+        assert e.value.status == cg.CGDIR_EBUSY
+        da, _ = ctx.wait(a)
+        d3 = ctx.wait(submit(ctx, c, kw))[0]      # a slot is free again
+        db, _ = ctx.wait(b)
+        assert torch.equal(da, db) and torch.equal(da, d3)
+
+
+def test_wait_timeout_leaves_the_request_in_flight():
+    c = phantom.make_case("headneck256", shape=(40, 128, 128))
+    kw = dict(levels=1, iters=[150], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as ctx:
+        r = submit(ctx, c, kw)
+        with pytest.raises(cg.CgdirError) as e:
+            ctx.wait(r, timeout_ms=0)
+        assert e.value.status == cg.CGDIR_ETIMEDOUT
+        d, st = ctx.wait(r)
+        ref, _ = single(ctx, c, kw)
+        assert torch.equal(d, ref) and st[0]["iters_run"] == 150
+
+
+def test_pageable_host_output_is_written_at_collection(cases, singles):
+    c, kw = cases[1]
+    with cg.Context(0) as ctx:
+        out = torch.empty((3,) + tuple(c.static.shape), dtype=torch.float32)       # pageable
+        r = submit(ctx, c, kw, dvf_out=out)
+        d, _ = ctx.wait(r)
+        assert d.data_ptr() == out.data_ptr()
+        assert torch.equal(out, singles[1][0])
+
+
+def test_cancel_frees_the_slot():
+    c = phantom.make_case("headneck256", shape=(40, 128, 128))
+    kw = dict(levels=1, iters=[400], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    small = dict(levels=1, iters=[5], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as ctx:
+        ctx.set_max_inflight(1)
+        r = submit(ctx, c, kw)
+        ctx.cancel(r)
+        d, st = ctx.wait(submit(ctx, c, small))
+        ref, rst = single(ctx, c, small)
+        assert torch.equal(d, ref) and st == rst
+
+
+def test_budget_admission_returns_busy_then_admits(cases):
+    c, kw = cases[2]
+    with cg.Context(0) as probe:
+        probe.wait(submit(probe, c, kw))
+        one = probe.mem_in_use()
+    with cg.Context(0, mem_budget_bytes=int(one * 1.5)) as ctx:
+        a = submit(ctx, c, kw)
+        with pytest.raises(cg.CgdirError) as e:
+            submit(ctx, c, kw)                   # a second slot's buffers would exceed the budget
+        assert e.value.status == cg.CGDIR_EBUSY
+        da, _ = ctx.wait(a)
+        db, _ = ctx.wait(submit(ctx, c, kw))     # reuses the first slot's buffers
+        assert torch.equal(da, db)
