@@ -55,6 +55,14 @@ def parse():
                          "run), printed as one JSON line")
     ap.add_argument("--shape", default=None,
                     help="with --only: nz,ny,nx of the inputs (the workload's case resampled)")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+                    help="single: the head-and-neck registration (default); batch: 32 cases of "
+                         "uneven sizes in one graph launch, FP16 images, against plain FP32 one "
+                         "at a time; serve: Poisson arrivals of the same mix at 1-64 requests/s "
+                         "under a 160 GB device budget, p50/p99 latency against plain FP32 one at "
+                         "a time")
+    ap.add_argument("--batch-n", type=int, default=32, help="cases in the batch / serving mix")
+    ap.add_argument("--rates", default="1,2,4,8,16,32,64", help="serve: arrival rates (requests/s)")
     return ap.parse_args()
 
 
@@ -370,6 +378,229 @@ def run_cgdir(args):
     return 0
 
 
+# --------------------------------------------------------------------------- #
+# the uneven-size mix: batched (one graph launch) and served (Poisson arrivals)
+# --------------------------------------------------------------------------- #
+MIX = {"seed": 4000, "levels": 3, "iters": [100, 50, 25], "budget_gb": 160}
+
+
+def build_mix(torch, dev, n):
+    """The mix of n cases, built on the device (FP32 images, FP16 copies,
+    uint8 masks), each with its voxel-iteration count."""
+    import phantom
+    cases = []
+    for tmpl, index, shp, names in phantom.batch_mix_specs(n, MIX["seed"]):
+        c = phantom.make_case_device(tmpl, index, shp, names, device=dev)
+        c.u_gt = c.body = None
+        cases.append({"S": c.static, "M": c.moving, "S16": c.static.half(), "M16": c.moving.half(),
+                      "SM": list(c.static_masks.unbind(0)), "MM": list(c.moving_masks.unbind(0)),
+                      "lam": c.lam, "sign": c.signs, "shape": tuple(shp), "k": c.k,
+                      "vi": phantom.voxel_iters(shp, MIX["levels"], MIX["iters"])})
+        torch.cuda.empty_cache()
+    return cases
+
+
+def mix_request(cg, c, half, dvf=None):
+    kw = dict(levels=MIX["levels"], iters=MIX["iters"], lam=c["lam"], sign=c["sign"],
+              stop_mode=cg.CGDIR_STOP_FIXED, storage_dtype=cg.CGDIR_F16 if half else cg.CGDIR_F32)
+    d = dict(static=c["S16"] if half else c["S"], moving=c["M16"] if half else c["M"],
+             static_masks=c["SM"], moving_masks=c["MM"], **kw)
+    if dvf is not None:
+        d["dvf_out"] = dvf
+    return d
+
+
+def mix_config(cases):
+    shapes = sorted({c["shape"] for c in cases})
+    return {"workload": f"batch_mix{len(cases)}: {len(cases)} registrations, sizes drawn uniformly "
+                        f"from {{128x128x64, 256x256x96, 384x384x128, 512x512x160}}, 2-8 uint8 masks, "
+                        f"bumps <= 10 voxels, 3-level pyramid 100/50/25, FIXED stop",
+            "shapes_zyx": [list(s) for s in shapes], "cases": len(cases),
+            "voxel_iters_total": int(sum(c["vi"] for c in cases)),
+            "l2": "inputs larger than L2 (several GB per pass)", "parallelism": "replicas x1"}
+
+
+def one_at_a_time(torch, cg, ctx, cases, stream):
+    """Plain FP32, one registration after another: per-case times (ms)."""
+    out = []
+    for c in cases:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d = mix_request(cg, c, False)
+        a.record(stream)
+        ctx.register(d.pop("static"), d.pop("moving"), d.pop("static_masks"), d.pop("moving_masks"), **d)
+        b.record(stream)
+        out.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in out]
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    import paper_1301_0970_gb300 as cg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    cases = build_mix(torch, dev, args.batch_n)
+    total_vi = sum(c["vi"] for c in cases)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    with cg.Context(0) as ctx:
+        # plain FP32, one at a time (warm-up passes capture every shape's graph)
+        for _ in range(max(args.warmup, 2)):
+            one_at_a_time(torch, cg, ctx, cases, stream)
+        per, tot = [], []
+        for _ in range(args.steps):
+            t = one_at_a_time(torch, cg, ctx, cases, stream)
+            per += t
+            tot.append(sum(t))
+        res["plain"] = {"value": total_vi * len(tot) / (sum(tot) / 1e3), "ms_per_pass": float(np.mean(tot)),
+                        "p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))}
+        # batched: every case in one graph launch
+        for half in (False, True):
+            outs = [torch.empty((3,) + c["shape"], dtype=torch.float32, device=dev) for c in cases]
+            reqs = [mix_request(cg, c, half, o) for c, o in zip(cases, outs)]
+            for _ in range(args.warmup):
+                ctx.register_batch(reqs)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            l0 = cg.launch_count()
+            with ClockSampler(gpu_uuid(torch, dev)) as clk:
+                for i in range(args.steps):
+                    ev[i][0].record(stream)
+                    ctx.register_batch(reqs)
+                    ev[i][1].record(stream)
+                torch.cuda.synchronize()
+            launches = cg.launch_count() - l0
+            ms = [a.elapsed_time(b) for a, b in ev]
+            res["f16" if half else "f32"] = {"value": total_vi * len(ms) / (sum(ms) / 1e3),
+                                             "ms_per_pass": float(np.mean(ms)), "launches": launches,
+                                             "clocks": clk.summary()}
+            del outs, reqs
+    b16 = res["f16"]
+    line = {"metric": METRIC, "value": b16["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b16["ms_per_pass"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 images, f32 arithmetic",
+            "data": "synthetic", "config": mix_config(cases),
+            "latency_ms": {"p50": b16["ms_per_pass"], "p99": b16["ms_per_pass"],
+                           "per": "registration (every case of a batch completes with the batch)"},
+            "gpu_launches": int(b16["launches"]), "clocks": b16["clocks"],
+            "batched_f32": {"value": res["f32"]["value"], "ms_per_pass": res["f32"]["ms_per_pass"]},
+            "plain_f32_one_at_a_time": {"value": res["plain"]["value"], "ms_per_pass": res["plain"]["ms_per_pass"],
+                                        "latency_ms": {"p50": res["plain"]["p50"], "p99": res["plain"]["p99"],
+                                                       "per": "registration"}},
+            "speedup_vs_plain_f32": b16["value"] / res["plain"]["value"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_trace(rng, rate, n_cases):
+    """Seeded Poisson arrivals at `rate` per second (8-32 requests, about 4 s
+    of arrivals) and the case of each request."""
+    import numpy as np
+    n = int(min(32, max(8, 4 * rate)))
+    gaps = rng.exponential(1.0 / rate, size=n)
+    return np.cumsum(gaps) - gaps[0], rng.integers(0, n_cases, size=n)
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+
+    import paper_1301_0970_gb300 as cg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    cases = build_mix(torch, dev, args.batch_n)
+    rates = [float(r) for r in args.rates.split(",")]
+    rng = np.random.Generator(np.random.PCG64(MIX["seed"] + 1))
+    traces = {r: serve_trace(rng, r, len(cases)) for r in rates}
+
+    def served(ctx, arrivals, which, half):
+        """Continuous admission: submit each request at its arrival time (or
+        as soon as a slot / the budget admits it), collect completions."""
+        lat, inflight, i, n = [], {}, 0, len(arrivals)
+        t0 = time.perf_counter()
+        t_end = t0
+        while i < n or inflight:
+            now = time.perf_counter() - t0
+            progressed = False
+            while i < n and arrivals[i] <= now:
+                c = cases[int(which[i])]
+                d = mix_request(cg, c, half)
+                try:
+                    r = ctx.submit(d.pop("static"), d.pop("moving"), d.pop("static_masks"),
+                                   d.pop("moving_masks"), **d)
+                except cg.CgdirError as e:
+                    if e.status != cg.CGDIR_EBUSY:
+                        raise
+                    break
+                inflight[r] = (arrivals[i], c["vi"])
+                i += 1
+                progressed = True
+            for r in list(inflight):
+                if ctx.poll(r):
+                    ctx.wait(r)
+                    t_done = time.perf_counter() - t0
+                    a, _ = inflight.pop(r)
+                    lat.append(1e3 * (t_done - a))
+                    t_end = max(t_end, t0 + t_done)
+                    progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+        vi = sum(cases[int(w)]["vi"] for w in which)
+        return lat, vi / (t_end - t0)
+
+    def plain(ctx, arrivals, which):
+        """One at a time, FP32, first come first served."""
+        lat, t0 = [], time.perf_counter()
+        for a, w in zip(arrivals, which):
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            d = mix_request(cg, cases[int(w)], False)
+            ctx.register(d.pop("static"), d.pop("moving"), d.pop("static_masks"), d.pop("moving_masks"), **d)
+            lat.append(1e3 * (time.perf_counter() - t0 - a))
+        vi = sum(cases[int(w)]["vi"] for w in which)
+        return lat, vi / (time.perf_counter() - t0)
+
+    rows = []
+    l0 = cg.launch_count()
+    with cg.Context(0, mem_budget_bytes=MIX["budget_gb"] << 30) as sctx, cg.Context(0) as pctx:
+        sctx.set_max_inflight(64)
+        everyone = (np.zeros(len(cases)), np.arange(len(cases)))
+        for _ in range(2):                                   # warm-up: slots, buffers, graphs
+            served(sctx, *everyone, True)
+        for _ in range(2):
+            plain(pctx, np.zeros(len(cases)), np.arange(len(cases)))
+        torch.cuda.synchronize()
+        l0 = cg.launch_count()
+        with ClockSampler(gpu_uuid(torch, dev)) as clk:
+            for r in rates:
+                arr, which = traces[r]
+                ls, vs = served(sctx, arr, which, True)
+                lp, vp = plain(pctx, arr, which)
+                rows.append({"rate_per_s": r, "requests": len(arr),
+                             "served_f16": {"value": vs, "p50_ms": float(np.percentile(ls, 50)),
+                                            "p99_ms": float(np.percentile(ls, 99))},
+                             "plain_f32": {"value": vp, "p50_ms": float(np.percentile(lp, 50)),
+                                           "p99_ms": float(np.percentile(lp, 99))}})
+        launches = cg.launch_count() - l0
+    top = max(rows, key=lambda x: x["served_f16"]["value"])
+    line = {"metric": METRIC, "value": top["served_f16"]["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": len(rates), "warmup": 2, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 images, f32 arithmetic",
+            "data": "synthetic", "config": dict(mix_config(cases), budget_gb=MIX["budget_gb"],
+                                                 max_inflight=64, arrivals="Poisson, seeded"),
+            "latency_ms": {"p50": top["served_f16"]["p50_ms"], "p99": top["served_f16"]["p99_ms"],
+                           "per": "registration, arrival to completion", "at_rate": top["rate_per_s"]},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "rates": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_only_kernel(args):
     """One kernel alone on the full-resolution inputs (u = half the
     ground-truth DVF, contour terms on for the force), for kernel profiling."""
@@ -461,6 +692,10 @@ def main():
         return run_reference(args)
     if args.only:
         return run_only_kernel(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     return run_cgdir(args)
 
 

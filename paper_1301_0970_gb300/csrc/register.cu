@@ -59,8 +59,26 @@ struct RegPlan {
     uint8_t *rowdist = nullptr;
     void *stage = nullptr;
     unsigned long long generation = 0;
-    size_t device_bytes = 0;           // what the slot's buffers need
+    // the slot buffers this plan needs: name and bytes (see plan_prepare)
+    enum { B_IMG, B_BITS, B_TEX, B_FIELDS, B_PARTIAL, B_STATE, B_ROWDIST, B_STAGE, B_COUNT };
+    size_t need[B_COUNT] = {};
 };
+
+const char *const kBufName[RegPlan::B_COUNT] = {"img", "bits", "tex", "fields", "partial", "state", "rowdist",
+                                                "stage"};
+
+// Bytes the slot's buffers must grow by to hold plan `pl` (ws_get rounding).
+size_t plan_growth(const RegPlan &pl, const WsSet &ws) {
+    size_t g = 0;
+    for (int b = 0; b < RegPlan::B_COUNT; ++b) {
+        if (!pl.need[b]) continue;
+        const size_t cap = round_up(pl.need[b], (size_t)1 << 21);
+        auto it = ws.bufs.find(kBufName[b]);
+        const size_t have = it == ws.bufs.end() ? 0 : it->second.cap;
+        if (have < pl.need[b]) g += cap - have;
+    }
+    return g;
+}
 
 void RegPlanDeleter::operator()(RegPlan *p) const { delete p; }
 
@@ -156,10 +174,17 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
                                    metric_partial_count(d[0], d[1], d[2])));
     }
     const size_t Ntot = pl.Ntot, Nf = pl.Nf;
-    auto rb = [](size_t b) { return round_up(b ? b : 256, (size_t)1 << 21); };
-    pl.device_bytes = rb(2 * Ntot * pl.esz) + rb(3 * Ntot) + rb(Ntot * pl.tsz) + rb(12 * 4 * Nf) +
-                      rb(np * kPartialStride * sizeof(double)) + rb(pl.state_bytes) + rb(uroi_scratch_bytes(Nf)) +
-                      rb(std::max(Nf * 4, (size_t)k * Nf));
+    pl.need[RegPlan::B_IMG] = 2 * Ntot * pl.esz;
+    pl.need[RegPlan::B_BITS] = 3 * Ntot;
+    pl.need[RegPlan::B_TEX] = Ntot * pl.tsz;
+    pl.need[RegPlan::B_FIELDS] = 4 * 3 * Nf * sizeof(float);
+    pl.need[RegPlan::B_PARTIAL] = std::max<size_t>(np * kPartialStride * sizeof(double), 256);
+    pl.need[RegPlan::B_STATE] = pl.state_bytes;
+    pl.need[RegPlan::B_ROWDIST] = std::max<size_t>(uroi_scratch_bytes(Nf), 256);
+    const bool need_stage = (S->where == CGDIR_HOST && S->dtype != pl.sdt) ||
+                            (M->where == CGDIR_HOST && M->dtype != pl.sdt) ||
+                            (k > 0 && (SM->where == CGDIR_HOST || MM->where == CGDIR_HOST));
+    pl.need[RegPlan::B_STAGE] = need_stage ? std::max(Nf * 4, (size_t)k * Nf) : 0;
     return CGDIR_OK;
 }
 
@@ -167,25 +192,13 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
 int plan_prepare(cgdir_ctx *ctx, Slot &sl, RegPlan &pl, cudaStream_t s) {
     const size_t Ntot = pl.Ntot, Nf = pl.Nf;
     const int L = pl.L, k = pl.k;
-    void *p_img, *p_bits, *p_fields, *p_part, *p_state, *p_rowdist, *p_tex, *p_stage = nullptr;
+    void *p[RegPlan::B_COUNT] = {};
     WsSet &ws = sl.ws;
-    TRY(ws_get(ctx, ws, s, "img", 2 * Ntot * pl.esz, &p_img));
-    TRY(ws_get(ctx, ws, s, "bits", 3 * Ntot, &p_bits));
-    TRY(ws_get(ctx, ws, s, "tex", Ntot * pl.tsz, &p_tex));
-    TRY(ws_get(ctx, ws, s, "fields", 4 * 3 * Nf * sizeof(float), &p_fields));
-    size_t np = 0;
-    for (int l = 0; l < L; ++l) {
-        const int *d = pl.dims[l];
-        np = std::max(np, std::max(force_partial_count(d[0], d[1], d[2], force_default_zchunk(d[0], d[1], d[2])),
-                                   metric_partial_count(d[0], d[1], d[2])));
-    }
-    TRY(ws_get(ctx, ws, s, "partial", np * kPartialStride * sizeof(double), &p_part));
-    TRY(ws_get(ctx, ws, s, "state", pl.state_bytes, &p_state));
-    TRY(ws_get(ctx, ws, s, "rowdist", uroi_scratch_bytes(Nf), &p_rowdist));
-    const bool need_stage = (pl.S->where == CGDIR_HOST && pl.S->dtype != pl.sdt) ||
-                            (pl.M->where == CGDIR_HOST && pl.M->dtype != pl.sdt) ||
-                            (k > 0 && (pl.SM->where == CGDIR_HOST || pl.MM->where == CGDIR_HOST));
-    if (need_stage) TRY(ws_get(ctx, ws, s, "stage", std::max(Nf * 4, (size_t)k * Nf), &p_stage));
+    for (int b = 0; b < RegPlan::B_COUNT; ++b)
+        if (pl.need[b]) TRY(ws_get(ctx, ws, s, kBufName[b], pl.need[b], &p[b]));
+    void *p_img = p[RegPlan::B_IMG], *p_bits = p[RegPlan::B_BITS], *p_tex = p[RegPlan::B_TEX],
+         *p_fields = p[RegPlan::B_FIELDS], *p_part = p[RegPlan::B_PARTIAL], *p_state = p[RegPlan::B_STATE],
+         *p_rowdist = p[RegPlan::B_ROWDIST], *p_stage = p[RegPlan::B_STAGE];
     pl.generation = ws.generation;
     for (int l = 0; l < L; ++l) {
         pl.T[l] = (char *)p_img + pl.off[l] * pl.esz;
@@ -581,15 +594,26 @@ int cgdir_submit(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, c
     std::unique_ptr<RegPlan, RegPlanDeleter> pl(new RegPlan());
     TRY(plan_make(ctx, S, M, SM, MM, P, dvf_where, *pl));
     DeviceGuard g(ctx->device);
-    // a free slot (slot 0 is left to cgdir_register); prefer one whose buffers fit
+    // a free slot (slot 0 is left to cgdir_register): first one that already
+    // holds a graph for this request (no capture, no growth), else the one
+    // whose buffers must grow least
     int pick = -1;
     size_t best = (size_t)-1;
+    bool best_warm = false;
     for (int i = 1; i <= ctx->max_slots; ++i) {
         Slot &sl = slot_at(ctx, (size_t)i);
         if (sl.busy) continue;
-        const size_t have = sl.ws.bytes();
-        const size_t grow = pl->device_bytes > have ? pl->device_bytes - have : 0;
-        if (grow < best) { best = grow; pick = i; }
+        const size_t grow = plan_growth(*pl, sl.ws);
+        bool warm = false;
+        if (grow == 0 && ctx->use_graphs) {
+            pl->generation = sl.ws.generation;
+            warm = sl.ws.graphs.count(plan_key(ctx, *pl)) > 0;
+        }
+        if ((warm && !best_warm) || (warm == best_warm && grow < best)) {
+            best = grow;
+            best_warm = warm;
+            pick = i;
+        }
     }
     if (pick < 0) return fail(ctx, CGDIR_EBUSY, "submit: every slot is busy");
     Slot &sl = *ctx->slots[pick];

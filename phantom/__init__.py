@@ -44,8 +44,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 import numpy as np
 import torch
 
-__all__ = ["Case", "CONFIGS", "make_case", "config_names", "batch_mix_cases",
-           "voxel_iters"]
+__all__ = ["Case", "CONFIGS", "make_case", "make_case_device", "config_names", "batch_mix_cases",
+           "batch_mix_specs", "voxel_iters"]
 
 AIR = -1000.0
 
@@ -204,7 +204,7 @@ def _layer_occupancy(layer: Layer, px, py, pz, shape, width=0.5):
 
 
 def _paint(layers: Sequence[Layer], px, py, pz, shape) -> np.ndarray:
-    v = torch.full(px.shape, AIR, dtype=torch.float64)
+    v = torch.full(px.shape, AIR, dtype=torch.float64, device=px.device)
     for layer in layers:
         if not layer.painted:
             continue
@@ -213,11 +213,11 @@ def _paint(layers: Sequence[Layer], px, py, pz, shape) -> np.ndarray:
     return v
 
 
-def _grid(shape):
+def _grid(shape, device=None):
     nz, ny, nx = shape
-    z, y, x = torch.meshgrid(torch.arange(nz, dtype=torch.float64),
-                             torch.arange(ny, dtype=torch.float64),
-                             torch.arange(nx, dtype=torch.float64), indexing="ij")
+    z, y, x = torch.meshgrid(torch.arange(nz, dtype=torch.float64, device=device),
+                             torch.arange(ny, dtype=torch.float64, device=device),
+                             torch.arange(nx, dtype=torch.float64, device=device), indexing="ij")
     return x, y, z
 
 
@@ -225,7 +225,7 @@ def _grid(shape):
 # ground-truth deformation
 # --------------------------------------------------------------------------- #
 def _bump_field(bumps, px, py, pz):
-    out = torch.zeros((3,) + tuple(px.shape), dtype=torch.float64)
+    out = torch.zeros((3,) + tuple(px.shape), dtype=torch.float64, device=px.device)
     for (c, sig, amp) in bumps:
         g = torch.exp(-((px - c[0]) ** 2 + (py - c[1]) ** 2 + (pz - c[2]) ** 2)
                       / (2.0 * sig * sig))
@@ -263,9 +263,9 @@ def _make_bumps(rng, cfg: Config, shape, cap):
     return bumps
 
 
-def _scale_bumps(bumps, shape, cap):
+def _scale_bumps(bumps, shape, cap, device=None):
     """Scale amplitudes so max |u_gt| == cap and the displacement gradient <= 0.5."""
-    x, y, z = _grid(shape)
+    x, y, z = _grid(shape, device)
     u = _bump_field(bumps, x, y, z)
     mag = float(torch.sqrt((u * u).sum(dim=0)).max())
     if mag <= 0:
@@ -281,9 +281,9 @@ def _scale_bumps(bumps, shape, cap):
     return [(c, s, amp * scale) for (c, s, amp) in bumps], u * scale
 
 
-def _invert(bumps, shape, tol=1e-5, max_iter=200):
+def _invert(bumps, shape, tol=1e-5, max_iter=200, device=None):
     """w with w(y) = -u_gt(y + w(y)), by fixed-point iteration."""
-    x, y, z = _grid(shape)
+    x, y, z = _grid(shape, device)
     w = -_bump_field(bumps, x, y, z)
     for _ in range(max_iter):
         nw = -_bump_field(bumps, x + w[0], y + w[1], z + w[2])
@@ -312,6 +312,23 @@ def _bias_field(rng, shape):
                 b += a * np.cos(math.pi * (kx * x / max(nx, 1) + ky * y / max(ny, 1)
                                            + kz * z / max(nz, 1)) + phase)
     return b / max(float(np.abs(b).max()), 1e-12)
+
+
+def _bias_field_device(rng, shape, device):
+    """``_bias_field`` evaluated with torch on ``device`` (the same draws)."""
+    x, y, z = _grid(shape, device)
+    nz, ny, nx = shape
+    b = torch.zeros(shape, dtype=torch.float64, device=device)
+    for kx in range(3):
+        for ky in range(3):
+            for kz in range(3):
+                if kx + ky + kz == 0:
+                    continue
+                a = rng.normal()
+                phase = rng.uniform(0, 2 * math.pi)
+                b += a * torch.cos(math.pi * (kx * x / max(nx, 1) + ky * y / max(ny, 1)
+                                              + kz * z / max(nz, 1)) + phase)
+    return b / max(float(b.abs().max()), 1e-12)
 
 
 def _streaks(rng, shape, n_lines=6, amp=60.0):
@@ -424,6 +441,69 @@ def _generate(name: str, index: int = 0, shape: Optional[Tuple[int, int, int]] =
                 lam=[cfg.lam] * len(mask_names))
 
 
+def make_case_device(name: str, index: int = 0, shape: Optional[Tuple[int, int, int]] = None,
+                     masks: Optional[Sequence[str]] = None, device="cuda") -> Case:
+    """``make_case`` evaluated with torch on ``device``: the same anatomy,
+    bumps (the same NumPy draws) and deformation model, for volumes too large
+    to build on the host in reasonable time.  The image noise comes from
+    torch's generator seeded with the case seed, so the images are not the
+    host case's bit for bit.  Fields are device tensors: static / moving
+    float32 [nz,ny,nx], masks uint8 [k,nz,ny,nx], u_gt float32 [3,...]."""
+    cfg = CONFIGS[name]
+    shape = tuple(int(s) for s in (shape or cfg.shape))
+    seed = 1000 * cfg.number + int(index)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ratio = min(shape[a] / cfg.shape[a] for a in range(3))
+    cap = max(cfg.cap * ratio, 1.0)
+    bumps = _make_bumps(rng, cfg, shape, cap)
+    bumps, u_gt = _scale_bumps(bumps, shape, cap, device)
+    w = _invert(bumps, shape, device=device)
+    x, y, z = _grid(shape, device)
+    mx, my, mz = x + w[0], y + w[1], z + w[2]
+    del w
+    static = _paint(cfg.layers, x, y, z, shape)
+    moving = _paint(cfg.layers, mx, my, mz, shape)
+    layers = {l.name: l for l in cfg.layers}
+    mask_names = list(masks) if masks is not None else list(cfg.masks)
+    k = len(mask_names)
+    smasks = torch.empty((k,) + shape, dtype=torch.uint8, device=device)
+    mmasks = torch.empty_like(smasks)
+    signs = []
+    for i, m in enumerate(mask_names):
+        L = layers[m]
+        smasks[i] = (_layer_occupancy(L, x, y, z, shape) >= 0.5)
+        mmasks[i] = (_layer_occupancy(L, mx, my, mz, shape) >= 0.5)
+        signs.append(1 if L.hu >= _surround_hu(cfg, L) else -1)
+    body = (_layer_occupancy(layers[cfg.body], x, y, z, shape) >= 0.5).to(torch.uint8)
+    del mx, my, mz, x, y, z
+    if cfg.cbct:
+        moving = moving * (1.0 + 0.05 * _bias_field_device(rng, shape, device)) + \
+            torch.from_numpy(np.ascontiguousarray(_streaks(rng, shape))).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    static = static + cfg.noise_static * torch.randn(shape, generator=g, dtype=torch.float64, device=device)
+    moving = moving + cfg.noise_moving * torch.randn(shape, generator=g, dtype=torch.float64, device=device)
+    return Case(name=name, seed=seed, static=static.float().contiguous(), moving=moving.float().contiguous(),
+                static_masks=smasks, moving_masks=mmasks, u_gt=u_gt.float().contiguous(), body=body,
+                signs=signs, mask_names=mask_names, spacing_mm=cfg.spacing_mm,
+                levels=cfg.levels, iters=tuple(cfg.iters), lam=[cfg.lam] * k)
+
+
+def batch_mix_specs(n: int = 32, seed: int = 4000, scale: float = 1.0):
+    """The draws of ``batch_mix_cases`` without building the cases: a list of
+    (template, index, shape, mask names)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        shp = BATCH_SHAPES[int(rng.integers(len(BATCH_SHAPES)))]
+        shp = tuple(max(4, int(round(s * scale))) for s in shp)
+        tmpl = "headneck256" if rng.integers(2) == 0 else "pelvis512"
+        names = CONFIGS[tmpl].masks
+        k = int(rng.integers(2, 9))
+        out.append((tmpl, 100 + i, shp, [names[j % len(names)] for j in range(k)]))
+    return out
+
+
 def _surround_hu(cfg: Config, layer: Layer) -> float:
     """HU of the tissue a structure is embedded in (the last painted layer
     before it whose name marks a body tissue)."""
@@ -442,16 +522,9 @@ def batch_mix_cases(n: int = 32, seed: int = 4000, scale: float = 1.0) -> List[C
     """The uneven-size mix: sizes uniform over four CT shapes, 2-8 masks each
     (structures drawn from the head-and-neck and pelvic templates), bumps
     <= 10 voxels.  ``scale`` < 1 shrinks every shape (for tests)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
     out = []
-    for i in range(n):
-        shp = BATCH_SHAPES[int(rng.integers(len(BATCH_SHAPES)))]
-        shp = tuple(max(4, int(round(s * scale))) for s in shp)
-        tmpl = "headneck256" if rng.integers(2) == 0 else "pelvis512"
-        names = CONFIGS[tmpl].masks
-        k = int(rng.integers(2, 9))
-        chosen = [names[j % len(names)] for j in range(k)]
-        c = make_case(tmpl, index=100 + i, shape=shp, masks=chosen)
+    for i, (tmpl, index, shp, chosen) in enumerate(batch_mix_specs(n, seed, scale)):
+        c = make_case(tmpl, index=index, shape=shp, masks=chosen)
         c.name = f"batch{i}:{tmpl}"
         out.append(c)
     return out
