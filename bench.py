@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", default="cgdir", choices=["cgdir", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", choices=["force", "smooth", "compose"], default=None,
+    ap.add_argument("--only", choices=["force", "smooth", "compose", "iterate"], default=None,
                     help="profiling aid: launch only the named kernel (via the C ABI primitive) "
                          "on the workload's full-resolution inputs, W + K times, and print its "
                          "CUDA-event time")
@@ -627,9 +627,13 @@ def run_only_kernel(args):
     elif args.only == "smooth":
         fn = lambda ctx: ctx.smooth(u, 1.0, out=du)
         nbytes = 24 * n
-    else:
+    elif args.only == "compose":
         fn = lambda ctx: ctx.compose(u, dus, cg.CGDIR_COMPOSE, 0.0, out=du)
         nbytes = 36 * n
+    else:   # one whole iteration: force, smoothing + composite update, smoothing
+        un = torch.empty_like(u)
+        fn = lambda ctx: ctx.iterate(I0, T0, mb, sb, case.lam, case.signs, u, out=un)
+        nbytes = 95 * n
     with cg.Context(0) as ctx:
         for _ in range(args.warmup):
             fn(ctx)

@@ -96,7 +96,26 @@ struct ForceArgs {
     float lambda[kMaxMasks];
     float half_sign[kMaxMasks];   // s_i / 2
     FinishArgs fin;               // fused reduction (fin.done null = none)
+    // Two-pass force (used when wfield is set and the volume has < 2^31
+    // voxels): pass 1 writes I0~ to wfield, the corners' mask AND << 8 | OR
+    // to wstate and, where the corners disagree on bit j, P_j to
+    // pfield[j][N]; pass 2 takes the stencils from them.
+    float *wfield;
+    uint16_t *wstate;
+    float *pfield;
 };
+
+// Bytes of the two-pass force scratch for n voxels and k structures.
+inline size_t force_scratch_bytes(size_t n, int k) {
+    return n * 4 + ((n * 2 + 255) / 256) * 256 + (size_t)k * n * 4 + 512;
+}
+// Point the two-pass scratch fields of `a` into `scratch` (n voxels).
+inline void force_scratch_assign(ForceArgs &a, void *scratch, size_t n) {
+    char *p = static_cast<char *>(scratch);
+    a.wfield = reinterpret_cast<float *>(p);
+    a.wstate = reinterpret_cast<uint16_t *>(p + ((n * 4 + 255) / 256) * 256);
+    a.pfield = reinterpret_cast<float *>(p + ((n * 4 + 255) / 256) * 256 + ((n * 2 + 255) / 256) * 256);
+}
 
 // Process-wide count of kernels launched by this library (instrumentation).
 void note_launch(unsigned n = 1);
@@ -130,11 +149,13 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
                           float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr);
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
                            float *out, const int *stop_flag, cudaStream_t s);
-// Algorithm A steps 2 + 3 in one pass: out = G(du) + u(x + G(du)) (or u + G(du));
-// tmp (3N floats) is used only when the fused TMA kernel is not eligible.
+// Algorithm A steps 2 + 3: out = G(du) + u(x + G(du)) (or u + G(du)).  By
+// default G(du) goes to tmp (3N floats) and a composite-update kernel
+// follows; one_pass fuses both into one TMA kernel over all three
+// components (fewer bytes, but register-bound and slower on GB300).
 cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
                                   int nz, float *out, float *tmp, const int *stop_flag, cudaStream_t s,
-                                  int *err);
+                                  int *err, bool one_pass = false);
 cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,
                         cudaStream_t s);
 

@@ -31,6 +31,8 @@
 // ring in shared memory; the gradients of the middle plane are then read
 // from the ring.  Halo points outside the volume take the clamped index,
 // which reproduces the clamped central difference at the border.
+#include <algorithm>
+
 #include "cgdir_internal.cuh"
 #include "tma.cuh"
 
@@ -41,38 +43,50 @@ namespace {
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
-// Fixed-order block reduction of (ssd, count, max) into partial[bid].  Each
-// thread's sum covers only its own column of a z-chunk (a few dozen
-// non-negative terms), so it is kept in FP32 and widened here; everything
-// from the warp level up is FP64.
+// Block reduction of (ssd, count, max) into partial[bid].  Each thread's
+// SSD covers only its own column of a z-chunk (a few dozen non-negative
+// terms) and is kept in FP32; it enters the block sum as an exact
+// fixed-point integer (units of 2^-12 HU^2), so the in-block sum is exact
+// and independent of order and needs no FP64 arithmetic (slow on this
+// GPU).  The block total is exactly representable in FP64 and the
+// cross-block sum (finalize_block) is FP64.
+constexpr float kSsdScale = 4096.f;
+
 template <int NTHREADS>
 __device__ void block_partial(float ssd_f, int cnt_i, float mx, double *partial, int bid) {
-    double ssd = (double)ssd_f, cnt = (double)cnt_i;
-    __shared__ double rs[NTHREADS / 32], rc[NTHREADS / 32];
+    __shared__ unsigned long long rs[NTHREADS / 32];
+    __shared__ double rd[NTHREADS / 32];
+    __shared__ int rc[NTHREADS / 32];
     __shared__ float rm[NTHREADS / 32];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    ssd = warp_sum(ssd);
-    cnt = warp_sum(cnt);
+    // beyond 2^40 HU^2 per thread the fixed-point block sum could overflow:
+    // such a block (never met by CT-range images) sums in FP64 instead
+    const bool wide = __syncthreads_or(!(ssd_f <= 1.0995e12f));
+    unsigned long long q = wide ? 0ull : __float2ull_rn(ssd_f * kSsdScale);
+    double d = wide ? (double)ssd_f : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (wide) d += __shfl_xor_sync(0xffffffffu, d, o);
+        else q += __shfl_xor_sync(0xffffffffu, q, o);
+        cnt_i += __shfl_xor_sync(0xffffffffu, cnt_i, o);
+    }
     mx = warp_max(mx);
-    if ((tid & 31) == 0) { rs[tid >> 5] = ssd; rc[tid >> 5] = cnt; rm[tid >> 5] = mx; }
+    if ((tid & 31) == 0) { rs[tid >> 5] = q; rd[tid >> 5] = d; rc[tid >> 5] = cnt_i; rm[tid >> 5] = mx; }
     __syncthreads();
     if (tid == 0) {
-        double s = 0, c = 0;
+        unsigned long long s = 0;
+        double sd = 0.0;
+        long long c = 0;
         float m = 0.f;
-        for (int w = 0; w < NTHREADS / 32; ++w) { s += rs[w]; c += rc[w]; m = fmaxf(m, rm[w]); }
-        partial[(size_t)bid * kPartialStride + 0] = s;
-        partial[(size_t)bid * kPartialStride + 1] = c;
+        for (int w = 0; w < NTHREADS / 32; ++w) { s += rs[w]; sd += rd[w]; c += rc[w]; m = fmaxf(m, rm[w]); }
+        partial[(size_t)bid * kPartialStride + 0] = wide ? sd : (double)s * (1.0 / (double)kSsdScale);
+        partial[(size_t)bid * kPartialStride + 1] = (double)c;
         partial[(size_t)bid * kPartialStride + 2] = (double)m;
         partial[(size_t)bid * kPartialStride + 3] = 0.0;
     }
@@ -98,7 +112,20 @@ __device__ void finalize_block(const double *__restrict__ partial, int nblocks, 
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nt = blockDim.x * blockDim.y;
     double s = 0.0, c = 0.0, m = 0.0;
-    for (int b = tid; b < nblocks; b += nt) {
+    // four partials in flight per thread, summed in the same (ascending) order
+    constexpr int U = 4;
+    int b = tid;
+    for (; b + (U - 1) * nt < nblocks; b += U * nt) {
+        double3 v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const double *p = partial + (size_t)(b + q * nt) * kPartialStride;
+            v[q] = make_double3(__ldcg(p), __ldcg(p + 1), __ldcg(p + 2));
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) { s += v[q].x; c += v[q].y; m = fmax(m, v[q].z); }
+    }
+    for (; b < nblocks; b += nt) {
         s += __ldcg(partial + (size_t)b * kPartialStride + 0);
         c += __ldcg(partial + (size_t)b * kPartialStride + 1);
         m = fmax(m, __ldcg(partial + (size_t)b * kPartialStride + 2));
@@ -269,6 +296,290 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
     }
     if (a.partial) {
         block_partial<NT>(ssd, cnt, mx, a.partial,
+                          (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+        if (a.fin.done) finish_if_last(a.partial, gridDim.x * gridDim.y * gridDim.z, a.fin);
+    }
+}
+
+
+// ---- two-pass version --------------------------------------------------------
+// Pass 1 (k_warp_pass): one thread per voxel, no halo and no barrier, so the
+// eight independent corner gathers of many voxels are in flight at once.  It
+// writes I0~, and for the structure terms the AND / OR of the corners' mask
+// bits; P_j is stored only where the corners disagree on bit j -- elsewhere
+// it is bit_j (I0~ + offset), rebuilt in pass 2 from I0~ and the bits.
+// Pass 2 (k_force_pass): each thread marches its (x, y) column along z with
+// the z-1, z, z+1 values in registers and the x / y neighbours from L1,
+// forms the gradients, Eq. 7 and du, and the RMS-ID partials.  Pass 1 costs
+// 6 + 4k bytes per voxel of extra traffic (written, then read once), but
+// both passes keep all warps busy instead of waiting at per-plane barriers.
+// The eight corners of one interpolation point, loaded (pass 1).
+template <typename IT>
+struct CornerSet {
+    float c[8];
+    unsigned m[8];
+    float wx, wy, wz;
+};
+
+// Clamp x + u, find the corners and issue their loads (texels when the
+// structure terms are on and texels exist, else image values and mask bits).
+template <bool CONTOUR, typename IT>
+__device__ __forceinline__ void corner_load(const ForceArgs &a, const float *__restrict__ u, int x, int y,
+                                            int z, int i, int N, CornerSet<IT> &cs) {
+    using TT = typename TexOf<IT>::type;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny;
+    const float px = fminf(fmaxf((float)x + __ldg(u + i), 0.f), (float)(nx - 1));
+    const float py = fminf(fmaxf((float)y + __ldg(u + N + i), 0.f), (float)(ny - 1));
+    const float pz = fminf(fmaxf((float)z + __ldg(u + 2 * N + i), 0.f), (float)(nz - 1));
+    const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+    cs.wx = px - fx; cs.wy = py - fy; cs.wz = pz - fz;
+    const int dx = ix < nx - 1 ? 1 : 0, dy = iy < ny - 1 ? nx : 0, dz = iz < nz - 1 ? nxy : 0;
+    const int b0 = iz * nxy + iy * nx + ix;
+    const int o[8] = {0, dx, dy, dy + dx, dz, dz + dx, dz + dy, dz + dy + dx};
+    if (CONTOUR && a.mtex != nullptr) {
+        const TT *__restrict__ q0 = static_cast<const TT *>(a.mtex) + b0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tex_unpack<IT>(__ldg(q0 + o[q]), cs.c[q], cs.m[q]);
+    } else {
+        const IT *__restrict__ q0 = static_cast<const IT *>(a.I0) + b0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cs.c[q] = ld_img<IT>(q0 + o[q]);
+        if (CONTOUR) {
+            const uint8_t *__restrict__ r0 = a.mbits + b0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cs.m[q] = __ldg(r0 + o[q]);
+        }
+    }
+}
+
+// Interpolate I0~ from the loaded corners, write it, the corner bits'
+// AND / OR and, where they disagree, P_j.
+template <bool CONTOUR, typename IT>
+__device__ __forceinline__ void corner_finish(const ForceArgs &a, int i, int N, const CornerSet<IT> &cs) {
+    const float wx = cs.wx, wy = cs.wy, wz = cs.wz;
+    const float *c = cs.c;
+    const float e00 = fmaf(wx, c[1] - c[0], c[0]), e10 = fmaf(wx, c[3] - c[2], c[2]);
+    const float e01 = fmaf(wx, c[5] - c[4], c[4]), e11 = fmaf(wx, c[7] - c[6], c[6]);
+    const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
+    a.wfield[i] = fmaf(wz, f1 - f0, f0);
+    if (CONTOUR) {
+        const unsigned *m = cs.m;
+        const unsigned andb = m[0] & m[1] & m[2] & m[3] & m[4] & m[5] & m[6] & m[7];
+        const unsigned orb = m[0] | m[1] | m[2] | m[3] | m[4] | m[5] | m[6] | m[7];
+        a.wstate[i] = (uint16_t)((andb << 8) | orb);
+        unsigned mixed = orb & ~andb;
+        if (mixed) {
+            const float off = a.offset;
+            const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
+            float q[8];
+            q[0] = ax * ay * az * (c[0] + off); q[1] = wx * ay * az * (c[1] + off);
+            q[2] = ax * wy * az * (c[2] + off); q[3] = wx * wy * az * (c[3] + off);
+            q[4] = ax * ay * wz * (c[4] + off); q[5] = wx * ay * wz * (c[5] + off);
+            q[6] = ax * wy * wz * (c[6] + off); q[7] = wx * wy * wz * (c[7] + off);
+            while (mixed) {
+                const int j = __ffs(mixed) - 1;
+                mixed &= mixed - 1u;
+                float pj = 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) pj += ((m[t] >> j) & 1u) ? q[t] : 0.f;
+                a.pfield[j * N + i] = pj;
+            }
+        }
+    }
+}
+
+template <bool CONTOUR, typename IT>
+__global__ void __launch_bounds__(NT, 4) k_warp_pass(ForceArgs a, int zw) {
+    if (a.stop_flag && *a.stop_flag) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const int nxy = nx * ny, N = nxy * nz;
+    const int zb = blockIdx.z * zw, ze = min(zb + zw, nz);
+    const float *__restrict__ u = a.u;
+    // two planes at a time: both points' 16 corner loads are in flight together
+    int z = zb;
+    for (; z + 1 < ze; z += 2) {
+        const int i0 = z * nxy + y * nx + x, i1 = i0 + nxy;
+        CornerSet<IT> c0, c1;
+        corner_load<CONTOUR, IT>(a, u, x, y, z, i0, N, c0);
+        corner_load<CONTOUR, IT>(a, u, x, y, z + 1, i1, N, c1);
+        corner_finish<CONTOUR, IT>(a, i0, N, c0);
+        corner_finish<CONTOUR, IT>(a, i1, N, c1);
+    }
+    if (z < ze) {
+        const int i0 = z * nxy + y * nx + x;
+        CornerSet<IT> c0;
+        corner_load<CONTOUR, IT>(a, u, x, y, z, i0, N, c0);
+        corner_finish<CONTOUR, IT>(a, i0, N, c0);
+    }
+}
+
+// Sums over a set m of structures (bit j = structure j), one table entry
+// per m: Lam = sum lambda_j, H1 = sum lambda_j h_j, H2 = sum lambda_j
+// (2 h_j + h_j^2), H3 = sum lambda_j h_j (1 + h_j), with h_j = s_j / 2.
+// For a structure whose bits agree over the stencil (b_j: P_j =
+// b_j (I0~ + offset); c_j = 1 + h_j b_j; n_j its static bit) the Eq. 7 terms
+// are a_j = |g| c_j and r_j = r0 + h_j d_j with d_j = n_j T' - b_j J
+// (T' = T0 + offset, J = I0~ + offset), so over a set U of such structures
+//   sum lambda_j a_j r_j = |g| (r0 (Lam[U] + H1[b]) + (T' - J) H3[n & b]
+//                               + T' H1[n & ~b] - J H3[b & ~n])
+//   sum lambda_j a_j^2  = |g|^2 (Lam[U] + H2[b])
+// (b, n restricted to U): table reads instead of a loop over the
+// structures.  Identical images and masks give exactly r0 = 0, T' = J and
+// n = b, hence exactly zero.
+struct ContourTables {
+    float lam[256], h1[256], h2[256], h3[256];
+};
+
+__device__ __forceinline__ void build_tables(const ForceArgs &a, ContourTables &t, int tid) {
+    for (int m = tid; m < 256; m += NT) {
+        float L = 0.f, A1 = 0.f, A2 = 0.f, A3 = 0.f;
+        for (int j = 0; j < a.k; ++j) {
+            if ((m >> j) & 1) {
+                const float l = a.lambda[j], h = a.half_sign[j];
+                L += l;
+                A1 += l * h;
+                A2 += l * (2.f * h + h * h);
+                A3 += l * h * (1.f + h);
+            }
+        }
+        t.lam[m] = L; t.h1[m] = A1; t.h2[m] = A2; t.h3[m] = A3;
+    }
+}
+
+// P_j at a stencil point from pass 1's outputs.
+__device__ __forceinline__ float p_at(const ForceArgs &a, int j, int N, int idx, float w, unsigned st) {
+    const unsigned andb = st >> 8, orb = st & 0xffu;
+    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldg(a.pfield + j * N + idx);
+    return ((andb >> j) & 1u) ? w + a.offset : 0.f;
+}
+
+// Loads of one plane of pass 2 for one thread's column.
+template <bool CONTOUR, typename IT>
+struct PlaneLoads {
+    float wp, wxm, wxp, wym, wyp, t;
+    unsigned sp, sxm, sxp, sym, syp, sb, ur;
+};
+
+// Issue every load of plane z (centre index ic) at once: one memory
+// latency per plane, hidden behind the previous plane's arithmetic.
+template <bool CONTOUR, typename IT>
+__device__ __forceinline__ void plane_load(const ForceArgs &a, int ic, int ip, int oxm, int oxp, int oym, int oyp,
+                                           PlaneLoads<CONTOUR, IT> &L) {
+    const float *__restrict__ W = a.wfield;
+    L.wp = __ldg(W + ip);
+    L.wxm = __ldg(W + ic + oxm); L.wxp = __ldg(W + ic + oxp);
+    L.wym = __ldg(W + ic + oym); L.wyp = __ldg(W + ic + oyp);
+    L.t = ld_img<IT>(static_cast<const IT *>(a.T0) + ic);
+    L.ur = a.uroi ? __ldg(a.uroi + ic) : 1u;
+    if (CONTOUR) {
+        const uint16_t *__restrict__ S = a.wstate;
+        L.sp = __ldg(S + ip);
+        L.sxm = __ldg(S + ic + oxm); L.sxp = __ldg(S + ic + oxp);
+        L.sym = __ldg(S + ic + oym); L.syp = __ldg(S + ic + oyp);
+        L.sb = __ldg(a.sbits + ic);
+    }
+}
+
+template <bool CONTOUR, typename IT>
+__global__ void __launch_bounds__(NT) k_force_pass(ForceArgs a, int zchunk) {
+    if (a.stop_flag && *a.stop_flag) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    const int nxy = nx * ny, N = nxy * nz;
+    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
+    float ssd = 0.f, mx = 0.f;
+    int cnt = 0;
+    __shared__ ContourTables tab;
+    if (CONTOUR) {
+        build_tables(a, tab, threadIdx.y * TX + threadIdx.x);
+        __syncthreads();
+    }
+    if (x < nx && y < ny) {
+        const float off = a.offset;
+        float *__restrict__ du = a.du;
+        const int col = y * nx + x;
+        const int oxm = x > 0 ? -1 : 0, oxp = x < nx - 1 ? 1 : 0;
+        const int oym = y > 0 ? -nx : 0, oyp = y < ny - 1 ? nx : 0;
+        int ic = zb * nxy + col;
+        int im = (zb > 0 ? zb - 1 : 0) * nxy + col;
+        float Wm = __ldg(a.wfield + im), Wc = __ldg(a.wfield + ic);
+        unsigned Sm = 0, Sc = 0;
+        if (CONTOUR) { Sm = __ldg(a.wstate + im); Sc = __ldg(a.wstate + ic); }
+        PlaneLoads<CONTOUR, IT> cur, nxt;
+        plane_load<CONTOUR, IT>(a, ic, zb < nz - 1 ? ic + nxy : ic, oxm, oxp, oym, oyp, cur);
+        for (int z = zb; z < ze; ++z, ic += nxy) {
+            const int ip = z < nz - 1 ? ic + nxy : ic;
+            if (z + 1 < ze)        // prefetch the next plane
+                plane_load<CONTOUR, IT>(a, ic + nxy, z + 1 < nz - 1 ? ic + 2 * nxy : ic + nxy, oxm, oxp, oym,
+                                        oyp, nxt);
+            const float Wp = cur.wp, Wxm = cur.wxm, Wxp = cur.wxp, Wym = cur.wym, Wyp = cur.wyp;
+            const float gxv = 0.5f * (Wxp - Wxm), gyv = 0.5f * (Wyp - Wym), gzv = 0.5f * (Wp - Wm);
+            const float T = cur.t;
+            const float w0 = Wc;
+            const float r0 = T - w0;
+            if (a.warped) a.warped[ic] = w0;
+            const float g2 = gxv * gxv + gyv * gyv + gzv * gzv;
+            float dux = 0.f, duy = 0.f, duz = 0.f;
+            const unsigned Sp = CONTOUR ? cur.sp : 0u;
+            if (g2 != 0.f) {
+                const float inv = g2 > 1e-30f ? rsqrtf(g2) : 1.f / sqrtf(g2);
+                const float gn = g2 * inv;
+                const float nxv = gxv * inv, nyv = gyv * inv, nzv = gzv * inv;
+                float num = gn * r0, den = gn * gn;
+                if (CONTOUR) {
+                    const unsigned Sxm = cur.sxm, Sxp = cur.sxp, Sym = cur.sym, Syp = cur.syp, sb = cur.sb;
+                    const float Toff = T + off;
+                    const unsigned A = (Sc & Sxm & Sxp & Sym & Syp & Sm & Sp) >> 8;
+                    const unsigned O = (Sc | Sxm | Sxp | Sym | Syp | Sm | Sp) & 0xffu;
+                    const unsigned kmask = (1u << a.k) - 1u;
+                    unsigned mixed = O & ~A & kmask;
+                    {
+                        const unsigned U = kmask & ~mixed, bU = A & U, nU = sb & U;
+                        const float J = w0 + off;
+                        const float cr = 1.f + tab.lam[U] + tab.h1[bU];
+                        float cn = r0 * cr;
+                        cn = fmaf(Toff - J, tab.h3[nU & bU], cn);
+                        cn = fmaf(Toff, tab.h1[nU & ~bU], cn);
+                        cn = fmaf(-J, tab.h3[bU & ~nU], cn);
+                        num = gn * cn;
+                        den = gn * gn * (1.f + tab.lam[U] + tab.h2[bU]);
+                    }
+                    // near a structure border: P_j from pass 1 at the stencil points
+                    while (mixed) {
+                        const int j = __ffs(mixed) - 1;
+                        mixed &= mixed - 1u;
+                        const float hs = a.half_sign[j];
+                        const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
+                        const float dPx = 0.5f * (p_at(a, j, N, ic + oxp, Wxp, Sxp) - p_at(a, j, N, ic + oxm, Wxm, Sxm));
+                        const float dPy = 0.5f * (p_at(a, j, N, ic + oyp, Wyp, Syp) - p_at(a, j, N, ic + oym, Wym, Sym));
+                        const float dPz = 0.5f * (p_at(a, j, N, ip, Wp, Sp) - p_at(a, j, N, im, Wm, Sm));
+                        const float aj = gn + hs * (dPx * nxv + dPy * nyv + dPz * nzv);
+                        const float rj = r0 + hs * (inside - p_at(a, j, N, ic, w0, Sc));
+                        num = fmaf(a.lambda[j] * aj, rj, num);
+                        den = fmaf(a.lambda[j] * aj, aj, den);
+                    }
+                }
+                const float v = __fdividef(num, den + r0 * r0);
+                dux = v * nxv; duy = v * nyv; duz = v * nzv;
+            }
+            du[ic] = dux;
+            du[N + ic] = duy;
+            du[2 * N + ic] = duz;
+            if (cur.ur) {
+                ssd = fmaf(r0, r0, ssd);
+                cnt += 1;
+            }
+            mx = fmaxf(mx, dux * dux + duy * duy + duz * duz);
+            Wm = Wc; Wc = Wp; im = ic;
+            if (CONTOUR) { Sm = Sc; Sc = Sp; }
+            cur = nxt;
+        }
+    }
+    if (a.partial) {
+        block_partial<NT>(ssd, cnt, sqrtf(mx), a.partial,
                           (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
         if (a.fin.done) finish_if_last(a.partial, gridDim.x * gridDim.y * gridDim.z, a.fin);
     }
@@ -609,6 +920,12 @@ int force_default_zchunk(int nx, int ny, int nz) {
     return pick_zchunk(nz, (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY), 4, 2);
 }
 
+// z chunks of pass 1 of the two-pass force: short, so the grid is several
+// waves deep.
+static int two_pass_zchunk(int nx, int ny, int nz) {
+    return pick_zchunk(nz, (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY), 8, 4);
+}
+
 size_t force_partial_count(int nx, int ny, int nz, int zchunk) {
     return (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zchunk - 1) / zchunk);
 }
@@ -618,6 +935,21 @@ static cudaError_t launch_force_t(const ForceArgs &a, int zchunk, dim3 grid, dim
                                   int *err) {
     const bool contour = a.contour && a.k > 0;
     const size_t N = (size_t)a.nx * a.ny * a.nz;
+    if (a.wfield != nullptr && N < (size_t)1 << 31) {
+        const int zc = two_pass_zchunk(a.nx, a.ny, a.nz);
+        dim3 g(grid.x, grid.y, (a.nz + zc - 1) / zc);
+        // pass 2 marches the caller's (longer) z chunks: fewer CTAs, so fewer
+        // end-of-block fences before the fused reduction
+        if (contour) {
+            k_warp_pass<true, IT><<<g, block, 0, s>>>(a, zc);
+            k_force_pass<true, IT><<<grid, block, 0, s>>>(a, zchunk);
+        } else {
+            k_warp_pass<false, IT><<<g, block, 0, s>>>(a, zc);
+            k_force_pass<false, IT><<<grid, block, 0, s>>>(a, zchunk);
+        }
+        note_launch(2);
+        return cudaGetLastError();
+    }
     if (err != nullptr && N < (size_t)1 << 31 && (!contour || a.mtex != nullptr)) {
         ForceMaps m;
         const uint64_t du4[4] = {(uint64_t)a.nx, (uint64_t)a.ny, (uint64_t)a.nz, 3};
@@ -657,6 +989,7 @@ cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaS
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
     dim3 block(TX, TY);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+
     if (a.img_dtype == CGDIR_F16) return launch_force_t<__half>(a, zchunk, grid, block, s, err);
     if (a.img_dtype == CGDIR_BF16) return launch_force_t<__nv_bfloat16>(a, zchunk, grid, block, s, err);
     return launch_force_t<float>(a, zchunk, grid, block, s, err);

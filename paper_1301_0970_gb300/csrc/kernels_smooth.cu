@@ -349,21 +349,19 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
     }
 }
 
-__global__ void k_copy(const float *__restrict__ in, float *__restrict__ out, size_t n,
-                       const int *stop_flag) {
+// Composite update u_new = du + u(x + du) (trilinear, clamped) or u + du,
+// one voxel per thread along x-y tiles marching a few planes in z.
+__global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict__ u, const float *__restrict__ du,
+                                                         int mode, int nx, int ny, int nz, int zc,
+                                                         float *__restrict__ out, const int *stop_flag) {
     if (stop_flag && *stop_flag) return;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        out[i] = in[i];
-}
-
-// u_new(x) = du(x) + u(x + du(x)) (trilinear, clamped), or u + du.
-__global__ void k_compose(const float *__restrict__ u, const float *__restrict__ du, int mode,
-                          int nx, int ny, int nz, float *__restrict__ out, const int *stop_flag) {
-    if (stop_flag && *stop_flag) return;
-    const size_t N = (size_t)nx * ny * nz;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (size_t)gridDim.x * blockDim.x) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const int zb = blockIdx.z * zc, ze = min(zb + zc, nz);
+    const size_t nxy = (size_t)nx * ny, N = nxy * nz;
+    const float fxmax = (float)(nx - 1), fymax = (float)(ny - 1), fzmax = (float)(nz - 1);
+    for (int z = zb; z < ze; ++z) {
+        const size_t i = (size_t)z * nxy + (size_t)y * nx + x;
         const float dx = __ldg(du + i), dy = __ldg(du + N + i), dz = __ldg(du + 2 * N + i);
         if (mode == CGDIR_ADDITIVE) {
             out[i] = __ldg(u + i) + dx;
@@ -371,23 +369,30 @@ __global__ void k_compose(const float *__restrict__ u, const float *__restrict__
             out[2 * N + i] = __ldg(u + 2 * N + i) + dz;
             continue;
         }
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
-        const Corners c = corners((float)x + dx, (float)y + dy, (float)z + dz, nx, ny, nz);
-        float ax = 0.f, ay = 0.f, az = 0.f;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int cx = (q & 1) ? c.x1 : c.x0, cy = (q & 2) ? c.y1 : c.y0, cz = (q & 4) ? c.z1 : c.z0;
-            const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
-                            ((q & 4) ? c.wz : 1.f - c.wz);
-            const size_t ci = vox(cx, cy, cz, nx, ny);
-            ax = fmaf(w, __ldg(u + ci), ax);
-            ay = fmaf(w, __ldg(u + N + ci), ay);
-            az = fmaf(w, __ldg(u + 2 * N + ci), az);
-        }
+        const float px = fminf(fmaxf((float)x + dx, 0.f), fxmax);
+        const float py = fminf(fmaxf((float)y + dy, 0.f), fymax);
+        const float pz = fminf(fmaxf((float)z + dz, 0.f), fzmax);
+        const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+        const float wx = px - fx, wy = py - fy, wz = pz - fz;
+        const int ddx = ix < nx - 1 ? 1 : 0, ddy = iy < ny - 1 ? nx : 0;
+        const size_t ddz = iz < nz - 1 ? nxy : 0;
+        const size_t b0 = (size_t)iz * nxy + (size_t)iy * nx + ix;
+        const float ax = trilinear_at(u, b0, ddx, ddy, (int)ddz, wx, wy, wz);
+        const float ay = trilinear_at(u + N, b0, ddx, ddy, (int)ddz, wx, wy, wz);
+        const float az = trilinear_at(u + 2 * N, b0, ddx, ddy, (int)ddz, wx, wy, wz);
         out[i] = dx + ax;
         out[N + i] = dy + ay;
         out[2 * N + i] = dz + az;
     }
+}
+
+__global__ void k_copy(const float *__restrict__ in, float *__restrict__ out, size_t n,
+                       const int *stop_flag) {
+    if (stop_flag && *stop_flag) return;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
 }
 
 // z chunk of the smoothing kernels: about two waves of resident CTAs (4 per
@@ -478,14 +483,14 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
 
 cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
                                   int nz, float *out, float *tmp, const int *stop_flag, cudaStream_t s,
-                                  int *err) {
+                                  int *err, bool one_pass) {
     const Taps t = gauss_taps(sigma);
-    if (t.r > 0 && err != nullptr) {
+    if (one_pass && t.r > 0 && err != nullptr) {
         bool launched = false;
         cudaError_t e = smooth_tma<3, true>(du, u, mode, out, 3, t, nx, ny, nz, stop_flag, err, s, &launched);
         if (e != cudaSuccess || launched) return e;
     }
-    // unfused: smooth du into tmp, then compose
+    // smooth du into tmp, then compose
     cudaError_t e = launch_smooth(du, 3, sigma, nx, ny, nz, tmp, stop_flag, s, err);
     if (e != cudaSuccess) return e;
     return launch_compose(u, tmp, mode, nx, ny, nz, out, stop_flag, s);
@@ -493,8 +498,10 @@ cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, flo
 
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
                            float *out, const int *stop_flag, cudaStream_t s) {
-    const size_t N = (size_t)nx * ny * nz;
-    k_compose<<<flat_grid(N), 256, 0, s>>>(u, du, mode, nx, ny, nz, out, stop_flag);
+    const long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+    const int zc = pick_zchunk(nz, tiles, 8, 4);
+    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + zc - 1) / zc), block(TX, TY);
+    k_compose_tiles<<<grid, block, 0, s>>>(u, du, mode, nx, ny, nz, zc, out, stop_flag);
     note_launch();
     return cudaGetLastError();
 }

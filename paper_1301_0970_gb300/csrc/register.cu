@@ -58,14 +58,15 @@ struct RegPlan {
     int *meta = nullptr;
     uint8_t *rowdist = nullptr;
     void *stage = nullptr;
+    void *fscr = nullptr;              // two-pass force scratch (null: one-pass kernels)
     unsigned long long generation = 0;
     // the slot buffers this plan needs: name and bytes (see plan_prepare)
-    enum { B_IMG, B_BITS, B_TEX, B_FIELDS, B_PARTIAL, B_STATE, B_ROWDIST, B_STAGE, B_COUNT };
+    enum { B_IMG, B_BITS, B_TEX, B_FIELDS, B_PARTIAL, B_STATE, B_ROWDIST, B_STAGE, B_FSCR, B_COUNT };
     size_t need[B_COUNT] = {};
 };
 
 const char *const kBufName[RegPlan::B_COUNT] = {"img", "bits", "tex", "fields", "partial", "state", "rowdist",
-                                                "stage"};
+                                                "stage", "fscr"};
 
 // Bytes the slot's buffers must grow by to hold plan `pl` (ws_get rounding).
 size_t plan_growth(const RegPlan &pl, const WsSet &ws) {
@@ -185,6 +186,8 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
                             (M->where == CGDIR_HOST && M->dtype != pl.sdt) ||
                             (k > 0 && (SM->where == CGDIR_HOST || MM->where == CGDIR_HOST));
     pl.need[RegPlan::B_STAGE] = need_stage ? std::max(Nf * 4, (size_t)k * Nf) : 0;
+    // two-pass force scratch (sized for the finest level, reused by every level)
+    pl.need[RegPlan::B_FSCR] = (ctx->plain_kernels || ctx->fused_force) ? 0 : force_scratch_bytes(Nf, k);
     return CGDIR_OK;
 }
 
@@ -215,6 +218,7 @@ int plan_prepare(cgdir_ctx *ctx, Slot &sl, RegPlan &pl, cudaStream_t s) {
     pl.meta = (int *)((char *)p_state + (size_t)L * pl.hcap * sizeof(double));
     pl.rowdist = (uint8_t *)p_rowdist;
     pl.stage = p_stage;
+    pl.fscr = p[RegPlan::B_FSCR];
     pl.ufinal = ((L - 1 - pl.first) % 2 == 0) ? pl.ua : pl.ub;
 
     // images (finest level), converted to the storage type where needed
@@ -318,6 +322,7 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
         a.u = ucur; a.du = pl.du; a.warped = nullptr; a.partial = pl.partial; a.stop_flag = flags + l;
         a.nx = lx; a.ny = ly; a.nz = lz;
         a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
+        if (pl.fscr) force_scratch_assign(a, pl.fscr, pl.Nl[l]);
         const int zc = force_default_zchunk(lx, ly, lz);
         const int cap = P->iters[l];
         a.fin.done = done + l;
@@ -332,7 +337,7 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
             { ProfScope ps(prof, m, s, CGDIR_K_FORCE, l); CK(launch_force(a, zc, &nb, s, kerr(ctx))); }
             { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3
               CK(launch_smooth_compose(pl.du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, pl.du2, uoth,
-                                       flags + l, s, kerr(ctx))); }
+                                       flags + l, s, kerr(ctx), ctx->fused_force)); }
             { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_U, l);    // step 4
               CK(launch_smooth(pl.du2, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx))); }
         }
@@ -352,7 +357,7 @@ std::string plan_key(cgdir_ctx *ctx, const RegPlan &pl) {
         key, sizeof key, "%d %d %d|%d|%d %d %.9g %.9g %d %u %d %.17g %.17g %.17g %.17g %.17g %.9g %d %d %llu %u %d|",
         pl.nx, pl.ny, pl.nz, pl.L, pl.k, pl.first, P->sigma_fluid, P->sigma_diff, P->compose_mode,
         P->contour_level_mask, P->stop_mode, P->eps, P->spacing_mm[0], P->spacing_mm[1], P->spacing_mm[2],
-        P->margin_mm, P->intensity_offset, (int)ctx->plain_kernels, pl.maxcap, pl.generation, ctx->prof_mask, pl.sdt);
+        P->margin_mm, P->intensity_offset, (int)ctx->plain_kernels + 2 * (int)ctx->fused_force, pl.maxcap, pl.generation, ctx->prof_mask, pl.sdt);
     std::string s(key, (size_t)len);
     for (int l = 0; l < pl.L; ++l) s += std::to_string(P->iters[l]) + ",";
     for (int j = 0; j < pl.k; ++j) {

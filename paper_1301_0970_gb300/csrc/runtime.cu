@@ -306,6 +306,7 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     }
     const char *kern = std::getenv("CGDIR_KERNELS");
     c->plain_kernels = kern && std::strcmp(kern, "plain") == 0;
+    c->fused_force = kern && std::strcmp(kern, "fused") == 0;
     const char *gr = std::getenv("CGDIR_GRAPHS");
     c->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -379,6 +380,12 @@ static int force_impl(cgdir_ctx *ctx, const ForceArgs &a, double *stats_host) {
         TRY(ws_get(ctx, "force_tex", N * tex_elem_size(a.img_dtype), &tex));
         CK(launch_make_texels(a.I0, a.img_dtype, a.mbits, N, tex, ctx->stream));
         b.mtex = tex;
+    }
+    if (!ctx->plain_kernels && !ctx->fused_force) {
+        const size_t N = (size_t)a.nx * a.ny * a.nz;
+        void *scr = nullptr;
+        TRY(ws_get(ctx, "force_scr", force_scratch_bytes(N, b.contour ? b.k : 0), &scr));
+        force_scratch_assign(b, scr, N);
     }
     if (stats_host) {
         TRY(ws_get(ctx, "partial", force_partial_count(a.nx, a.ny, a.nz, zc) * kPartialStride * sizeof(double), &part));
@@ -474,7 +481,7 @@ int cgdir_iterate(cgdir_ctx *ctx, const float *I0, const float *T0, const uint8_
         CK(launch_compose(u_in, du_out, compose_mode, nx, ny, nz, un, nullptr, ctx->stream));
     } else {
         CK(launch_smooth_compose(du, u_in, compose_mode, sigma_fluid, nx, ny, nz, un, (float *)t3, nullptr,
-                                 ctx->stream, kerr(ctx)));
+                                 ctx->stream, kerr(ctx), ctx->fused_force));
     }
     CK(launch_smooth(un, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx)));
     return CGDIR_OK;

@@ -85,6 +85,7 @@ struct cgdir_ctx {
     bool use_graphs = true;
     int device = 0;
     bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
+    bool fused_force = false;     // CGDIR_KERNELS=fused: one-pass TMA force kernel instead of two passes
     int *err_word = nullptr;      // device word set by a kernel whose bounded wait ran out
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on

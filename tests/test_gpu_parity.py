@@ -35,8 +35,9 @@ SHAPES = [(9, 21, 45), (1, 1, 1), (3, 8, 32), (17, 33, 70), (5, 1, 7), (9, 21, 4
 
 
 def make_context(kernels: str):
-    """A context whose kernels are the TMA ones where eligible ("tma") or the
-    plain-load ones everywhere ("plain")."""
+    """A context with the default kernels ("tma": two-pass force, TMA
+    smoothing where eligible), the one-pass TMA force kernel ("fused") or the
+    plain-load kernels everywhere ("plain")."""
     import os
     old = os.environ.get("CGDIR_KERNELS")
     os.environ["CGDIR_KERNELS"] = kernels
@@ -49,7 +50,7 @@ def make_context(kernels: str):
             os.environ["CGDIR_KERNELS"] = old
 
 
-@pytest.fixture(scope="module", params=["tma", "plain"])
+@pytest.fixture(scope="module", params=["tma", "fused", "plain"])
 def ctx(request):
     c = make_context(request.param)
     yield c
@@ -203,14 +204,16 @@ def test_force(ctx, k, contour, shape):
     assert abs(stats[2] - float(np.sqrt((ref ** 2).sum(0)).max())) <= 1e-4
 
 
-def test_force_uniform_mask_fast_path_matches_general_path():
-    """The TMA kernel's shortcut where all corners share their mask bits must
-    agree with the plain kernel's per-corner accumulation."""
+@pytest.mark.parametrize("kernels", ["tma", "fused"])
+def test_force_uniform_mask_fast_path_matches_general_path(kernels):
+    """The shortcut where all corners share their mask bits (two-pass and
+    one-pass TMA force) must agree with the plain kernel's per-corner
+    accumulation."""
     c = phantom.make_case("headneck256", shape=(16, 64, 64))
     u = (0.5 * c.u_gt).astype(np.float32)
     args = (dev(c.moving), dev(c.static), dev(pack(c.moving_masks)), dev(pack(c.static_masks)),
             [0.5] * c.k, c.signs, dev(u))
-    a = make_context("tma")
+    a = make_context(kernels)
     b = make_context("plain")
     try:
         da = host(a.force(*args))
@@ -451,7 +454,7 @@ def test_profile_reports_every_kernel_class():
 
 # ------------------------------------------------- 16-bit image storage (FP32 math)
 @pytest.mark.parametrize("storage", [cg.CGDIR_F16, cg.CGDIR_BF16])
-@pytest.mark.parametrize("kernels", ["tma", "plain"])
+@pytest.mark.parametrize("kernels", ["tma", "fused", "plain"])
 @pytest.mark.parametrize("shape", [(20, 48, 48), (13, 30, 37)])
 def test_half_storage_registration_within_a_tenth_of_a_voxel(storage, kernels, shape):
     """Images stored in FP16 / BF16, all arithmetic FP32: with FP16 storage the
