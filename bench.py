@@ -282,6 +282,7 @@ def run_cgdir(args):
 
     ctx = cg.Context(local)
     stream = torch.cuda.current_stream(dev)
+    tuning = ctx.autotune(case.shape, case.k, L)          # per-level kernel schedule
     for _ in range(args.warmup):
         ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
     torch.cuda.synchronize()
@@ -370,7 +371,12 @@ def run_cgdir(args):
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
                 "cpu_baseline": cpu, "clocks": clk.summary(),
                 "kernel_breakdown_ms": {f"{p['kernel']}@L{p['level']}": round(p["total_ms"], 4)
-                                        for p in breakdown}}
+                                        for p in breakdown},
+                "tuning": [{"shape_zyx": list(t["shape"]), "smooth": t["smooth"],
+                            "smooth_zchunk": t["smooth_zchunk"], "force_zchunk": t["force_zchunk"],
+                            "smooth_ms": round(t["smooth_ms"], 4), "force_ms": round(t["force_ms"], 4),
+                            "untuned_smooth_ms": round(t["default_smooth_ms"], 4),
+                            "untuned_force_ms": round(t["default_force_ms"], 4)} for t in tuning]}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -447,6 +453,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
     res = {}
     with cg.Context(0) as ctx:
+        ctx.set_autotune(True)        # each new level shape is tuned at its first registration
         # plain FP32, one at a time (warm-up passes capture every shape's graph)
         for _ in range(max(args.warmup, 2)):
             one_at_a_time(torch, cg, ctx, cases, stream)
@@ -570,6 +577,8 @@ def run_serve(args):
     l0 = cg.launch_count()
     with cg.Context(0, mem_budget_bytes=MIX["budget_gb"] << 30) as sctx, cg.Context(0) as pctx:
         sctx.set_max_inflight(64)
+        sctx.set_autotune(True)
+        pctx.set_autotune(True)
         everyone = (np.zeros(len(cases)), np.arange(len(cases)))
         for _ in range(2):                                   # warm-up: slots, buffers, graphs
             served(sctx, *everyone, True)

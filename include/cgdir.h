@@ -398,6 +398,39 @@ int cgdir_profile(cgdir_ctx *ctx, unsigned kernel_mask);
    number of entries written (negative status on error). */
 int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap);
 
+/* ---- autotuner (not in the paper: an execution choice) --------------------
+ * For each level shape of a pyramid it times, on synthetic data of that
+ * shape, the candidate configurations of the smoothing kernel (TMA z-march
+ * with three z-chunk lengths, 3-D shared-memory tile) and of the force
+ * stencil pass (three z-chunk lengths) on ctx's stream, and keeps the
+ * fastest.  Later registrations of those shapes use the choices (results
+ * are the same to rounding: only the launch geometry changes, except that
+ * the two smoothing kernels may differ in the last bit).  Blocking. */
+#define CGDIR_SMOOTH_MARCH 1
+#define CGDIR_SMOOTH_TILE  2
+typedef struct {
+    int   nx, ny, nz;           /* level shape                                   */
+    int   contour;              /* structure terms on at this level               */
+    int   storage_dtype;        /* CGDIR_F32 / F16 / BF16                          */
+    int   smooth_variant;       /* CGDIR_SMOOTH_MARCH / CGDIR_SMOOTH_TILE           */
+    int   smooth_zchunk;        /* z chunk of the z-march (0 = n/a)                 */
+    int   force_zchunk;         /* z chunk of the force stencil pass                */
+    float smooth_ms, force_ms;  /* best time of one launch (3-component smoothing) */
+    float default_smooth_ms, default_force_ms;   /* the untuned choice's times     */
+} cgdir_tuning;
+
+/* Tune every level of a `levels`-level pyramid whose finest level is
+   nx x ny x nz, with k structures, structure terms at the levels of
+   contour_level_mask, image storage storage_dtype (CGDIR_F32/F16/BF16) and
+   Gaussian sigma (voxels).  Errors: EINVAL, ENOMEM, ECUDA. */
+int cgdir_autotune(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int levels, unsigned contour_level_mask,
+                   int storage_dtype, float sigma);
+/* on != 0: registrations tune each level shape they have not seen before
+   they run (a few milliseconds per new shape). */
+int cgdir_set_autotune(cgdir_ctx *ctx, int on);
+/* Copy up to cap tuned shapes into out; returns how many there are. */
+int cgdir_tuning_read(const cgdir_ctx *ctx, cgdir_tuning *out, int cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,6 +58,16 @@ class cgdir_level_stats(ctypes.Structure):
                 ("rms_id", POINTER(c_double))]
 
 
+class cgdir_tuning(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("contour", c_int), ("storage_dtype", c_int),
+                ("smooth_variant", c_int), ("smooth_zchunk", c_int), ("force_zchunk", c_int),
+                ("smooth_ms", c_float), ("force_ms", c_float), ("default_smooth_ms", c_float),
+                ("default_force_ms", c_float)]
+
+
+CGDIR_SMOOTH_MARCH, CGDIR_SMOOTH_TILE = 1, 2
+
+
 class cgdir_kernel_time(ctypes.Structure):
     _fields_ = [("kernel", c_int), ("level", c_int), ("launches", c_longlong), ("total_ms", c_double)]
 
@@ -80,6 +90,9 @@ _SIGNATURES = {
     "cgdir_register": (c_int, [c_void_p, POINTER(cgdir_volume), POINTER(cgdir_volume),
                                POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
                                c_void_p, c_int, POINTER(cgdir_level_stats)]),
+    "cgdir_autotune": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_uint, c_int, c_float]),
+    "cgdir_set_autotune": (c_int, [c_void_p, c_int]),
+    "cgdir_tuning_read": (c_int, [c_void_p, POINTER(cgdir_tuning), c_int]),
     "cgdir_register_batch": (c_int, [c_void_p, c_int, POINTER(cgdir_volume), POINTER(cgdir_volume),
                                      POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
                                      POINTER(c_void_p), c_int, POINTER(cgdir_level_stats)]),
@@ -330,6 +343,31 @@ class Context:
         return [{"kernel": KERNEL_NAMES[buf[i].kernel], "level": buf[i].level,
                  "launches": int(buf[i].launches), "total_ms": float(buf[i].total_ms)}
                 for i in range(n)]
+
+    # ---- autotuner -------------------------------------------------------------
+    def autotune(self, shape, k: int, levels: int, contour_level_mask: Optional[int] = None,
+                 storage_dtype: int = CGDIR_F32, sigma: float = 1.0):
+        """Time the kernel configurations of every level shape of a pyramid
+        whose finest level is `shape` = (nz, ny, nx) and keep the fastest."""
+        nz, ny, nx = shape
+        mask = (1 << (levels - 1)) if contour_level_mask is None else contour_level_mask
+        self._check(load().cgdir_autotune(self._h, nx, ny, nz, k, levels, mask, storage_dtype, sigma),
+                    "cgdir_autotune")
+        return self.tuning()
+
+    def set_autotune(self, on: bool = True):
+        self._check(load().cgdir_set_autotune(self._h, int(bool(on))), "cgdir_set_autotune")
+
+    def tuning(self):
+        n = load().cgdir_tuning_read(self._h, None, 0)
+        buf = (cgdir_tuning * max(n, 1))()
+        n = load().cgdir_tuning_read(self._h, buf, n)
+        names = {CGDIR_SMOOTH_MARCH: "march", CGDIR_SMOOTH_TILE: "tile"}
+        return [{"shape": (b.nz, b.ny, b.nx), "contour": bool(b.contour), "storage_dtype": b.storage_dtype,
+                 "smooth": names.get(b.smooth_variant, str(b.smooth_variant)), "smooth_zchunk": b.smooth_zchunk,
+                 "force_zchunk": b.force_zchunk, "smooth_ms": b.smooth_ms, "force_ms": b.force_ms,
+                 "default_smooth_ms": b.default_smooth_ms, "default_force_ms": b.default_force_ms}
+                for b in buf[:n]]
 
     # ---- whole registration ------------------------------------------------
     def register(self, static, moving, static_masks=None, moving_masks=None, **kw):

@@ -1,0 +1,263 @@
+// Autotuner for the per-level kernel schedule (not part of the paper: an
+// execution choice).  For one pyramid level shape it times, on synthetic
+// data of that shape, the candidate launch configurations of the two
+// kernels whose best configuration depends on the shape:
+//   smoothing: the TMA z-march with its default z chunk, half and double
+//              that chunk, and the 3-D shared-memory tile kernel;
+//   force:     the stencil pass with the default z chunk, half and double.
+// The fastest of each is recorded in the context and used by every later
+// registration of that shape (and baked into its CUDA graph).
+#include "runtime_internal.hpp"
+
+#include <algorithm>
+
+using namespace cgdir;
+using namespace cgdir::rt;
+
+namespace {
+
+__device__ __forceinline__ unsigned hash3(unsigned x, unsigned y, unsigned z, unsigned s) {
+    unsigned h = x * 0x8da6b343u ^ y * 0xd8163841u ^ z * 0xcb1ab31fu ^ s * 0x165667b1u;
+    h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12; h *= 0x297a2d39u; h ^= h >> 15;
+    return h;
+}
+
+// Synthetic level: CT-like values with structure, blocky masks (so both the
+// uniform and the mixed structure paths run), displacements up to 1.5 voxels.
+template <typename IT>
+__global__ void k_tune_fill(IT *I0, IT *T0, uint8_t *mbits, uint8_t *sbits, uint8_t *uroi, float *u, int nx,
+                            int ny, int nz, int k) {
+    const size_t N = (size_t)nx * ny * nz;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+        const float base = 40.f * __sinf(0.11f * x) * __cosf(0.07f * y) + 30.f * __sinf(0.13f * z);
+        const float n0 = (float)(hash3(x, y, z, 1) & 1023u) * (50.f / 1023.f);
+        const float n1 = (float)(hash3(x, y, z, 2) & 1023u) * (50.f / 1023.f);
+        I0[i] = from_f<IT>(base + n0);
+        T0[i] = from_f<IT>(base + n1);
+        unsigned mb = 0, sb = 0;
+        for (int j = 0; j < k; ++j) {
+            if (((x / 24 + y / 24 + z / 12 + j) % 3) == 0) mb |= 1u << j;
+            if ((((x + 2) / 24 + y / 24 + z / 12 + j) % 3) == 0) sb |= 1u << j;
+        }
+        mbits[i] = (uint8_t)mb;
+        sbits[i] = (uint8_t)sb;
+        uroi[i] = 1;
+        for (int c = 0; c < 3; ++c)
+            u[c * N + i] = ((float)(hash3(x / 4, y / 4, z / 4, 10 + c) & 255u) - 127.5f) * (1.5f / 127.5f);
+    }
+}
+
+}  // namespace
+
+namespace cgdir {
+namespace rt {
+
+int force_zchunk_min(int nx, int ny, int nz) { return std::max(1, force_default_zchunk(nx, ny, nz) / 2); }
+
+static const TunedLevel *find_tuned(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
+    auto it = ctx->tuned.find(TuneKey{nx, ny, nz, contour ? 1 : 0, sdt});
+    return it == ctx->tuned.end() ? nullptr : &it->second;
+}
+
+SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
+    SmoothChoice ch;
+    if (ctx->smooth_variant != SMOOTH_AUTO) {
+        ch.variant = ctx->smooth_variant;
+        return ch;
+    }
+    if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt)) {
+        ch.variant = t->smooth_variant;
+        ch.zchunk = t->smooth_zchunk;
+    }
+    return ch;
+}
+
+int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
+    if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt))
+        if (t->force_zchunk > 0) return t->force_zchunk;
+    return force_default_zchunk(nx, ny, nz);
+}
+
+// Average time of `reps` launches of `body` after two untimed ones (ms).
+template <typename Body>
+static int time_ms(cgdir_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int reps, float *ms, Body body) {
+    cudaStream_t s = ctx->stream;
+    for (int r = 0; r < 2; ++r) CK(body(s));
+    CK(cudaEventRecord(a, s));
+    for (int r = 0; r < reps; ++r) CK(body(s));
+    CK(cudaEventRecord(b, s));
+    CK(cudaEventSynchronize(b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, a, b));
+    *ms = t / (float)reps;
+    return CGDIR_OK;
+}
+
+int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int sdt, float sigma) {
+    if (!dims_ok(nx, ny, nz) || k < 0 || k > kMaxMasks) return fail(ctx, CGDIR_EINVAL, "autotune: bad shape");
+    if (ctx->plain_kernels || ctx->fused_force) return CGDIR_OK;     // nothing to choose
+    contour = contour && k > 0;
+    DeviceGuard g(ctx->device);
+    const size_t N = (size_t)nx * ny * nz;
+    const size_t esz = img_elem_size(sdt), tsz = tex_elem_size(sdt);
+    void *img, *bits, *tex, *fields, *scr, *part, *state;
+    TRY(ws_get(ctx, "tune_img", 2 * N * esz, &img));
+    TRY(ws_get(ctx, "tune_bits", 3 * N, &bits));
+    TRY(ws_get(ctx, "tune_tex", N * tsz, &tex));
+    TRY(ws_get(ctx, "tune_fields", 3 * 3 * N * sizeof(float), &fields));
+    TRY(ws_get(ctx, "tune_scr", force_scratch_bytes(N, contour ? k : 0), &scr));
+    const size_t np = force_partial_count(nx, ny, nz, force_zchunk_min(nx, ny, nz));
+    TRY(ws_get(ctx, "tune_part", np * kPartialStride * sizeof(double), &part));
+    TRY(ws_get(ctx, "tune_state", 256, &state));
+    cudaStream_t s = ctx->stream;
+    char *I0 = (char *)img, *T0 = (char *)img + N * esz;
+    uint8_t *mb = (uint8_t *)bits, *sb = mb + N, *ur = mb + 2 * N;
+    float *u = (float *)fields, *du = u + 3 * N, *out = du + 3 * N;
+    const unsigned fg = (unsigned)std::min<size_t>((N + 255) / 256, 152 * 8);
+    if (sdt == CGDIR_F16)
+        k_tune_fill<__half><<<fg, 256, 0, s>>>((__half *)I0, (__half *)T0, mb, sb, ur, u, nx, ny, nz, k);
+    else if (sdt == CGDIR_BF16)
+        k_tune_fill<__nv_bfloat16><<<fg, 256, 0, s>>>((__nv_bfloat16 *)I0, (__nv_bfloat16 *)T0, mb, sb, ur, u, nx, ny,
+                                                      nz, k);
+    else
+        k_tune_fill<float><<<fg, 256, 0, s>>>((float *)I0, (float *)T0, mb, sb, ur, u, nx, ny, nz, k);
+    CK(cudaGetLastError());
+    if (contour) CK(launch_make_texels(I0, sdt, mb, N, tex, s));
+    CK(cudaMemsetAsync(state, 0, 256, s));
+
+    // force with the fused reduction, as in a registration
+    ForceArgs a{};
+    {
+        float lam[kMaxMasks];
+        int8_t sg[kMaxMasks];
+        for (int j = 0; j < kMaxMasks; ++j) { lam[j] = 1e-3f; sg[j] = (j & 1) ? -1 : 1; }
+        TRY(fill_force_args(ctx, a, k, lam, sg, 1000.f, contour));
+    }
+    a.I0 = I0; a.T0 = T0; a.img_dtype = sdt; a.mbits = mb; a.sbits = sb; a.uroi = ur;
+    a.mtex = contour ? tex : nullptr;
+    a.u = u; a.du = du; a.partial = (double *)part; a.stop_flag = nullptr;
+    a.nx = nx; a.ny = ny; a.nz = nz; a.contour = contour;
+    force_scratch_assign(a, scr, N);
+    double *hist = (double *)state;
+    int *meta = (int *)((char *)state + 64);
+    a.fin.done = (unsigned *)(meta + 8);
+    a.fin.st.hist = hist; a.fin.st.hist_len = meta; a.fin.st.iters_run = meta + 1; a.fin.st.stop_reason = meta + 2;
+    a.fin.st.stop_flag = meta + 3; a.fin.st.hist_cap = 1;
+    a.fin.n = 0; a.fin.cap = 1 << 30; a.fin.stop_mode = CGDIR_STOP_FIXED; a.fin.eps = 0.0;
+
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    TunedLevel best;
+    const int reps = N > ((size_t)4 << 20) ? 5 : 20;
+    int rc = CGDIR_OK;
+    {
+        const int d = force_default_zchunk(nx, ny, nz);
+        const int cand[3] = {d, std::max(1, d / 2), std::min(nz, 2 * d)};
+        float bt = 1e30f;
+        for (int ci = 0; ci < 3 && rc == CGDIR_OK; ++ci) {
+            if (ci > 0 && cand[ci] == cand[0]) continue;
+            float ms = 0.f;
+            rc = time_ms(ctx, e0, e1, reps, &ms, [&](cudaStream_t st) { return launch_force(a, cand[ci], nullptr, st, kerr(ctx)); });
+            if (ci == 0) best.default_force_ms = ms;
+            if (rc == CGDIR_OK && ms < bt) { bt = ms; best.force_zchunk = cand[ci]; best.force_ms = ms; }
+        }
+    }
+    if (rc == CGDIR_OK) {
+        float bt = 1e30f;
+        const int d = smooth_default_zchunk(nx, ny, nz, 3);
+        SmoothChoice cand[4];
+        int nc = 0;
+        if (nx % 4 == 0) {
+            cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = d;
+            if (std::max(1, d / 2) != d) { cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = std::max(1, d / 2); }
+            if (std::min(nz, 2 * d) != d) { cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = std::min(nz, 2 * d); }
+        }
+        cand[nc].variant = SMOOTH_TILE; cand[nc++].zchunk = 0;
+        const SmoothChoice dflt{smooth_auto_variant(nx, ny, nz), 0};
+        for (int ci = 0; ci < nc && rc == CGDIR_OK; ++ci) {
+            float ms = 0.f;
+            rc = time_ms(ctx, e0, e1, reps, &ms, [&](cudaStream_t st) {
+                return launch_smooth(u, 3, sigma, nx, ny, nz, out, nullptr, st, kerr(ctx), cand[ci]);
+            });
+            const bool is_default = cand[ci].variant == dflt.variant &&
+                                    (cand[ci].variant == SMOOTH_TILE || cand[ci].zchunk == d);
+            if (is_default) best.default_smooth_ms = ms;
+            if (rc == CGDIR_OK && ms < bt) {
+                bt = ms;
+                best.smooth_variant = cand[ci].variant;
+                best.smooth_zchunk = cand[ci].zchunk;
+                best.smooth_ms = ms;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(rc);
+    TRY(check_err_word(ctx));
+    // give the scratch back (a tuned shape may be large)
+    CK(cudaStreamSynchronize(s));
+    for (auto it = ctx->ws.bufs.begin(); it != ctx->ws.bufs.end();) {
+        if (it->first.rfind("tune_", 0) == 0) {
+            cudaFree(it->second.p);
+            ctx->in_use -= it->second.cap;
+            it = ctx->ws.bufs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    ctx->tuned[TuneKey{nx, ny, nz, contour ? 1 : 0, sdt}] = best;
+    ++ctx->tune_gen;
+    return CGDIR_OK;
+}
+
+}  // namespace rt
+}  // namespace cgdir
+
+extern "C" {
+
+int cgdir_autotune(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int levels, unsigned contour_level_mask,
+                   int storage_dtype, float sigma) {
+    if (!ctx) return CGDIR_EINVAL;
+    ctx->err.clear();
+    if (!dims_ok(nx, ny, nz) || levels < 1 || levels > CGDIR_MAX_LEVELS || k < 0 || k > kMaxMasks ||
+        storage_dtype < CGDIR_F32 || storage_dtype > CGDIR_BF16 || !sigma_ok(sigma))
+        return fail(ctx, CGDIR_EINVAL, "autotune: bad arguments");
+    int d[3] = {nx, ny, nz};
+    int dims[CGDIR_MAX_LEVELS][3];
+    for (int l = levels - 1; l >= 0; --l) {
+        for (int a = 0; a < 3; ++a) dims[l][a] = d[a];
+        for (int a = 0; a < 3; ++a) d[a] = (d[a] + 1) / 2;
+    }
+    for (int l = 0; l < levels; ++l)
+        TRY(tune_level(ctx, dims[l][0], dims[l][1], dims[l][2], k, (contour_level_mask >> l) & 1u, storage_dtype,
+                       sigma));
+    return CGDIR_OK;
+}
+
+int cgdir_set_autotune(cgdir_ctx *ctx, int on) {
+    if (!ctx) return CGDIR_EINVAL;
+    ctx->autotune_on = on != 0;
+    return CGDIR_OK;
+}
+
+int cgdir_tuning_read(const cgdir_ctx *ctx, cgdir_tuning *out, int cap) {
+    if (!ctx || (cap > 0 && !out)) return -CGDIR_EINVAL;
+    int n = 0;
+    for (const auto &kv : ctx->tuned) {
+        if (n < cap) {
+            cgdir_tuning &o = out[n];
+            o.nx = kv.first[0]; o.ny = kv.first[1]; o.nz = kv.first[2];
+            o.contour = kv.first[3]; o.storage_dtype = kv.first[4];
+            o.smooth_variant = kv.second.smooth_variant; o.smooth_zchunk = kv.second.smooth_zchunk;
+            o.force_zchunk = kv.second.force_zchunk;
+            o.smooth_ms = kv.second.smooth_ms; o.force_ms = kv.second.force_ms;
+            o.default_smooth_ms = kv.second.default_smooth_ms; o.default_force_ms = kv.second.default_force_ms;
+        }
+        ++n;
+    }
+    return n;
+}
+
+}  // extern "C"

@@ -143,10 +143,21 @@ size_t metric_partial_count(int nx, int ny, int nz);
 cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, int n, int cap,
                             int stop_mode, double eps, double *stats_out, cudaStream_t s);
 
+// Smoothing kernel variants: the TMA z-march (large volumes), the 3-D
+// shared-memory tile (small volumes), or chosen by size.
+enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2 };
+int smooth_auto_variant(int nx, int ny, int nz);
+// Kernel choice for one smoothing launch: variant and (z-march) z chunk, 0 = default.
+struct SmoothChoice {
+    int variant = SMOOTH_AUTO;
+    int zchunk = 0;
+};
+int smooth_default_zchunk(int nx, int ny, int nz, int ncomp);
 // err: device word set to 1 if a bounded wait inside the kernel ran out;
 // nullptr selects the plain-load kernel (no waits).
 cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int ny, int nz,
-                          float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr);
+                          float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr,
+                          SmoothChoice ch = SmoothChoice());
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
                            float *out, const int *stop_flag, cudaStream_t s);
 // Algorithm A steps 2 + 3: out = G(du) + u(x + G(du)) (or u + G(du)).  By
@@ -155,7 +166,7 @@ cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, in
 // components (fewer bytes, but register-bound and slower on GB300).
 cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
                                   int nz, float *out, float *tmp, const int *stop_flag, cudaStream_t s,
-                                  int *err, bool one_pass = false);
+                                  int *err, bool one_pass = false, SmoothChoice ch = SmoothChoice());
 cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,
                         cudaStream_t s);
 

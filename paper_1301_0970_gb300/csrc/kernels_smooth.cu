@@ -25,6 +25,7 @@
 #include "cgdir_internal.cuh"
 #include "tma.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace cgdir {
@@ -387,6 +388,74 @@ __global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict
     }
 }
 
+// ---- 3-D tile version (small volumes) ------------------------------------
+// A CTA loads a 16 x 16 x 8 output tile of one component with its R-voxel
+// halo into shared memory (clamped indices) and runs the x, y and z passes
+// there; no z march, so a small level's whole volume is filtered in one
+// short wave instead of a long chain of plane steps.
+constexpr int QX = 16, QY = 16, QZ = 8;
+
+template <int R>
+struct TileGeom {
+    static constexpr int AX = QX + 2 * R, AY = QY + 2 * R, AZ = QZ + 2 * R;
+    static constexpr int IN = AX * AY * AZ;            // input with halo
+    static constexpr int XO = QX * AY * AZ;            // after the x pass
+    static constexpr int YO = QX * QY * AZ;            // after the y pass (reuses the input buffer)
+    static constexpr size_t bytes() { return sizeof(float) * ((size_t)IN + XO); }
+};
+
+template <int R>
+__global__ void __launch_bounds__(NT) k_smooth_tile(const float *__restrict__ in, float *__restrict__ out,
+                                                    Taps taps, int nx, int ny, int nz, int tiles_z,
+                                                    const int *stop_flag) {
+    if (stop_flag && *stop_flag) return;
+    using G = TileGeom<R>;
+    constexpr int K = 2 * R + 1, AX = G::AX, AY = G::AY, AZ = G::AZ;
+    extern __shared__ float sm[];
+    float *A = sm, *B = sm + G::IN;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int comp = blockIdx.z / tiles_z, tz = blockIdx.z % tiles_z;
+    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = tz * QZ;
+    const size_t nxy = (size_t)nx * ny;
+    const float *src = in + (size_t)comp * nxy * nz;
+    for (int p = tid; p < G::IN; p += NT) {
+        const int hx = p % AX, hy = (p / AX) % AY, hz = p / (AX * AY);
+        const int gx = clampi(x0 - R + hx, 0, nx - 1), gy = clampi(y0 - R + hy, 0, ny - 1),
+                  gz = clampi(z0 - R + hz, 0, nz - 1);
+        A[p] = __ldg(src + (size_t)gz * nxy + (size_t)gy * nx + gx);
+    }
+    __syncthreads();
+    for (int p = tid; p < G::XO; p += NT) {            // x pass: [AZ][AY][QX]
+        const int ox = p % QX, r = p / QX;
+        const float *row = A + r * AX + ox;
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc = fmaf(taps.w[j], row[j], acc);
+        B[p] = acc;
+    }
+    __syncthreads();
+    for (int p = tid; p < G::YO; p += NT) {            // y pass: [AZ][QY][QX] into A
+        const int ox = p % QX, oy = (p / QX) % QY, hz = p / (QX * QY);
+        const float *colp = B + (hz * AY + oy) * QX + ox;
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc = fmaf(taps.w[j], colp[j * QX], acc);
+        A[p] = acc;
+    }
+    __syncthreads();
+    float *dst = out + (size_t)comp * nxy * nz;
+    for (int p = tid; p < QX * QY * QZ; p += NT) {      // z pass to memory
+        const int ox = p % QX, oy = (p / QX) % QY, oz = p / (QX * QY);
+        const int gx = x0 + ox, gy = y0 + oy, gz = z0 + oz;
+        if (gx >= nx || gy >= ny || gz >= nz) continue;
+        const float *colp = A + (oz * QY + oy) * QX + ox;
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc = fmaf(taps.w[j], colp[j * QX * QY], acc);
+        dst[(size_t)gz * nxy + (size_t)gy * nx + gx] = acc;
+    }
+}
+
 __global__ void k_copy(const float *__restrict__ in, float *__restrict__ out, size_t n,
                        const int *stop_flag) {
     if (stop_flag && *stop_flag) return;
@@ -412,14 +481,15 @@ unsigned flat_grid(size_t n) {
 template <int R, int NC, bool COMPOSE>
 static cudaError_t smooth_tma_r(const float *in, const float *ucomp, int mode, float *out, int ncomp,
                                 const Taps &t, int nx, int ny, int nz, const int *stop_flag, int *err,
-                                cudaStream_t s, bool *launched) {
+                                cudaStream_t s, bool *launched, int zc_override) {
     using G = SmoothGeom<R, NC>;
     CUtensorMap m;
     const uint64_t dims[4] = {(uint64_t)nx, (uint64_t)ny, (uint64_t)nz, (uint64_t)ncomp};
     const uint32_t box[4] = {(uint32_t)G::BXW, (uint32_t)G::BY, 1u, (uint32_t)NC};
     *launched = false;
     if (!encode_tensor_map(&m, in, 4, dims, box, 4)) return cudaSuccess;
-    const int zc = smooth_zchunk(nx, ny, nz, SY, NC == 1 ? ncomp : 1, NC == 1 ? 4 : 2);
+    const int zc = zc_override > 0 ? std::min(zc_override, nz)
+                                   : smooth_zchunk(nx, ny, nz, SY, NC == 1 ? ncomp : 1, NC == 1 ? 4 : 2);
     const int nchunks = (nz + zc - 1) / zc;
     dim3 grid((nx + TX - 1) / TX, (ny + SY - 1) / SY, nchunks * (NC == 1 ? ncomp : 1)), block(TX, TY);
     const size_t smem = G::bytes();
@@ -435,15 +505,41 @@ static cudaError_t smooth_tma_r(const float *in, const float *ucomp, int mode, f
 template <int NC, bool COMPOSE>
 static cudaError_t smooth_tma(const float *in, const float *ucomp, int mode, float *out, int ncomp,
                               const Taps &t, int nx, int ny, int nz, const int *stop_flag, int *err,
-                              cudaStream_t s, bool *launched) {
+                              cudaStream_t s, bool *launched, int zc = 0) {
     switch (t.r) {
-        case 1: return smooth_tma_r<1, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
-        case 2: return smooth_tma_r<2, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
-        case 3: return smooth_tma_r<3, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
-        case 4: return smooth_tma_r<4, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
-        case 5: return smooth_tma_r<5, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
-        case 6: return smooth_tma_r<6, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched);
+        case 1: return smooth_tma_r<1, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 2: return smooth_tma_r<2, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 3: return smooth_tma_r<3, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 4: return smooth_tma_r<4, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 5: return smooth_tma_r<5, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 6: return smooth_tma_r<6, NC, COMPOSE>(in, ucomp, mode, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
         default: *launched = false; return cudaErrorInvalidValue;
+    }
+}
+
+template <int R>
+static cudaError_t smooth_tile_r(const float *in, int ncomp, const Taps &t, int nx, int ny, int nz, float *out,
+                                 const int *stop_flag, cudaStream_t s) {
+    const int tz = (nz + QZ - 1) / QZ;
+    dim3 grid((nx + QX - 1) / QX, (ny + QY - 1) / QY, tz * ncomp), block(TX, TY);
+    const size_t smem = TileGeom<R>::bytes();
+    cudaError_t e = ensure_smem((const void *)k_smooth_tile<R>, smem);
+    if (e != cudaSuccess) return e;
+    k_smooth_tile<R><<<grid, block, smem, s>>>(in, out, t, nx, ny, nz, tz, stop_flag);
+    note_launch();
+    return cudaGetLastError();
+}
+
+static cudaError_t smooth_tile(const float *in, int ncomp, const Taps &t, int nx, int ny, int nz, float *out,
+                               const int *stop_flag, cudaStream_t s) {
+    switch (t.r) {
+        case 1: return smooth_tile_r<1>(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+        case 2: return smooth_tile_r<2>(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+        case 3: return smooth_tile_r<3>(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+        case 4: return smooth_tile_r<4>(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+        case 5: return smooth_tile_r<5>(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+        case 6: return smooth_tile_r<6>(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -464,8 +560,17 @@ static cudaError_t smooth_plain(const float *in, int ncomp, const Taps &t, int n
     return cudaGetLastError();
 }
 
+int smooth_auto_variant(int nx, int ny, int nz) {
+    return (size_t)nx * ny * nz < ((size_t)2 << 20) ? SMOOTH_TILE : SMOOTH_MARCH;
+}
+
+int smooth_default_zchunk(int nx, int ny, int nz, int ncomp) {
+    return smooth_zchunk(nx, ny, nz, SY, ncomp, 4);
+}
+
 cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int ny, int nz,
-                          float *out, const int *stop_flag, cudaStream_t s, int *err) {
+                          float *out, const int *stop_flag, cudaStream_t s, int *err, SmoothChoice ch) {
+    int variant = ch.variant;
     const Taps t = gauss_taps(sigma);
     const size_t N = (size_t)nx * ny * nz;
     if (t.r == 0) {
@@ -474,8 +579,13 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
         return cudaGetLastError();
     }
     if (err != nullptr) {
+        // small volumes: the 3-D tile kernel (one short wave); large: the
+        // TMA z-march, whose plane pipeline needs long chunks to pay off
+        if (variant == SMOOTH_AUTO) variant = smooth_auto_variant(nx, ny, nz);
+        if (variant == SMOOTH_TILE) return smooth_tile(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
         bool launched = false;
-        cudaError_t e = smooth_tma<1, false>(in, nullptr, 0, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched);
+        cudaError_t e =
+            smooth_tma<1, false>(in, nullptr, 0, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched, ch.zchunk);
         if (e != cudaSuccess || launched) return e;
     }
     return smooth_plain(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
@@ -483,7 +593,7 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
 
 cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
                                   int nz, float *out, float *tmp, const int *stop_flag, cudaStream_t s,
-                                  int *err, bool one_pass) {
+                                  int *err, bool one_pass, SmoothChoice ch) {
     const Taps t = gauss_taps(sigma);
     if (one_pass && t.r > 0 && err != nullptr) {
         bool launched = false;
@@ -491,7 +601,7 @@ cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, flo
         if (e != cudaSuccess || launched) return e;
     }
     // smooth du into tmp, then compose
-    cudaError_t e = launch_smooth(du, 3, sigma, nx, ny, nz, tmp, stop_flag, s, err);
+    cudaError_t e = launch_smooth(du, 3, sigma, nx, ny, nz, tmp, stop_flag, s, err, ch);
     if (e != cudaSuccess) return e;
     return launch_compose(u, tmp, mode, nx, ny, nz, out, stop_flag, s);
 }

@@ -171,7 +171,7 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
     size_t np = 0;
     for (int l = 0; l < L; ++l) {
         const int *d = pl.dims[l];
-        np = std::max(np, std::max(force_partial_count(d[0], d[1], d[2], force_default_zchunk(d[0], d[1], d[2])),
+        np = std::max(np, std::max(force_partial_count(d[0], d[1], d[2], force_zchunk_min(d[0], d[1], d[2])),
                                    metric_partial_count(d[0], d[1], d[2])));
     }
     const size_t Ntot = pl.Ntot, Nf = pl.Nf;
@@ -188,6 +188,18 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
     pl.need[RegPlan::B_STAGE] = need_stage ? std::max(Nf * 4, (size_t)k * Nf) : 0;
     // two-pass force scratch (sized for the finest level, reused by every level)
     pl.need[RegPlan::B_FSCR] = (ctx->plain_kernels || ctx->fused_force) ? 0 : force_scratch_bytes(Nf, k);
+    return CGDIR_OK;
+}
+
+// Tune the level shapes of `pl` not seen before (when autotuning is on).
+int plan_autotune(cgdir_ctx *ctx, const RegPlan &pl) {
+    if (!ctx->autotune_on) return CGDIR_OK;
+    for (int l = pl.first; l < pl.L; ++l) {
+        const int contour = ((pl.P.contour_level_mask >> l) & 1u) && pl.k > 0;
+        if (ctx->tuned.count(TuneKey{pl.dims[l][0], pl.dims[l][1], pl.dims[l][2], contour, pl.sdt})) continue;
+        TRY(tune_level(ctx, pl.dims[l][0], pl.dims[l][1], pl.dims[l][2], pl.k, contour, pl.sdt,
+                       std::max(pl.P.sigma_fluid, pl.P.sigma_diff)));
+    }
     return CGDIR_OK;
 }
 
@@ -323,7 +335,8 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
         a.nx = lx; a.ny = ly; a.nz = lz;
         a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
         if (pl.fscr) force_scratch_assign(a, pl.fscr, pl.Nl[l]);
-        const int zc = force_default_zchunk(lx, ly, lz);
+        const int zc = force_zchunk_for(ctx, lx, ly, lz, a.contour, sdt);
+        const SmoothChoice sch = smooth_choice(ctx, lx, ly, lz, a.contour, sdt);
         const int cap = P->iters[l];
         a.fin.done = done + l;
         a.fin.st = st;
@@ -337,9 +350,9 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
             { ProfScope ps(prof, m, s, CGDIR_K_FORCE, l); CK(launch_force(a, zc, &nb, s, kerr(ctx))); }
             { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3
               CK(launch_smooth_compose(pl.du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, pl.du2, uoth,
-                                       flags + l, s, kerr(ctx), ctx->fused_force)); }
+                                       flags + l, s, kerr(ctx), ctx->fused_force, sch)); }
             { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_U, l);    // step 4
-              CK(launch_smooth(pl.du2, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx))); }
+              CK(launch_smooth(pl.du2, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx), sch)); }
         }
         int nb = 0;
         FinishArgs fm = a.fin;
@@ -357,7 +370,8 @@ std::string plan_key(cgdir_ctx *ctx, const RegPlan &pl) {
         key, sizeof key, "%d %d %d|%d|%d %d %.9g %.9g %d %u %d %.17g %.17g %.17g %.17g %.17g %.9g %d %d %llu %u %d|",
         pl.nx, pl.ny, pl.nz, pl.L, pl.k, pl.first, P->sigma_fluid, P->sigma_diff, P->compose_mode,
         P->contour_level_mask, P->stop_mode, P->eps, P->spacing_mm[0], P->spacing_mm[1], P->spacing_mm[2],
-        P->margin_mm, P->intensity_offset, (int)ctx->plain_kernels + 2 * (int)ctx->fused_force, pl.maxcap, pl.generation, ctx->prof_mask, pl.sdt);
+        P->margin_mm, P->intensity_offset, (int)ctx->plain_kernels + 2 * (int)ctx->fused_force + 4 * ctx->smooth_variant + 16 * (int)ctx->tune_gen,
+        pl.maxcap, pl.generation, ctx->prof_mask, pl.sdt);
     std::string s(key, (size_t)len);
     for (int l = 0; l < pl.L; ++l) s += std::to_string(P->iters[l]) + ",";
     for (int j = 0; j < pl.k; ++j) {
@@ -494,6 +508,7 @@ int cgdir_register(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M,
     cudaStream_t s = ctx->stream;
     Slot &sl = slot_at(ctx, 0);
     if (sl.busy) return fail(ctx, CGDIR_EBUSY, "register: slot 0 is serving a request");
+    TRY(plan_autotune(ctx, pl));
     TRY(plan_prepare(ctx, sl, pl, s));
     const ProfList *used = nullptr;
     TRY(plan_run(ctx, sl, pl, s, &used));
@@ -522,6 +537,7 @@ int cgdir_register_batch(cgdir_ctx *ctx, int count, const cgdir_volume *statics,
     }
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
+    for (int i = 0; i < count; ++i) TRY(plan_autotune(ctx, pls[i]));
     for (int i = 0; i < count; ++i) {
         Slot &sl = slot_at(ctx, (size_t)i);
         if (sl.busy) return fail(ctx, CGDIR_EBUSY, "register_batch: a slot is serving a request");
@@ -599,6 +615,7 @@ int cgdir_submit(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, c
     std::unique_ptr<RegPlan, RegPlanDeleter> pl(new RegPlan());
     TRY(plan_make(ctx, S, M, SM, MM, P, dvf_where, *pl));
     DeviceGuard g(ctx->device);
+    TRY(plan_autotune(ctx, *pl));
     // a free slot (slot 0 is left to cgdir_register): first one that already
     // holds a graph for this request (no capture, no growth), else the one
     // whose buffers must grow least

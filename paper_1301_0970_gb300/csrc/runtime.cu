@@ -307,6 +307,10 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     const char *kern = std::getenv("CGDIR_KERNELS");
     c->plain_kernels = kern && std::strcmp(kern, "plain") == 0;
     c->fused_force = kern && std::strcmp(kern, "fused") == 0;
+    const char *sv = std::getenv("CGDIR_SMOOTH");
+    c->smooth_variant = !sv ? SMOOTH_AUTO
+                            : std::strcmp(sv, "tile") == 0 ? SMOOTH_TILE
+                            : std::strcmp(sv, "march") == 0 ? SMOOTH_MARCH : SMOOTH_AUTO;
     const char *gr = std::getenv("CGDIR_GRAPHS");
     c->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -369,6 +373,13 @@ int cgdir_warp(cgdir_ctx *ctx, const float *f, const float *u, int nx, int ny, i
     return CGDIR_OK;
 }
 
+// Smoothing choice of the primitives: the context's forced variant, else by size.
+static SmoothChoice prim_smooth(const cgdir_ctx *ctx) {
+    SmoothChoice ch;
+    ch.variant = ctx->smooth_variant;
+    return ch;
+}
+
 static int force_impl(cgdir_ctx *ctx, const ForceArgs &a, double *stats_host) {
     void *part = nullptr, *st = nullptr;
     ForceArgs b = a;
@@ -428,7 +439,7 @@ int cgdir_smooth(cgdir_ctx *ctx, const float *in, int ncomp, float sigma, int nx
     if (!in || !out || in == out || ncomp < 1 || ncomp > 3 || !dims_ok(nx, ny, nz) || !sigma_ok(sigma))
         return fail(ctx, CGDIR_EINVAL, "smooth: bad arguments");
     DeviceGuard g(ctx->device);
-    CK(launch_smooth(in, ncomp, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx)));
+    CK(launch_smooth(in, ncomp, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
     return CGDIR_OK;
 }
 
@@ -447,7 +458,7 @@ int cgdir_compose(cgdir_ctx *ctx, const float *u, const float *du, int mode, flo
     void *tmp = nullptr;
     TRY(ws_get(ctx, "field_tmp", 3 * N * sizeof(float), &tmp));
     CK(launch_compose(u, du, mode, nx, ny, nz, (float *)tmp, nullptr, ctx->stream));
-    CK(launch_smooth((float *)tmp, 3, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx)));
+    CK(launch_smooth((float *)tmp, 3, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
     return CGDIR_OK;
 }
 
@@ -477,13 +488,13 @@ int cgdir_iterate(cgdir_ctx *ctx, const float *I0, const float *T0, const uint8_
     a.nx = nx; a.ny = ny; a.nz = nz;
     TRY(force_impl(ctx, a, stats_host));
     if (du_out) {   // the smoothed du is wanted: steps 2 and 3 separately
-        CK(launch_smooth(du, 3, sigma_fluid, nx, ny, nz, du_out, nullptr, ctx->stream, kerr(ctx)));
+        CK(launch_smooth(du, 3, sigma_fluid, nx, ny, nz, du_out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
         CK(launch_compose(u_in, du_out, compose_mode, nx, ny, nz, un, nullptr, ctx->stream));
     } else {
         CK(launch_smooth_compose(du, u_in, compose_mode, sigma_fluid, nx, ny, nz, un, (float *)t3, nullptr,
-                                 ctx->stream, kerr(ctx), ctx->fused_force));
+                                 ctx->stream, kerr(ctx), ctx->fused_force, prim_smooth(ctx)));
     }
-    CK(launch_smooth(un, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx)));
+    CK(launch_smooth(un, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
     return CGDIR_OK;
 }
 

@@ -4,6 +4,7 @@
 
 #include "cgdir_internal.cuh"
 
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <map>
@@ -47,6 +48,16 @@ struct WsSet {
     size_t bytes() const;
 };
 
+// Kernel choices for one pyramid level shape, picked by timing (autotune.cu).
+struct TunedLevel {
+    int smooth_variant = 0;    // SMOOTH_MARCH / SMOOTH_TILE
+    int smooth_zchunk = 0;     // z chunk of the z-march smoothing (0 = default)
+    int force_zchunk = 0;      // z chunk of the force stencil pass (0 = default)
+    float smooth_ms = 0.f, force_ms = 0.f;   // best times measured
+    float default_smooth_ms = 0.f, default_force_ms = 0.f;
+};
+using TuneKey = std::array<int, 5>;   // nx, ny, nz, structure terms on, image storage type
+
 struct RegPlan;   // register.cu
 struct RegPlanDeleter { void operator()(RegPlan *p) const; };
 
@@ -86,6 +97,7 @@ struct cgdir_ctx {
     int device = 0;
     bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
     bool fused_force = false;     // CGDIR_KERNELS=fused: one-pass TMA force kernel instead of two passes
+    int smooth_variant = 0;       // SMOOTH_AUTO / MARCH / TILE (CGDIR_SMOOTH=auto|march|tile)
     int *err_word = nullptr;      // device word set by a kernel whose bounded wait ran out
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
@@ -99,6 +111,9 @@ struct cgdir_ctx {
     std::vector<std::unique_ptr<cgdir::rt::Slot>> slots;
     int max_slots = 8;                            // serving concurrency
     long long next_ticket = 1;
+    std::map<cgdir::rt::TuneKey, cgdir::rt::TunedLevel> tuned;   // autotuned level shapes
+    unsigned tune_gen = 0;                        // bumped when a choice changes (graph keys)
+    bool autotune_on = false;                     // tune unseen level shapes before a registration
 };
 
 namespace cgdir {
@@ -155,6 +170,15 @@ int auto_sign_impl(cgdir_ctx *ctx, const void *T0, int dtype, const uint8_t *sbi
                    int nz, int8_t *sign_host);
 unsigned long long launches_now();
 void launches_sub(unsigned long long n);
+
+// Tuned (else default) kernel choices for a level shape.
+SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
+int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
+// Smallest force z chunk any tuning may choose (sizes the partial buffers).
+int force_zchunk_min(int nx, int ny, int nz);
+// Time the candidate kernels of one level shape on synthetic data and
+// record the fastest (autotune.cu).  k structures, sigma of the smoothing.
+int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int sdt, float sigma);
 
 }  // namespace rt
 }  // namespace cgdir

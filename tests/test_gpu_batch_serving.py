@@ -172,3 +172,34 @@ def test_budget_admission_returns_busy_then_admits(cases):
         da, _ = ctx.wait(a)
         db, _ = ctx.wait(submit(ctx, c, kw))     # reuses the first slot's buffers
         assert torch.equal(da, db)
+
+
+def test_autotune_records_every_level_and_keeps_results():
+    """The autotuner picks launch geometry only: a registration after tuning
+    gives the same DVF, bit for bit, as an untuned context (FIXED stopping)."""
+    c = phantom.make_case("headneck256", shape=(24, 96, 96))
+    kw = dict(levels=3, iters=[6, 4, 3], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as plain:
+        ref, rst = single(plain, c, kw)
+    with cg.Context(0) as ctx:
+        tab = ctx.autotune(c.shape, c.k, 3)
+        assert len(tab) == 3
+        assert {t["shape"] for t in tab} == {(6, 24, 24), (12, 48, 48), (24, 96, 96)}
+        for t in tab:
+            assert t["smooth"] in ("march", "tile") and t["force_zchunk"] >= 1
+            assert 0 < t["smooth_ms"] <= t["default_smooth_ms"] * 1.0001 + 1e-6
+            assert 0 < t["force_ms"] <= t["default_force_ms"] * 1.0001 + 1e-6
+        got, st = single(ctx, c, kw)
+        assert torch.equal(got, ref)
+        assert [s["iters_run"] for s in st] == [s["iters_run"] for s in rst]
+
+
+def test_autotune_on_first_use():
+    c = phantom.make_case("phantom64", shape=(16, 40, 44))
+    kw = dict(levels=2, iters=[5, 4], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as ctx:
+        ctx.set_autotune(True)
+        a, _ = single(ctx, c, kw)
+        assert len(ctx.tuning()) == 2
+        b, _ = single(ctx, c, kw)
+        assert torch.equal(a, b)

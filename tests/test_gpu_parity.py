@@ -163,6 +163,29 @@ def test_smooth(ctx, sigma, shape):
     close_elementwise(one, oracle.gauss(u[0], sigma))
 
 
+@pytest.mark.parametrize("variant", ["tile", "march"])
+@pytest.mark.parametrize("shape", [(40, 256, 256), (9, 21, 44), (17, 33, 68)])
+def test_smooth_variants(variant, shape):
+    """Both smoothing kernels (3-D tile, TMA z-march) on the same field, one
+    of them past the size where the automatic choice switches."""
+    import os
+    old = os.environ.get("CGDIR_SMOOTH")
+    os.environ["CGDIR_SMOOTH"] = variant
+    try:
+        c = cg.Context(0)
+    finally:
+        if old is None:
+            del os.environ["CGDIR_SMOOTH"]
+        else:
+            os.environ["CGDIR_SMOOTH"] = old
+    try:
+        f = rand_field(shape)
+        got = host(c.smooth(dev(f), 1.0))
+    finally:
+        c.close()
+    close_elementwise(got, oracle.gauss_field(f, 1.0))
+
+
 @pytest.mark.parametrize("mode", [cg.CGDIR_COMPOSE, cg.CGDIR_ADDITIVE])
 @pytest.mark.parametrize("sigma", [0.0, 1.0])
 def test_compose(ctx, mode, sigma):
