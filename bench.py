@@ -49,10 +49,6 @@ def parse():
                     help="profiling aid: launch only the named kernel (via the C ABI primitive) "
                          "on the workload's full-resolution inputs, W + K times, and print its "
                          "CUDA-event time")
-    ap.add_argument("--accuracy", action="store_true",
-                    help="final-DVF RMS difference to the FP64 oracle for FP32 / FP16 / BF16 image "
-                         "storage on the 64x64x32 and 256x256x96 cases (and a shortened 512x512x160 "
-                         "run), printed as one JSON line")
     ap.add_argument("--shape", default=None,
                     help="with --only: nz,ny,nx of the inputs (the workload's case resampled)")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
@@ -660,47 +656,8 @@ def run_only_kernel(args):
     return 0
 
 
-def run_accuracy(args):
-    """DVF error of the GPU registration against the FP64 oracle, per config
-    and image storage type (the oracle always runs on the FP32 images)."""
-    import numpy as np
-    import torch
-
-    import oracle
-    import paper_1301_0970_gb300 as cg
-    import phantom
-
-    dev = torch.device("cuda", 0)
-    runs = [("phantom64", None, 1, [100]), ("headneck256", None, 3, [100, 50, 25]),
-            ("pelvis512", None, 3, [10, 5, 2])]
-    out = {}
-    with cg.Context(0) as ctx:
-        for name, shape, levels, iters in runs:
-            c = phantom.make_case(name, shape=shape)
-            t0 = time.perf_counter()
-            ref, _ = oracle.register(c.static, c.moving, c.static_masks, c.moving_masks, levels=levels,
-                                     iters=iters, lam=c.lam, sign=c.signs, stop_mode=oracle.STOP_FIXED)
-            t_oracle = time.perf_counter() - t0
-            row = {"iters": iters, "oracle_seconds": round(t_oracle, 2)}
-            for label, code in (("f32", cg.CGDIR_F32), ("f16", cg.CGDIR_F16), ("bf16", cg.CGDIR_BF16)):
-                dvf, _ = ctx.register(torch.from_numpy(c.static).to(dev), torch.from_numpy(c.moving).to(dev),
-                                      [torch.from_numpy(m).to(dev) for m in c.static_masks],
-                                      [torch.from_numpy(m).to(dev) for m in c.moving_masks],
-                                      levels=levels, iters=iters, lam=c.lam, sign=c.signs,
-                                      stop_mode=cg.CGDIR_STOP_FIXED, storage_dtype=code)
-                d = dvf.cpu().numpy().astype(np.float64) - ref
-                row[label] = float(np.sqrt((d ** 2).sum(axis=0).mean()))
-            gt = np.sqrt((c.u_gt.astype(np.float64) ** 2).sum(axis=0).mean())
-            row["rms_u_gt"] = float(gt)
-            out[f"{name} {'x'.join(map(str, c.shape[::-1]))}"] = row
-    print(json.dumps({"dvf_rms_error_vs_fp64_oracle_voxels": out}), flush=True)
-    return 0
-
-
 def main():
     args = parse()
-    if args.accuracy:
-        return run_accuracy(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.only:

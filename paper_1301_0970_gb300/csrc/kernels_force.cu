@@ -324,13 +324,13 @@ struct CornerSet {
 // Clamp x + u, find the corners and issue their loads (texels when the
 // structure terms are on and texels exist, else image values and mask bits).
 template <bool CONTOUR, typename IT>
-__device__ __forceinline__ void corner_load(const ForceArgs &a, const float *__restrict__ u, int x, int y,
-                                            int z, int i, int N, CornerSet<IT> &cs) {
+__device__ __forceinline__ void corner_load(const ForceArgs &a, float ux, float uy, float uz, int x, int y, int z,
+                                            CornerSet<IT> &cs) {
     using TT = typename TexOf<IT>::type;
     const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny;
-    const float px = fminf(fmaxf((float)x + __ldg(u + i), 0.f), (float)(nx - 1));
-    const float py = fminf(fmaxf((float)y + __ldg(u + N + i), 0.f), (float)(ny - 1));
-    const float pz = fminf(fmaxf((float)z + __ldg(u + 2 * N + i), 0.f), (float)(nz - 1));
+    const float px = fminf(fmaxf((float)x + ux, 0.f), (float)(nx - 1));
+    const float py = fminf(fmaxf((float)y + uy, 0.f), (float)(ny - 1));
+    const float pz = fminf(fmaxf((float)z + uz, 0.f), (float)(nz - 1));
     const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
     const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
     cs.wx = px - fx; cs.wy = py - fy; cs.wz = pz - fz;
@@ -398,21 +398,30 @@ __global__ void __launch_bounds__(NT, 4) k_warp_pass(ForceArgs a, int zw) {
     const int nxy = nx * ny, N = nxy * nz;
     const int zb = blockIdx.z * zw, ze = min(zb + zw, nz);
     const float *__restrict__ u = a.u;
-    // two planes at a time: both points' 16 corner loads are in flight together
+    // two planes at a time: both points' 16 corner loads are in flight
+    // together, and the next two planes' displacements load meanwhile
+    const int col = y * nx + x;
+    auto disp = [&](int z, float &dx, float &dy, float &dz) {
+        const int i = z * nxy + col;
+        dx = __ldg(u + i); dy = __ldg(u + N + i); dz = __ldg(u + 2 * N + i);
+    };
+    float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    if (zb < ze) disp(zb, ax, ay, az);
+    if (zb + 1 < ze) disp(zb + 1, bx, by, bz);
     int z = zb;
     for (; z + 1 < ze; z += 2) {
-        const int i0 = z * nxy + y * nx + x, i1 = i0 + nxy;
         CornerSet<IT> c0, c1;
-        corner_load<CONTOUR, IT>(a, u, x, y, z, i0, N, c0);
-        corner_load<CONTOUR, IT>(a, u, x, y, z + 1, i1, N, c1);
-        corner_finish<CONTOUR, IT>(a, i0, N, c0);
-        corner_finish<CONTOUR, IT>(a, i1, N, c1);
+        corner_load<CONTOUR, IT>(a, ax, ay, az, x, y, z, c0);
+        corner_load<CONTOUR, IT>(a, bx, by, bz, x, y, z + 1, c1);
+        if (z + 2 < ze) disp(z + 2, ax, ay, az);
+        if (z + 3 < ze) disp(z + 3, bx, by, bz);
+        corner_finish<CONTOUR, IT>(a, z * nxy + col, N, c0);
+        corner_finish<CONTOUR, IT>(a, (z + 1) * nxy + col, N, c1);
     }
     if (z < ze) {
-        const int i0 = z * nxy + y * nx + x;
         CornerSet<IT> c0;
-        corner_load<CONTOUR, IT>(a, u, x, y, z, i0, N, c0);
-        corner_finish<CONTOUR, IT>(a, i0, N, c0);
+        corner_load<CONTOUR, IT>(a, ax, ay, az, x, y, z, c0);
+        corner_finish<CONTOUR, IT>(a, z * nxy + col, N, c0);
     }
 }
 

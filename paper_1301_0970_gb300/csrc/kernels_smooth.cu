@@ -361,10 +361,18 @@ __global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict
     const int zb = blockIdx.z * zc, ze = min(zb + zc, nz);
     const size_t nxy = (size_t)nx * ny, N = nxy * nz;
     const float fxmax = (float)(nx - 1), fymax = (float)(ny - 1), fzmax = (float)(nz - 1);
+    const size_t col = (size_t)y * nx + x;
+    // the next plane's du loads while this plane's corners are gathered
+    float nx0 = 0.f, ny0 = 0.f, nz0 = 0.f;
+    if (zb < ze) {
+        const size_t i = (size_t)zb * nxy + col;
+        nx0 = __ldg(du + i); ny0 = __ldg(du + N + i); nz0 = __ldg(du + 2 * N + i);
+    }
     for (int z = zb; z < ze; ++z) {
-        const size_t i = (size_t)z * nxy + (size_t)y * nx + x;
-        const float dx = __ldg(du + i), dy = __ldg(du + N + i), dz = __ldg(du + 2 * N + i);
+        const size_t i = (size_t)z * nxy + col;
+        const float dx = nx0, dy = ny0, dz = nz0;
         if (mode == CGDIR_ADDITIVE) {
+            if (z + 1 < ze) { nx0 = __ldg(du + i + nxy); ny0 = __ldg(du + N + i + nxy); nz0 = __ldg(du + 2 * N + i + nxy); }
             out[i] = __ldg(u + i) + dx;
             out[N + i] = __ldg(u + N + i) + dy;
             out[2 * N + i] = __ldg(u + 2 * N + i) + dz;
@@ -379,12 +387,25 @@ __global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict
         const int ddx = ix < nx - 1 ? 1 : 0, ddy = iy < ny - 1 ? nx : 0;
         const size_t ddz = iz < nz - 1 ? nxy : 0;
         const size_t b0 = (size_t)iz * nxy + (size_t)iy * nx + ix;
-        const float ax = trilinear_at(u, b0, ddx, ddy, (int)ddz, wx, wy, wz);
-        const float ay = trilinear_at(u + N, b0, ddx, ddy, (int)ddz, wx, wy, wz);
-        const float az = trilinear_at(u + 2 * N, b0, ddx, ddy, (int)ddz, wx, wy, wz);
-        out[i] = dx + ax;
-        out[N + i] = dy + ay;
-        out[2 * N + i] = dz + az;
+        float cx[8], cy[8], cz[8];
+        const size_t o[8] = {0, (size_t)ddx, (size_t)ddy, (size_t)(ddy + ddx), ddz, ddz + ddx, ddz + ddy,
+                             ddz + ddy + ddx};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            cx[q] = __ldg(u + b0 + o[q]);
+            cy[q] = __ldg(u + N + b0 + o[q]);
+            cz[q] = __ldg(u + 2 * N + b0 + o[q]);
+        }
+        if (z + 1 < ze) { nx0 = __ldg(du + i + nxy); ny0 = __ldg(du + N + i + nxy); nz0 = __ldg(du + 2 * N + i + nxy); }
+        auto tri = [&](const float *c) {
+            const float e00 = fmaf(wx, c[1] - c[0], c[0]), e10 = fmaf(wx, c[3] - c[2], c[2]);
+            const float e01 = fmaf(wx, c[5] - c[4], c[4]), e11 = fmaf(wx, c[7] - c[6], c[6]);
+            const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
+            return fmaf(wz, f1 - f0, f0);
+        };
+        out[i] = dx + tri(cx);
+        out[N + i] = dy + tri(cy);
+        out[2 * N + i] = dz + tri(cz);
     }
 }
 
