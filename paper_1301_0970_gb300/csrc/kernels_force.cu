@@ -493,7 +493,7 @@ __device__ __forceinline__ void plane_load(const ForceArgs &a, int ic, int ip, i
 }
 
 template <bool CONTOUR, typename IT>
-__global__ void __launch_bounds__(NT) k_force_pass(ForceArgs a, int zchunk) {
+__global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
     if (a.stop_flag && *a.stop_flag) return;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -517,9 +517,11 @@ __global__ void __launch_bounds__(NT) k_force_pass(ForceArgs a, int zchunk) {
         float Wm = __ldg(a.wfield + im), Wc = __ldg(a.wfield + ic);
         unsigned Sm = 0, Sc = 0;
         if (CONTOUR) { Sm = __ldg(a.wstate + im); Sc = __ldg(a.wstate + ic); }
-        PlaneLoads<CONTOUR, IT> cur, nxt;
-        plane_load<CONTOUR, IT>(a, ic, zb < nz - 1 ? ic + nxy : ic, oxm, oxp, oym, oyp, cur);
-        for (int z = zb; z < ze; ++z, ic += nxy) {
+        PlaneLoads<CONTOUR, IT> bufA, bufB;
+        plane_load<CONTOUR, IT>(a, ic, zb < nz - 1 ? ic + nxy : ic, oxm, oxp, oym, oyp, bufA);
+        int z = zb;
+        // one plane: consumes `cur`, prefetches the next plane into `nxt`
+        auto step = [&](const PlaneLoads<CONTOUR, IT> &cur, PlaneLoads<CONTOUR, IT> &nxt) {
             const int ip = z < nz - 1 ? ic + nxy : ic;
             if (z + 1 < ze)        // prefetch the next plane
                 plane_load<CONTOUR, IT>(a, ic + nxy, z + 1 < nz - 1 ? ic + 2 * nxy : ic + nxy, oxm, oxp, oym,
@@ -584,8 +586,15 @@ __global__ void __launch_bounds__(NT) k_force_pass(ForceArgs a, int zchunk) {
             mx = fmaxf(mx, dux * dux + duy * duy + duz * duz);
             Wm = Wc; Wc = Wp; im = ic;
             if (CONTOUR) { Sm = Sc; Sc = Sp; }
-            cur = nxt;
+            ++z;
+            ic += nxy;
+        };
+        // two planes per turn, the prefetch buffers alternating (no copies)
+        for (; z + 1 < ze;) {
+            step(bufA, bufB);
+            step(bufB, bufA);
         }
+        if (z < ze) step(bufA, bufB);
     }
     if (a.partial) {
         block_partial<NT>(ssd, cnt, sqrtf(mx), a.partial,
