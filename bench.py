@@ -344,7 +344,7 @@ def run_cgdir(args):
         bytes_per_launch = FORCE_BYTES_PER_VOXEL[True] * N
         peak, peak_src = measured_peaks()
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_force (finest level, contour terms on)",
+        roofline = {"bound": "hbm", "kernel": "force step = k_warp_pass + k_force_pass (finest level, contour terms on)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": force_traffic_record(case),
                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
