@@ -307,7 +307,7 @@ def run_cgdir(args):
     value = whole_job_value(world, vox_iters, args.steps, max_total_ms)
 
     # ---- one profiled step with every kernel class timed (breakdown only)
-    ctx.profile(list(range(7)))
+    ctx.profile(list(range(8)))
     flush.zero_()
     ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
     breakdown = ctx.profile_read()

@@ -380,7 +380,8 @@ unsigned long long cgdir_launch_count(void);
 #define CGDIR_K_FINALIZE   4   /* RMS-ID reduction and stop test (kernel 5)  */
 #define CGDIR_K_METRIC     5   /* warp-only metric pass after a level's cap  */
 #define CGDIR_K_SETUP      6   /* pyramid, masks, UROI, signs, prolongation  */
-#define CGDIR_K_COUNT      7
+#define CGDIR_K_LEVEL      7   /* a whole small level in one cooperative launch */
+#define CGDIR_K_COUNT      8
 
 typedef struct {
     int       kernel;     /* CGDIR_K_*                                       */

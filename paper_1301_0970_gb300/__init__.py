@@ -73,8 +73,8 @@ class cgdir_kernel_time(ctypes.Structure):
 
 
 CGDIR_K_FORCE, CGDIR_K_SMOOTH_DU, CGDIR_K_COMPOSE, CGDIR_K_SMOOTH_U, CGDIR_K_FINALIZE, \
-    CGDIR_K_METRIC, CGDIR_K_SETUP = range(7)
-KERNEL_NAMES = ["force", "smooth_du", "compose", "smooth_u", "finalize", "metric", "setup"]
+    CGDIR_K_METRIC, CGDIR_K_SETUP, CGDIR_K_LEVEL = range(8)
+KERNEL_NAMES = ["force", "smooth_du", "compose", "smooth_u", "finalize", "metric", "setup", "level"]
 
 _SIGNATURES = {
     "cgdir_launch_count": (ctypes.c_ulonglong, []),

@@ -73,6 +73,11 @@ SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int con
     return ch;
 }
 
+bool use_level_coop(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
+    (void)contour; (void)sdt;
+    return (long)nx * ny * nz <= ctx->coop_max_voxels;
+}
+
 int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
     if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt))
         if (t->force_zchunk > 0) return t->force_zchunk;

@@ -105,6 +105,25 @@ struct ForceArgs {
     float *pfield;
 };
 
+// One whole pyramid level (all iterations of Algorithm A) in one cooperative
+// launch: every CTA is resident, phases are separated by bounded grid
+// barriers (see kernels_force.cu, k_level_coop).  For small levels, whose
+// per-iteration kernels are too short to fill the GPU.
+struct LevelCoopArgs {
+    ForceArgs f;                  // images, masks, texels, structure terms, u (in/out), du,
+                                  // two-pass scratch (wfield / wstate / pfield), UROI;
+                                  // f.fin.st is the level's stop state; f.fin.cap / stop_mode / eps
+    float *tmp1, *tmp2, *ub;      // 3N floats each
+    Taps tf, td;                  // Gaussian taps of du and of u
+    int compose_mode;
+    unsigned long long *sums;     // [2][4] zeroed before the launch
+    unsigned *bar;                // [2] grid-barrier counter and generation, zeroed before the launch
+    int *err;                     // set to 1 if a barrier wait ran out
+};
+// CTAs of the cooperative level kernel for this level (0: cannot run it).
+int level_coop_grid(int nx, int ny, int nz, bool contour, int img_dtype);
+cudaError_t launch_level_coop(const LevelCoopArgs &p, int grid, cudaStream_t s);
+
 // Bytes of the two-pass force scratch for n voxels and k structures.
 inline size_t force_scratch_bytes(size_t n, int k) {
     return n * 4 + ((n * 2 + 255) / 256) * 256 + (size_t)k * n * 4 + 512;

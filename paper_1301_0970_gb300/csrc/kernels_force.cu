@@ -866,6 +866,265 @@ __global__ void __launch_bounds__(NT) k_force_tma(const __grid_constant__ ForceM
     }
 }
 
+// ---- cooperative level kernel (small levels) --------------------------------
+// All iterations of one level in one launch.  Each iteration is eight
+// grid-wide phases separated by barriers: warp (pass 1), force + RMS-ID
+// (pass 2), the stop decision, x / y / z passes of the Gaussian of du with
+// the composite update fused into the z pass, and x / y / z passes of the
+// Gaussian of u.  Every phase has the arithmetic of the per-iteration
+// kernels (same formulas, same order of operations), so both give the same
+// DVF.  Buffers written inside the kernel are read with L2-only loads
+// (ld.global.cg): the L1 is not coherent across CTAs.  Every barrier wait is
+// bounded; a CTA whose wait runs out records the error and returns.
+
+// Sense-reversing grid barrier over `nb` resident CTAs; false if the wait
+// ran out (about 1 s).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nb, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        ok = 1;
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nb - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > kWaitLimitCycles) { atomicExch(err, 1); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ float p_at_cg(const ForceArgs &a, int j, int N, int idx, float w, unsigned st) {
+    const unsigned andb = st >> 8, orb = st & 0xffu;
+    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldcg(a.pfield + j * N + idx);
+    return ((andb >> j) & 1u) ? w + a.offset : 0.f;
+}
+
+// One pass of the separable Gaussian along axis `stride` (1, nx or nx*ny)
+// over all three components: out = sum_j w_j in[clamp(p + j - R)].
+__device__ __forceinline__ void coop_pass(const float *in, float *out, const Taps &t, int stride, int n_axis,
+                                          int nx, int nxy, int N, int gt, int gs, int axis) {
+    const int R = t.r;
+    for (int e = gt; e < 3 * N; e += gs) {
+        const int c = e / N, i = e - c * N;
+        const int pos = axis == 0 ? i % nx : axis == 1 ? (i / nx) % (nxy / nx) : i / nxy;
+        const float *src = in + (size_t)c * N + i;
+        float acc = 0.f;
+        for (int j = 0; j <= 2 * R; ++j) {
+            const int q = min(max(pos + j - R, 0), n_axis - 1);
+            acc = fmaf(t.w[j], __ldcg(src + (q - pos) * stride), acc);
+        }
+        out[e] = acc;
+    }
+}
+
+template <bool CONTOUR, typename IT>
+__global__ void __launch_bounds__(NT, 2) k_level_coop(const __grid_constant__ LevelCoopArgs p) {
+    const ForceArgs &a = p.f;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, N = nxy * nz;
+    const int tid = threadIdx.y * TX + threadIdx.x, gt = blockIdx.x * NT + tid, gs = gridDim.x * NT;
+    const unsigned nb = gridDim.x;
+    const LevelState &st = a.fin.st;
+    float *u = const_cast<float *>(a.u);
+    __shared__ ContourTables tab;
+    if (CONTOUR) {
+        build_tables(a, tab, tid);
+        __syncthreads();
+    }
+    const float off = a.offset;
+    for (int n = 0;; ++n) {
+        // ---- pass 1: warp
+        for (int i = gt; i < N; i += gs) {
+            const int x = i % nx, y = (i / nx) % ny, z = i / nxy;
+            CornerSet<IT> cs;
+            corner_load<CONTOUR, IT>(a, __ldcg(u + i), __ldcg(u + N + i), __ldcg(u + 2 * N + i), x, y, z, cs);
+            corner_finish<CONTOUR, IT>(a, i, N, cs);
+        }
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+        // ---- pass 2: force and the RMS-ID sums
+        float ssd = 0.f;
+        int cnt = 0;
+        for (int i = gt; i < N; i += gs) {
+            const int x = i % nx, y = (i / nx) % ny, z = i / nxy;
+            const int oxm = x > 0 ? -1 : 0, oxp = x < nx - 1 ? 1 : 0;
+            const int oym = y > 0 ? -nx : 0, oyp = y < ny - 1 ? nx : 0;
+            const int ozm = z > 0 ? -nxy : 0, ozp = z < nz - 1 ? nxy : 0;
+            const float *W = a.wfield;
+            const float w0 = __ldcg(W + i);
+            const float Wxm = __ldcg(W + i + oxm), Wxp = __ldcg(W + i + oxp);
+            const float Wym = __ldcg(W + i + oym), Wyp = __ldcg(W + i + oyp);
+            const float Wm = __ldcg(W + i + ozm), Wp = __ldcg(W + i + ozp);
+            const float T = ld_img<IT>(static_cast<const IT *>(a.T0) + i);
+            const float gxv = 0.5f * (Wxp - Wxm), gyv = 0.5f * (Wyp - Wym), gzv = 0.5f * (Wp - Wm);
+            const float r0 = T - w0;
+            const float g2 = gxv * gxv + gyv * gyv + gzv * gzv;
+            float dux = 0.f, duy = 0.f, duz = 0.f;
+            if (g2 != 0.f) {
+                const float inv = g2 > 1e-30f ? rsqrtf(g2) : 1.f / sqrtf(g2);
+                const float gn = g2 * inv;
+                const float nxv = gxv * inv, nyv = gyv * inv, nzv = gzv * inv;
+                float num = gn * r0, den = gn * gn;
+                if (CONTOUR) {
+                    const uint16_t *S = a.wstate;
+                    const unsigned Sc = __ldcg(S + i), Sxm = __ldcg(S + i + oxm), Sxp = __ldcg(S + i + oxp);
+                    const unsigned Sym = __ldcg(S + i + oym), Syp = __ldcg(S + i + oyp);
+                    const unsigned Sm = __ldcg(S + i + ozm), Sp = __ldcg(S + i + ozp);
+                    const unsigned sb = __ldg(a.sbits + i);
+                    const float Toff = T + off;
+                    const unsigned A = (Sc & Sxm & Sxp & Sym & Syp & Sm & Sp) >> 8;
+                    const unsigned O = (Sc | Sxm | Sxp | Sym | Syp | Sm | Sp) & 0xffu;
+                    const unsigned kmask = (1u << a.k) - 1u;
+                    unsigned mixed = O & ~A & kmask;
+                    {
+                        const unsigned U = kmask & ~mixed, bU = A & U, nU = sb & U;
+                        const float J = w0 + off;
+                        const float cr = 1.f + tab.lam[U] + tab.h1[bU];
+                        float cn = r0 * cr;
+                        cn = fmaf(Toff - J, tab.h3[nU & bU], cn);
+                        cn = fmaf(Toff, tab.h1[nU & ~bU], cn);
+                        cn = fmaf(-J, tab.h3[bU & ~nU], cn);
+                        num = gn * cn;
+                        den = gn * gn * (1.f + tab.lam[U] + tab.h2[bU]);
+                    }
+                    while (mixed) {
+                        const int j = __ffs(mixed) - 1;
+                        mixed &= mixed - 1u;
+                        const float hs = a.half_sign[j];
+                        const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
+                        const float dPx = 0.5f * (p_at_cg(a, j, N, i + oxp, Wxp, Sxp) - p_at_cg(a, j, N, i + oxm, Wxm, Sxm));
+                        const float dPy = 0.5f * (p_at_cg(a, j, N, i + oyp, Wyp, Syp) - p_at_cg(a, j, N, i + oym, Wym, Sym));
+                        const float dPz = 0.5f * (p_at_cg(a, j, N, i + ozp, Wp, Sp) - p_at_cg(a, j, N, i + ozm, Wm, Sm));
+                        const float aj = gn + hs * (dPx * nxv + dPy * nyv + dPz * nzv);
+                        const float rj = r0 + hs * (inside - p_at_cg(a, j, N, i, w0, Sc));
+                        num = fmaf(a.lambda[j] * aj, rj, num);
+                        den = fmaf(a.lambda[j] * aj, aj, den);
+                    }
+                }
+                const float v = __fdividef(num, den + r0 * r0);
+                dux = v * nxv; duy = v * nyv; duz = v * nzv;
+            }
+            a.du[i] = dux;
+            a.du[N + i] = duy;
+            a.du[2 * N + i] = duz;
+            if (a.uroi == nullptr || __ldg(a.uroi + i)) {
+                ssd = fmaf(r0, r0, ssd);
+                cnt += 1;
+            }
+        }
+        {
+            // exact in-block sum (fixed point), then one atomic per CTA
+            __shared__ unsigned long long rs[NT / 32];
+            __shared__ int rc[NT / 32];
+            unsigned long long q = __float2ull_rn(fminf(ssd, 1.0995e12f) * kSsdScale);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                q += __shfl_xor_sync(0xffffffffu, q, o);
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            }
+            if ((tid & 31) == 0) { rs[tid >> 5] = q; rc[tid >> 5] = cnt; }
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long sq = 0, sc = 0;
+                for (int w = 0; w < NT / 32; ++w) { sq += rs[w]; sc += (unsigned long long)rc[w]; }
+                atomicAdd(p.sums + (n & 1) * 4 + 0, sq);
+                atomicAdd(p.sums + (n & 1) * 4 + 1, sc);
+            }
+        }
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+        // ---- the stop decision, taken identically by every CTA
+        {
+            const double S = (double)__ldcg(p.sums + (n & 1) * 4 + 0) * (1.0 / (double)kSsdScale);
+            const double C = (double)__ldcg(p.sums + (n & 1) * 4 + 1);
+            const double d = C > 0 ? sqrt(S / C) : 0.0;
+            bool stop = false;
+            if (a.fin.stop_mode == CGDIR_STOP_WINDOW10) {
+                stop = n >= 10 && (__ldcg(st.hist + n - 10) - d <= a.fin.eps);
+            } else if (a.fin.stop_mode == CGDIR_STOP_PAPER_LITERAL && n >= 11) {
+                const double ln = d - __ldcg(st.hist + n - 1);
+                const double lm = __ldcg(st.hist + n - 10) - __ldcg(st.hist + n - 11);
+                stop = (lm - ln) <= a.fin.eps;
+            }
+            const bool cap = n >= a.fin.cap;
+            if (blockIdx.x == 0 && tid == 0) {
+                if (n < st.hist_cap) st.hist[n] = d;
+                *st.hist_len = n + 1;
+                p.sums[((n + 1) & 1) * 4 + 0] = 0ull;
+                p.sums[((n + 1) & 1) * 4 + 1] = 0ull;
+                if (stop || cap) {
+                    *st.stop_flag = 1;
+                    *st.iters_run = n;
+                    *st.stop_reason = stop ? CGDIR_REASON_CONVERGED : CGDIR_REASON_CAP;
+                }
+            }
+            if (stop || cap) return;
+        }
+        // ---- Gaussian of du (x, y), z pass with the composite update fused
+        coop_pass(a.du, p.tmp1, p.tf, 1, nx, nx, nxy, N, gt, gs, 0);
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+        coop_pass(p.tmp1, p.tmp2, p.tf, nx, ny, nx, nxy, N, gt, gs, 1);
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+        for (int i = gt; i < N; i += gs) {
+            const int x = i % nx, y = (i / nx) % ny, z = i / nxy;
+            float s3[3];
+            for (int c = 0; c < 3; ++c) {
+                const float *src = p.tmp2 + (size_t)c * N + i;
+                float acc = 0.f;
+                for (int j = 0; j <= 2 * p.tf.r; ++j) {
+                    const int q = min(max(z + j - p.tf.r, 0), nz - 1);
+                    acc = fmaf(p.tf.w[j], __ldcg(src + (q - z) * nxy), acc);
+                }
+                s3[c] = acc;
+            }
+            float ax, ay, az;
+            if (p.compose_mode == CGDIR_ADDITIVE) {
+                ax = __ldcg(u + i); ay = __ldcg(u + N + i); az = __ldcg(u + 2 * N + i);
+            } else {
+                const float px = fminf(fmaxf((float)x + s3[0], 0.f), (float)(nx - 1));
+                const float py = fminf(fmaxf((float)y + s3[1], 0.f), (float)(ny - 1));
+                const float pz = fminf(fmaxf((float)z + s3[2], 0.f), (float)(nz - 1));
+                const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+                const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+                const float wx = px - fx, wy = py - fy, wz = pz - fz;
+                const int ddx = ix < nx - 1 ? 1 : 0, ddy = iy < ny - 1 ? nx : 0, ddz = iz < nz - 1 ? nxy : 0;
+                const int b0 = iz * nxy + iy * nx + ix;
+                const int o[8] = {0, ddx, ddy, ddy + ddx, ddz, ddz + ddx, ddz + ddy, ddz + ddy + ddx};
+                float r3[3];
+                for (int c = 0; c < 3; ++c) {
+                    float cc[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cc[q] = __ldcg(u + (size_t)c * N + b0 + o[q]);
+                    const float e00 = fmaf(wx, cc[1] - cc[0], cc[0]), e10 = fmaf(wx, cc[3] - cc[2], cc[2]);
+                    const float e01 = fmaf(wx, cc[5] - cc[4], cc[4]), e11 = fmaf(wx, cc[7] - cc[6], cc[6]);
+                    const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
+                    r3[c] = fmaf(wz, f1 - f0, f0);
+                }
+                ax = r3[0]; ay = r3[1]; az = r3[2];
+            }
+            p.ub[i] = s3[0] + ax;
+            p.ub[N + i] = s3[1] + ay;
+            p.ub[2 * N + i] = s3[2] + az;
+        }
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+        // ---- Gaussian of u
+        coop_pass(p.ub, p.tmp1, p.td, 1, nx, nx, nxy, N, gt, gs, 0);
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+        coop_pass(p.tmp1, p.tmp2, p.td, nx, ny, nx, nxy, N, gt, gs, 1);
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+        coop_pass(p.tmp2, u, p.td, nxy, nz, nx, nxy, N, gt, gs, 2);
+        if (!grid_barrier(p.bar, nb, p.err)) return;
+    }
+}
+
 // Metric-only pass: I0~ at every voxel and the UROI partial sums (the warp
 // of Algorithm A step 5 after a level's last update).
 constexpr int MT = 256;
@@ -1049,6 +1308,64 @@ cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, i
     k_finalize<<<1, FT, 0, s>>>(partial, nblocks, f);
     note_launch();
     return cudaGetLastError();
+}
+
+template <bool CONTOUR, typename IT>
+static int coop_blocks_per_sm() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cached[dev] == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_level_coop<CONTOUR, IT>, NT, 0) != cudaSuccess) {
+            cudaGetLastError();
+            nb = -1;
+        }
+        cached[dev] = nb > 0 ? nb : -1;
+    }
+    return cached[dev] > 0 ? cached[dev] : 0;
+}
+
+int level_coop_grid(int nx, int ny, int nz, bool contour, int img_dtype) {
+    const long N = (long)nx * ny * nz;
+    if (N <= 0 || N >= (1L << 31) / 3) return 0;
+    int per = 0;
+    if (img_dtype == CGDIR_F16) per = contour ? coop_blocks_per_sm<true, __half>() : coop_blocks_per_sm<false, __half>();
+    else if (img_dtype == CGDIR_BF16)
+        per = contour ? coop_blocks_per_sm<true, __nv_bfloat16>() : coop_blocks_per_sm<false, __nv_bfloat16>();
+    else per = contour ? coop_blocks_per_sm<true, float>() : coop_blocks_per_sm<false, float>();
+    if (per <= 0) return 0;
+    const long need = (N + NT - 1) / NT;
+    return (int)std::max(1L, std::min(need, (long)per * sm_count()));
+}
+
+template <bool CONTOUR, typename IT>
+static cudaError_t launch_coop_t(const LevelCoopArgs &p, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TX, TY);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_level_coop<CONTOUR, IT>, p);
+}
+
+cudaError_t launch_level_coop(const LevelCoopArgs &p, int grid, cudaStream_t s) {
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    const bool contour = p.f.contour && p.f.k > 0;
+    cudaError_t e;
+    if (p.f.img_dtype == CGDIR_F16)
+        e = contour ? launch_coop_t<true, __half>(p, grid, s) : launch_coop_t<false, __half>(p, grid, s);
+    else if (p.f.img_dtype == CGDIR_BF16)
+        e = contour ? launch_coop_t<true, __nv_bfloat16>(p, grid, s) : launch_coop_t<false, __nv_bfloat16>(p, grid, s);
+    else
+        e = contour ? launch_coop_t<true, float>(p, grid, s) : launch_coop_t<false, float>(p, grid, s);
+    note_launch();
+    return e;
 }
 
 cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,

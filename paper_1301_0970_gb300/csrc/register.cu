@@ -167,7 +167,9 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
     }
     pl.Nf = pl.Nl[L - 1];
     pl.Ntot = pl.off[L];
-    pl.state_bytes = (size_t)L * pl.hcap * sizeof(double) + 5 * CGDIR_MAX_LEVELS * sizeof(int);
+    // level histories, 5 ints per level, then 128 bytes per level for the
+    // cooperative level kernel (RMS-ID sums and grid-barrier words)
+    pl.state_bytes = (size_t)L * pl.hcap * sizeof(double) + 5 * CGDIR_MAX_LEVELS * sizeof(int) + 128 * CGDIR_MAX_LEVELS;
     size_t np = 0;
     for (int l = 0; l < L; ++l) {
         const int *d = pl.dims[l];
@@ -344,6 +346,29 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
         a.fin.stop_mode = P->stop_mode;
         a.fin.eps = P->eps;
         a.fin.stats_out = nullptr;
+        // small levels below the finest: all iterations in one cooperative launch
+        const int coop_grid = (l < L - 1 && 2 * pl.Nl[l] <= pl.Nf && !ctx->plain_kernels && !ctx->fused_force &&
+                               pl.fscr && use_level_coop(ctx, lx, ly, lz, a.contour, sdt))
+                                  ? level_coop_grid(lx, ly, lz, a.contour, sdt) : 0;
+        if (coop_grid > 0) {
+            LevelCoopArgs c{};
+            c.f = a;
+            c.f.partial = nullptr;
+            c.f.fin.done = nullptr;
+            c.tmp1 = pl.du2;                                  // 3 N_l floats of 3 N_finest
+            c.tmp2 = uoth;                                    // uoth holds 3 N_finest >= 6 N_l
+            c.ub = uoth + 3 * pl.Nl[l];
+            c.tf = gauss_taps(P->sigma_fluid);
+            c.td = gauss_taps(P->sigma_diff);
+            c.compose_mode = P->compose_mode;
+            char *area = (char *)pl.meta + 5 * CGDIR_MAX_LEVELS * sizeof(int) + 128 * l;
+            c.sums = (unsigned long long *)area;
+            c.bar = (unsigned *)(area + 64);
+            c.err = kerr(ctx);
+            ProfScope ps(prof, m, s, CGDIR_K_LEVEL, l);
+            CK(launch_level_coop(c, coop_grid, s));
+            continue;
+        }
         for (int n = 0; n < cap; ++n) {
             int nb = 0;
             a.fin.n = n;   // the force kernel's last CTA reduces delta^n and runs the stop test

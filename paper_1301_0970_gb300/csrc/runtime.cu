@@ -307,6 +307,8 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     const char *kern = std::getenv("CGDIR_KERNELS");
     c->plain_kernels = kern && std::strcmp(kern, "plain") == 0;
     c->fused_force = kern && std::strcmp(kern, "fused") == 0;
+    const char *cm = std::getenv("CGDIR_COOP_MAX");
+    c->coop_max_voxels = cm ? std::atol(cm) : 0;
     const char *sv = std::getenv("CGDIR_SMOOTH");
     c->smooth_variant = !sv ? SMOOTH_AUTO
                             : std::strcmp(sv, "tile") == 0 ? SMOOTH_TILE

@@ -98,6 +98,8 @@ struct cgdir_ctx {
     bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
     bool fused_force = false;     // CGDIR_KERNELS=fused: one-pass TMA force kernel instead of two passes
     int smooth_variant = 0;       // SMOOTH_AUTO / MARCH / TILE (CGDIR_SMOOTH=auto|march|tile)
+    long coop_max_voxels = 0;     // levels below the finest with at most this many voxels run
+                                  // the cooperative level kernel (CGDIR_COOP_MAX)
     int *err_word = nullptr;      // device word set by a kernel whose bounded wait ran out
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;            // private stream the graphs are captured on
@@ -174,6 +176,7 @@ void launches_sub(unsigned long long n);
 // Tuned (else default) kernel choices for a level shape.
 SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
 int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
+bool use_level_coop(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
 // Smallest force z chunk any tuning may choose (sizes the partial buffers).
 int force_zchunk_min(int nx, int ny, int nz);
 // Time the candidate kernels of one level shape on synthetic data and

@@ -203,3 +203,47 @@ def test_autotune_on_first_use():
         assert len(ctx.tuning()) == 2
         b, _ = single(ctx, c, kw)
         assert torch.equal(a, b)
+
+
+def _ctx_with_env(env):
+    import os
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return cg.Context(0)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.parametrize("stop", [cg.CGDIR_STOP_FIXED, cg.CGDIR_STOP_WINDOW10])
+def test_cooperative_level_kernel_matches_per_iteration_kernels(stop):
+    """Small levels run as one cooperative launch (all iterations, grid
+    barriers between phases) with the arithmetic of the per-iteration
+    kernels: the same DVF bit for bit, and histories equal to FP32
+    summation order."""
+    c = phantom.make_case("headneck256", shape=(40, 120, 124))
+    kw = dict(levels=3, iters=[30, 20, 4], lam=c.lam, sign=c.signs, stop_mode=stop, eps=1e-3,
+              contour_level_mask=3)
+    base = _ctx_with_env({})
+    coop = _ctx_with_env({"CGDIR_COOP_MAX": str(10 ** 7)})
+    try:
+        a, sa = single(base, c, kw)
+        b, sb = single(coop, c, kw)
+        coop.profile([cg.CGDIR_K_LEVEL])
+        single(coop, c, kw)
+        prof = coop.profile_read()
+    finally:
+        base.close()
+        coop.close()
+    assert {p["level"] for p in prof if p["kernel"] == "level"} == {0, 1}
+    assert [s["iters_run"] for s in sa] == [s["iters_run"] for s in sb]
+    for x, y in zip(sa, sb):
+        np.testing.assert_allclose(x["rms_id"], y["rms_id"], rtol=1e-6)
+    if stop == cg.CGDIR_STOP_FIXED:
+        assert torch.equal(a, b)
+    else:
+        assert float((a - b).abs().max()) <= 1e-4

@@ -461,7 +461,7 @@ def test_one_context_serves_changing_shapes():
 def test_profile_reports_every_kernel_class():
     c = phantom.make_case("phantom64", shape=(12, 32, 32))
     with cg.Context(0) as ctx:
-        ctx.profile(list(range(7)))
+        ctx.profile(list(range(8)))
         ctx.register(dev(c.static), dev(c.moving), [dev(m) for m in c.static_masks],
                      [dev(m) for m in c.moving_masks], levels=2, iters=[3, 2], lam=c.lam, sign=c.signs,
                      stop_mode=cg.CGDIR_STOP_FIXED)
