@@ -401,22 +401,24 @@ int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap);
 
 /* ---- autotuner (not in the paper: an execution choice) --------------------
  * For each level shape of a pyramid it times, on synthetic data of that
- * shape, the candidate configurations of the smoothing kernel (TMA z-march
- * with three z-chunk lengths, 3-D shared-memory tile) and of the force
- * stencil pass (three z-chunk lengths) on ctx's stream, and keeps the
- * fastest.  Later registrations of those shapes use the choices (results
+ * shape, the candidate configurations of the smoothing with the composite
+ * update (steps 2-4 of an iteration: TMA z-march with three z-chunk
+ * lengths, 3-D shared-memory tile, split xy + z kernels with the update in
+ * the z pass) and of the force stencil pass (three z-chunk lengths) on
+ * ctx's stream, and keeps the fastest.  Later registrations of those shapes use the choices (results
  * are the same to rounding: only the launch geometry changes, except that
  * the two smoothing kernels may differ in the last bit).  Blocking. */
 #define CGDIR_SMOOTH_MARCH 1
 #define CGDIR_SMOOTH_TILE  2
+#define CGDIR_SMOOTH_SPLIT 3
 typedef struct {
     int   nx, ny, nz;           /* level shape                                   */
     int   contour;              /* structure terms on at this level               */
     int   storage_dtype;        /* CGDIR_F32 / F16 / BF16                          */
-    int   smooth_variant;       /* CGDIR_SMOOTH_MARCH / CGDIR_SMOOTH_TILE           */
-    int   smooth_zchunk;        /* z chunk of the z-march (0 = n/a)                 */
+    int   smooth_variant;       /* CGDIR_SMOOTH_MARCH / _TILE / _SPLIT              */
+    int   smooth_zchunk;        /* z chunk of the z-march (0 = default / n/a)       */
     int   force_zchunk;         /* z chunk of the force stencil pass                */
-    float smooth_ms, force_ms;  /* best time of one launch (3-component smoothing) */
+    float smooth_ms, force_ms;  /* best times: steps 2-4 of one iteration; force   */
     float default_smooth_ms, default_force_ms;   /* the untuned choice's times     */
 } cgdir_tuning;
 

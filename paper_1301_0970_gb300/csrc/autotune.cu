@@ -2,8 +2,11 @@
 // execution choice).  For one pyramid level shape it times, on synthetic
 // data of that shape, the candidate launch configurations of the two
 // kernels whose best configuration depends on the shape:
-//   smoothing: the TMA z-march with its default z chunk, half and double
-//              that chunk, and the 3-D shared-memory tile kernel;
+//   smoothing (with the composite update, i.e. steps 2-4 of an iteration):
+//              the TMA z-march with its default z chunk, half and double
+//              that chunk (plus the separate update kernel), the 3-D
+//              shared-memory tile kernel (idem), and the split xy + z
+//              kernels with the update fused into the z pass;
 //   force:     the stencil pass with the default z chunk, half and double.
 // The fastest of each is recorded in the context and used by every later
 // registration of that shape (and baked into its CUDA graph).
@@ -110,7 +113,7 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     TRY(ws_get(ctx, "tune_img", 2 * N * esz, &img));
     TRY(ws_get(ctx, "tune_bits", 3 * N, &bits));
     TRY(ws_get(ctx, "tune_tex", N * tsz, &tex));
-    TRY(ws_get(ctx, "tune_fields", 3 * 3 * N * sizeof(float), &fields));
+    TRY(ws_get(ctx, "tune_fields", 4 * 3 * N * sizeof(float), &fields));
     TRY(ws_get(ctx, "tune_scr", force_scratch_bytes(N, contour ? k : 0), &scr));
     const size_t np = force_partial_count(nx, ny, nz, force_zchunk_min(nx, ny, nz));
     TRY(ws_get(ctx, "tune_part", np * kPartialStride * sizeof(double), &part));
@@ -118,7 +121,7 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     cudaStream_t s = ctx->stream;
     char *I0 = (char *)img, *T0 = (char *)img + N * esz;
     uint8_t *mb = (uint8_t *)bits, *sb = mb + N, *ur = mb + 2 * N;
-    float *u = (float *)fields, *du = u + 3 * N, *out = du + 3 * N;
+    float *u = (float *)fields, *du = u + 3 * N, *out = du + 3 * N, *sscr = out + 3 * N;
     const unsigned fg = (unsigned)std::min<size_t>((N + 255) / 256, 152 * 8);
     if (sdt == CGDIR_F16)
         k_tune_fill<__half><<<fg, 256, 0, s>>>((__half *)I0, (__half *)T0, mb, sb, ur, u, nx, ny, nz, k);
@@ -130,6 +133,7 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     CK(cudaGetLastError());
     if (contour) CK(launch_make_texels(I0, sdt, mb, N, tex, s));
     CK(cudaMemsetAsync(state, 0, 256, s));
+    CK(cudaMemsetAsync(du, 0, 3 * N * sizeof(float), s));
 
     // force with the fused reduction, as in a registration
     ForceArgs a{};
@@ -172,7 +176,7 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     if (rc == CGDIR_OK) {
         float bt = 1e30f;
         const int d = smooth_default_zchunk(nx, ny, nz, 3);
-        SmoothChoice cand[4];
+        SmoothChoice cand[6];
         int nc = 0;
         if (nx % 4 == 0) {
             cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = d;
@@ -180,11 +184,16 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
             if (std::min(nz, 2 * d) != d) { cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = std::min(nz, 2 * d); }
         }
         cand[nc].variant = SMOOTH_TILE; cand[nc++].zchunk = 0;
+        cand[nc].variant = SMOOTH_SPLIT; cand[nc++].zchunk = 0;
         const SmoothChoice dflt{smooth_auto_variant(nx, ny, nz), 0};
         for (int ci = 0; ci < nc && rc == CGDIR_OK; ++ci) {
             float ms = 0.f;
+            // one iteration's smoothing: G(du) with the composite update, then G(u')
             rc = time_ms(ctx, e0, e1, reps, &ms, [&](cudaStream_t st) {
-                return launch_smooth(u, 3, sigma, nx, ny, nz, out, nullptr, st, kerr(ctx), cand[ci]);
+                cudaError_t e = launch_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, sscr, nullptr, st,
+                                                      kerr(ctx), false, cand[ci]);
+                if (e != cudaSuccess) return e;
+                return launch_smooth(out, 3, sigma, nx, ny, nz, du, nullptr, st, kerr(ctx), cand[ci], sscr);
             });
             const bool is_default = cand[ci].variant == dflt.variant &&
                                     (cand[ci].variant == SMOOTH_TILE || cand[ci].zchunk == d);

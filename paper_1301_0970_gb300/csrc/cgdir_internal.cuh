@@ -163,8 +163,10 @@ cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, i
                             int stop_mode, double eps, double *stats_out, cudaStream_t s);
 
 // Smoothing kernel variants: the TMA z-march (large volumes), the 3-D
-// shared-memory tile (small volumes), or chosen by size.
-enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2 };
+// shared-memory tile (small volumes), the split xy + z kernels (needs a 3N
+// scratch field; with the composite update fused into the z pass), or
+// chosen by size.
+enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2, SMOOTH_SPLIT = 3 };
 int smooth_auto_variant(int nx, int ny, int nz);
 // Kernel choice for one smoothing launch: variant and (z-march) z chunk, 0 = default.
 struct SmoothChoice {
@@ -176,7 +178,7 @@ int smooth_default_zchunk(int nx, int ny, int nz, int ncomp);
 // nullptr selects the plain-load kernel (no waits).
 cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int ny, int nz,
                           float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr,
-                          SmoothChoice ch = SmoothChoice());
+                          SmoothChoice ch = SmoothChoice(), float *scratch = nullptr);
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
                            float *out, const int *stop_flag, cudaStream_t s);
 // Algorithm A steps 2 + 3: out = G(du) + u(x + G(du)) (or u + G(du)).  By

@@ -477,6 +477,174 @@ __global__ void __launch_bounds__(NT) k_smooth_tile(const float *__restrict__ in
     }
 }
 
+// ---- split version: xy pass and z pass as two kernels ------------------------
+// k_smooth_xy filters planes in x and y: a CTA takes a 32 x 32 output tile
+// of one component over a few consecutive planes; each plane's tile plus its
+// R-voxel halo is loaded (clamped indices, positions precomputed once; the
+// next plane's loads are issued before the current plane is filtered) into
+// shared memory, filtered along x in 4-output register blocks and along y in
+// 4-row register blocks.  k_smooth_z marches each (x, y) column through z
+// with the three components' last 2R+1 values in registers and, for the
+// du field, applies the composite update (Algorithm A step 3) on the spot:
+// the z pass is where all three smoothed components of a voxel first meet,
+// so the update costs no extra pass over memory.
+constexpr int XYT = 32;                // xy output tile (32 x 32)
+constexpr int XYZ = 4;                 // planes per CTA in the xy pass
+
+template <int R>
+__global__ void __launch_bounds__(NT) k_smooth_xy(const float *__restrict__ in, float *__restrict__ out, Taps taps,
+                                                  int nx, int ny, int nz, int zgroups, const int *stop_flag) {
+    if (stop_flag && *stop_flag) return;
+    constexpr int K = 2 * R + 1, AX = XYT + 2 * R, AY = XYT + 2 * R, NA = AX * AY;
+    constexpr int LPT = (NA + NT - 1) / NT;          // loads per thread per plane
+    constexpr int XT = AY * (XYT / 4);               // x-pass tasks (4 outputs each)
+    __shared__ float A[NA];
+    __shared__ __align__(16) float B[AY * XYT];
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int x0 = blockIdx.x * XYT, y0 = blockIdx.y * XYT;
+    const int comp = blockIdx.z / zgroups, zb = (blockIdx.z % zgroups) * XYZ, ze = min(zb + XYZ, nz);
+    const size_t nxy = (size_t)nx * ny, N = nxy * nz;
+    const float *src = in + (size_t)comp * N;
+    float *dst = out + (size_t)comp * N;
+    int loff[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) {
+        const int pidx = tid + q * NT;
+        const int hy = pidx / AX, hx = pidx - hy * AX;
+        const int gx = clampi(x0 - R + hx, 0, nx - 1), gy = clampi(y0 - R + hy, 0, ny - 1);
+        loff[q] = pidx < NA ? gy * nx + gx : -1;
+    }
+    float pre[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) pre[q] = loff[q] >= 0 ? __ldg(src + (size_t)zb * nxy + loff[q]) : 0.f;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int z = zb; z < ze; ++z) {
+#pragma unroll
+        for (int q = 0; q < LPT; ++q)
+            if (loff[q] >= 0) A[tid + q * NT] = pre[q];
+        __syncthreads();
+        if (z + 1 < ze) {                            // next plane's loads fly during the passes
+#pragma unroll
+            for (int q = 0; q < LPT; ++q) pre[q] = loff[q] >= 0 ? __ldg(src + (size_t)(z + 1) * nxy + loff[q]) : 0.f;
+        }
+        for (int task = tid; task < XT; task += NT) {   // x pass: row, 4 outputs
+            const int row = task >> 3, xs = (task & 7) * 4;
+            const float *a = A + row * AX + xs;
+            float v[4 + 2 * R];
+#pragma unroll
+            for (int i = 0; i < 4 + 2 * R; ++i) v[i] = a[i];
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                o0 = fmaf(taps.w[j], v[j], o0);
+                o1 = fmaf(taps.w[j], v[j + 1], o1);
+                o2 = fmaf(taps.w[j], v[j + 2], o2);
+                o3 = fmaf(taps.w[j], v[j + 3], o3);
+            }
+            *reinterpret_cast<float4 *>(B + row * XYT + xs) = make_float4(o0, o1, o2, o3);
+        }
+        __syncthreads();
+        {                                              // y pass: column tx, rows 4ty .. 4ty+3
+            float c[4 + 2 * R];
+#pragma unroll
+            for (int i = 0; i < 4 + 2 * R; ++i) c[i] = B[(4 * ty + i) * XYT + tx];
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) o[m] = fmaf(taps.w[j], c[j + m], o[m]);
+            const int x = x0 + tx;
+            if (x < nx) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int y = y0 + 4 * ty + m;
+                    if (y < ny) dst[(size_t)z * nxy + (size_t)y * nx + x] = o[m];
+                }
+            }
+        }
+        // the next plane overwrites A only after every thread has left the x pass
+    }
+}
+
+template <int R, int NC, bool COMPOSE>
+__global__ void __launch_bounds__(NT) k_smooth_z(const float *__restrict__ in, const float *__restrict__ u, int mode,
+                                                 float *__restrict__ out, Taps taps, int nx, int ny, int nz,
+                                                 int zchunk, const int *stop_flag) {
+    if (stop_flag && *stop_flag) return;
+    constexpr int K = 2 * R + 1;
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const int nchunks = (nz + zchunk - 1) / zchunk;
+    const int comp = NC == 1 ? (int)blockIdx.z / nchunks : 0;
+    const int zb = ((int)blockIdx.z % nchunks) * zchunk, ze = min(zb + zchunk, nz);
+    const int P = (ze - zb) + 2 * R;
+    const size_t nxy = (size_t)nx * ny, N = nxy * nz, col = (size_t)y * nx + x;
+    const float *src = in + (size_t)comp * N + col;
+    float *dst = out + (size_t)comp * N + col;
+    float ring[NC][K];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < K; ++j) ring[c][j] = 0.f;
+    float nxt[NC];
+    {
+        const size_t zo = (size_t)clampi(zb - R, 0, nz - 1) * nxy;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) nxt[c] = __ldg(src + c * N + zo);
+    }
+    const float fxmax = (float)(nx - 1), fymax = (float)(ny - 1), fzmax = (float)(nz - 1);
+    for (int t0 = 0; t0 < P; t0 += K) {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const int t = t0 + r;
+            if (t >= P) break;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ring[c][r] = nxt[c];
+            if (t + 1 < P) {
+                const size_t zo = (size_t)clampi(zb - R + t + 1, 0, nz - 1) * nxy;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) nxt[c] = __ldg(src + c * N + zo);
+            }
+            if (t < 2 * R) continue;
+            const int z = zb + t - 2 * R;
+            float sv[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j < K; ++j) acc = fmaf(taps.w[j], ring[c][(r + 1 + j) % K], acc);
+                sv[c] = acc;
+            }
+            const size_t i = (size_t)z * nxy;
+            if (COMPOSE) {
+                float a0, a1, a2;
+                if (mode == CGDIR_ADDITIVE) {
+                    a0 = __ldg(u + i + col); a1 = __ldg(u + N + i + col); a2 = __ldg(u + 2 * N + i + col);
+                } else {
+                    const float px = fminf(fmaxf((float)x + sv[0], 0.f), fxmax);
+                    const float py = fminf(fmaxf((float)y + sv[NC > 1 ? 1 : 0], 0.f), fymax);
+                    const float pz = fminf(fmaxf((float)z + sv[NC > 2 ? 2 : 0], 0.f), fzmax);
+                    const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+                    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+                    const float wx = px - fx, wy = py - fy, wz = pz - fz;
+                    const int ddx = ix < nx - 1 ? 1 : 0, ddy = iy < ny - 1 ? nx : 0;
+                    const size_t ddz = iz < nz - 1 ? nxy : 0;
+                    const size_t b0 = (size_t)iz * nxy + (size_t)iy * nx + ix;
+                    a0 = trilinear_at(u, b0, ddx, ddy, (int)ddz, wx, wy, wz);
+                    a1 = trilinear_at(u + N, b0, ddx, ddy, (int)ddz, wx, wy, wz);
+                    a2 = trilinear_at(u + 2 * N, b0, ddx, ddy, (int)ddz, wx, wy, wz);
+                }
+                dst[i] = sv[0] + a0;
+                dst[N + i] = sv[NC > 1 ? 1 : 0] + a1;
+                dst[2 * N + i] = sv[NC > 2 ? 2 : 0] + a2;
+            } else {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) dst[c * N + i] = sv[c];
+            }
+        }
+    }
+}
+
 __global__ void k_copy(const float *__restrict__ in, float *__restrict__ out, size_t n,
                        const int *stop_flag) {
     if (stop_flag && *stop_flag) return;
@@ -585,12 +753,50 @@ int smooth_auto_variant(int nx, int ny, int nz) {
     return (size_t)nx * ny * nz < ((size_t)2 << 20) ? SMOOTH_TILE : SMOOTH_MARCH;
 }
 
+template <int R>
+static cudaError_t smooth_split_r(const float *in, const float *u, int mode, bool compose, int ncomp, const Taps &t,
+                                  int nx, int ny, int nz, float *out, float *scratch, int zc_override,
+                                  const int *stop_flag, cudaStream_t s) {
+    const int zgroups = (nz + XYZ - 1) / XYZ;
+    dim3 g1((nx + XYT - 1) / XYT, (ny + XYT - 1) / XYT, zgroups * ncomp), block(TX, TY);
+    k_smooth_xy<R><<<g1, block, 0, s>>>(in, scratch, t, nx, ny, nz, zgroups, stop_flag);
+    const long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+    const int zc = zc_override > 0 ? std::min(zc_override, nz) : pick_zchunk(nz, tiles, 8, 1);
+    const int nch = (nz + zc - 1) / zc;
+    if (compose) {
+        dim3 g2((nx + TX - 1) / TX, (ny + TY - 1) / TY, nch);
+        k_smooth_z<R, 3, true><<<g2, block, 0, s>>>(scratch, u, mode, out, t, nx, ny, nz, zc, stop_flag);
+    } else if (ncomp == 3) {
+        dim3 g2((nx + TX - 1) / TX, (ny + TY - 1) / TY, nch);
+        k_smooth_z<R, 3, false><<<g2, block, 0, s>>>(scratch, nullptr, 0, out, t, nx, ny, nz, zc, stop_flag);
+    } else {
+        dim3 g2((nx + TX - 1) / TX, (ny + TY - 1) / TY, nch * ncomp);
+        k_smooth_z<R, 1, false><<<g2, block, 0, s>>>(scratch, nullptr, 0, out, t, nx, ny, nz, zc, stop_flag);
+    }
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+static cudaError_t smooth_split(const float *in, const float *u, int mode, bool compose, int ncomp, const Taps &t,
+                                int nx, int ny, int nz, float *out, float *scratch, int zc, const int *stop_flag,
+                                cudaStream_t s) {
+    switch (t.r) {
+        case 1: return smooth_split_r<1>(in, u, mode, compose, ncomp, t, nx, ny, nz, out, scratch, zc, stop_flag, s);
+        case 2: return smooth_split_r<2>(in, u, mode, compose, ncomp, t, nx, ny, nz, out, scratch, zc, stop_flag, s);
+        case 3: return smooth_split_r<3>(in, u, mode, compose, ncomp, t, nx, ny, nz, out, scratch, zc, stop_flag, s);
+        case 4: return smooth_split_r<4>(in, u, mode, compose, ncomp, t, nx, ny, nz, out, scratch, zc, stop_flag, s);
+        case 5: return smooth_split_r<5>(in, u, mode, compose, ncomp, t, nx, ny, nz, out, scratch, zc, stop_flag, s);
+        case 6: return smooth_split_r<6>(in, u, mode, compose, ncomp, t, nx, ny, nz, out, scratch, zc, stop_flag, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 int smooth_default_zchunk(int nx, int ny, int nz, int ncomp) {
     return smooth_zchunk(nx, ny, nz, SY, ncomp, 4);
 }
 
 cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int ny, int nz,
-                          float *out, const int *stop_flag, cudaStream_t s, int *err, SmoothChoice ch) {
+                          float *out, const int *stop_flag, cudaStream_t s, int *err, SmoothChoice ch, float *scratch) {
     int variant = ch.variant;
     const Taps t = gauss_taps(sigma);
     const size_t N = (size_t)nx * ny * nz;
@@ -604,6 +810,8 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
         // TMA z-march, whose plane pipeline needs long chunks to pay off
         if (variant == SMOOTH_AUTO) variant = smooth_auto_variant(nx, ny, nz);
         if (variant == SMOOTH_TILE) return smooth_tile(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
+        if (variant == SMOOTH_SPLIT && scratch != nullptr && scratch != in && scratch != out)
+            return smooth_split(in, nullptr, 0, false, ncomp, t, nx, ny, nz, out, scratch, ch.zchunk, stop_flag, s);
         bool launched = false;
         cudaError_t e =
             smooth_tma<1, false>(in, nullptr, 0, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched, ch.zchunk);
@@ -616,12 +824,18 @@ cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, flo
                                   int nz, float *out, float *tmp, const int *stop_flag, cudaStream_t s,
                                   int *err, bool one_pass, SmoothChoice ch) {
     const Taps t = gauss_taps(sigma);
+    if (!one_pass && t.r > 0 && err != nullptr) {
+        int variant = ch.variant == SMOOTH_AUTO ? smooth_auto_variant(nx, ny, nz) : ch.variant;
+        if (variant == SMOOTH_SPLIT)   // x/y pass, then the z pass with the composite update fused
+            return smooth_split(du, u, mode, true, 3, t, nx, ny, nz, out, tmp, ch.zchunk, stop_flag, s);
+    }
     if (one_pass && t.r > 0 && err != nullptr) {
         bool launched = false;
         cudaError_t e = smooth_tma<3, true>(du, u, mode, out, 3, t, nx, ny, nz, stop_flag, err, s, &launched);
         if (e != cudaSuccess || launched) return e;
     }
     // smooth du into tmp, then compose
+    if (ch.variant == SMOOTH_SPLIT) ch.variant = SMOOTH_MARCH;
     cudaError_t e = launch_smooth(du, 3, sigma, nx, ny, nz, tmp, stop_flag, s, err, ch);
     if (e != cudaSuccess) return e;
     return launch_compose(u, tmp, mode, nx, ny, nz, out, stop_flag, s);

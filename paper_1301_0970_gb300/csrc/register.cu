@@ -377,7 +377,7 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
               CK(launch_smooth_compose(pl.du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, pl.du2, uoth,
                                        flags + l, s, kerr(ctx), ctx->fused_force, sch)); }
             { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_U, l);    // step 4
-              CK(launch_smooth(pl.du2, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx), sch)); }
+              CK(launch_smooth(pl.du2, 3, P->sigma_diff, lx, ly, lz, ucur, flags + l, s, kerr(ctx), sch, uoth)); }
         }
         int nb = 0;
         FinishArgs fm = a.fin;

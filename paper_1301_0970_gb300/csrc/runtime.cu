@@ -312,7 +312,8 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     const char *sv = std::getenv("CGDIR_SMOOTH");
     c->smooth_variant = !sv ? SMOOTH_AUTO
                             : std::strcmp(sv, "tile") == 0 ? SMOOTH_TILE
-                            : std::strcmp(sv, "march") == 0 ? SMOOTH_MARCH : SMOOTH_AUTO;
+                            : std::strcmp(sv, "march") == 0 ? SMOOTH_MARCH
+                            : std::strcmp(sv, "split") == 0 ? SMOOTH_SPLIT : SMOOTH_AUTO;
     const char *gr = std::getenv("CGDIR_GRAPHS");
     c->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -441,7 +442,11 @@ int cgdir_smooth(cgdir_ctx *ctx, const float *in, int ncomp, float sigma, int nx
     if (!in || !out || in == out || ncomp < 1 || ncomp > 3 || !dims_ok(nx, ny, nz) || !sigma_ok(sigma))
         return fail(ctx, CGDIR_EINVAL, "smooth: bad arguments");
     DeviceGuard g(ctx->device);
-    CK(launch_smooth(in, ncomp, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
+    void *scr = nullptr;
+    if (ctx->smooth_variant == SMOOTH_SPLIT)
+        TRY(ws_get(ctx, "smooth_scr", (size_t)ncomp * nx * ny * nz * sizeof(float), &scr));
+    CK(launch_smooth(in, ncomp, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx),
+                     (float *)scr));
     return CGDIR_OK;
 }
 
@@ -496,7 +501,8 @@ int cgdir_iterate(cgdir_ctx *ctx, const float *I0, const float *T0, const uint8_
         CK(launch_smooth_compose(du, u_in, compose_mode, sigma_fluid, nx, ny, nz, un, (float *)t3, nullptr,
                                  ctx->stream, kerr(ctx), ctx->fused_force, prim_smooth(ctx)));
     }
-    CK(launch_smooth(un, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
+    CK(launch_smooth(un, 3, sigma_diff, nx, ny, nz, u_out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx),
+                     (float *)t3));
     return CGDIR_OK;
 }
 

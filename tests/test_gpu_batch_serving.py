@@ -186,7 +186,7 @@ def test_autotune_records_every_level_and_keeps_results():
         assert len(tab) == 3
         assert {t["shape"] for t in tab} == {(6, 24, 24), (12, 48, 48), (24, 96, 96)}
         for t in tab:
-            assert t["smooth"] in ("march", "tile") and t["force_zchunk"] >= 1
+            assert t["smooth"] in ("march", "tile", "split") and t["force_zchunk"] >= 1
             assert 0 < t["smooth_ms"] <= t["default_smooth_ms"] * 1.0001 + 1e-6
             assert 0 < t["force_ms"] <= t["default_force_ms"] * 1.0001 + 1e-6
         got, st = single(ctx, c, kw)
@@ -247,3 +247,20 @@ def test_cooperative_level_kernel_matches_per_iteration_kernels(stop):
         assert torch.equal(a, b)
     else:
         assert float((a - b).abs().max()) <= 1e-4
+
+
+@pytest.mark.parametrize("variant", ["split", "tile"])
+def test_smoothing_variants_give_the_same_registration(variant):
+    """Every smoothing variant (incl. the split kernels with the composite
+    update in the z pass) gives the same DVF as the z-march, bit for bit."""
+    c = phantom.make_case("headneck256", shape=(24, 72, 76))
+    kw = dict(levels=2, iters=[6, 5], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED, contour_level_mask=3)
+    a_ctx = _ctx_with_env({"CGDIR_SMOOTH": "march"})
+    b_ctx = _ctx_with_env({"CGDIR_SMOOTH": variant})
+    try:
+        a, _ = single(a_ctx, c, kw)
+        b, _ = single(b_ctx, c, kw)
+    finally:
+        a_ctx.close()
+        b_ctx.close()
+    assert torch.equal(a, b)

@@ -163,11 +163,12 @@ def test_smooth(ctx, sigma, shape):
     close_elementwise(one, oracle.gauss(u[0], sigma))
 
 
-@pytest.mark.parametrize("variant", ["tile", "march"])
-@pytest.mark.parametrize("shape", [(40, 256, 256), (9, 21, 44), (17, 33, 68)])
+@pytest.mark.parametrize("variant", ["tile", "march", "split"])
+@pytest.mark.parametrize("shape", [(40, 256, 256), (9, 21, 44), (17, 33, 68), (13, 37, 70)])
 def test_smooth_variants(variant, shape):
-    """Both smoothing kernels (3-D tile, TMA z-march) on the same field, one
-    of them past the size where the automatic choice switches."""
+    """The smoothing kernels (3-D tile, TMA z-march, split xy + z) on the
+    same field, one size past the point where the automatic choice
+    switches, one with ragged 32-wide tiles."""
     import os
     old = os.environ.get("CGDIR_SMOOTH")
     os.environ["CGDIR_SMOOTH"] = variant
