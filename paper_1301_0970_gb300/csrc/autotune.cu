@@ -65,8 +65,9 @@ static const TunedLevel *find_tuned(const cgdir_ctx *ctx, int nx, int ny, int nz
 
 SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
     SmoothChoice ch;
-    if (ctx->smooth_variant != SMOOTH_AUTO) {
+    if (ctx->smooth_variant != SMOOTH_AUTO || ctx->smooth_zchunk > 0) {
         ch.variant = ctx->smooth_variant;
+        ch.zchunk = ctx->smooth_zchunk;
         return ch;
     }
     if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt)) {
@@ -82,6 +83,7 @@ bool use_level_coop(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, i
 }
 
 int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
+    if (ctx->force_zchunk > 0) return std::max(force_zchunk_min(nx, ny, nz), std::min(ctx->force_zchunk, nz));
     if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt))
         if (t->force_zchunk > 0) return t->force_zchunk;
     return force_default_zchunk(nx, ny, nz);

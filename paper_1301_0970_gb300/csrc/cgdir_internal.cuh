@@ -103,6 +103,7 @@ struct ForceArgs {
     float *wfield;
     uint16_t *wstate;
     float *pfield;
+    int single_voxel;             // 1: pass 2 takes one voxel per thread even for even nx
 };
 
 // One whole pyramid level (all iterations of Algorithm A) in one cooperative

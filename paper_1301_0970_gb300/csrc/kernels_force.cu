@@ -464,6 +464,72 @@ __device__ __forceinline__ float p_at(const ForceArgs &a, int j, int N, int idx,
     if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldg(a.pfield + j * N + idx);
     return ((andb >> j) & 1u) ? w + a.offset : 0.f;
 }
+// The same through L2-only loads (P_j written by the same kernel).
+__device__ __forceinline__ float p_at_l2(const ForceArgs &a, int j, int N, int idx, float w, unsigned st) {
+    const unsigned andb = st >> 8, orb = st & 0xffu;
+    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldcg(a.pfield + j * N + idx);
+    return ((andb >> j) & 1u) ? w + a.offset : 0.f;
+}
+
+// Eq. 7 at one voxel from its 7-point stencil of I0~ (w0 centre; x-, x+,
+// y-, y+, z-, z+ neighbours) and corner-bit words, the static image T and
+// bits sb; i* are the stencil points' indices (for the stored P_j).  Every
+// multiply-add is written out (no compiler contraction), so the result does
+// not depend on where this function is inlined.
+template <bool CONTOUR, bool L2ONLY = false>
+__device__ __forceinline__ void force_voxel(const ForceArgs &a, const ContourTables &tab, int N, float w0, float Wxm,
+                                            float Wxp, float Wym, float Wyp, float Wm, float Wp, float T, unsigned Sc,
+                                            unsigned Sxm, unsigned Sxp, unsigned Sym, unsigned Syp, unsigned Sm,
+                                            unsigned Sp, unsigned sb, int ic, int ixm, int ixp, int iym, int iyp,
+                                            int im, int ip, float &dux, float &duy, float &duz, float &r0) {
+    const float off = a.offset;
+    const float gxv = 0.5f * (Wxp - Wxm), gyv = 0.5f * (Wyp - Wym), gzv = 0.5f * (Wp - Wm);
+    r0 = T - w0;
+    const float g2 = fmaf(gzv, gzv, fmaf(gyv, gyv, __fmul_rn(gxv, gxv)));
+    dux = 0.f; duy = 0.f; duz = 0.f;
+    if (g2 == 0.f) return;
+    const float inv = g2 > 1e-30f ? rsqrtf(g2) : 1.f / sqrtf(g2);
+    const float gn = __fmul_rn(g2, inv);
+    const float nxv = __fmul_rn(gxv, inv), nyv = __fmul_rn(gyv, inv), nzv = __fmul_rn(gzv, inv);
+    float num = __fmul_rn(gn, r0), den = __fmul_rn(gn, gn);
+    if (CONTOUR) {
+        const float Toff = T + off;
+        const unsigned A = (Sc & Sxm & Sxp & Sym & Syp & Sm & Sp) >> 8;
+        const unsigned O = (Sc | Sxm | Sxp | Sym | Syp | Sm | Sp) & 0xffu;
+        const unsigned kmask = (1u << a.k) - 1u;
+        unsigned mixed = O & ~A & kmask;
+        {
+            const unsigned U = kmask & ~mixed, bU = A & U, nU = sb & U;
+            const float J = w0 + off;
+            const float cr = 1.f + tab.lam[U] + tab.h1[bU];
+            float cn = __fmul_rn(r0, cr);
+            cn = fmaf(Toff - J, tab.h3[nU & bU], cn);
+            cn = fmaf(Toff, tab.h1[nU & ~bU], cn);
+            cn = fmaf(-J, tab.h3[bU & ~nU], cn);
+            num = __fmul_rn(gn, cn);
+            den = __fmul_rn(__fmul_rn(gn, gn), 1.f + tab.lam[U] + tab.h2[bU]);
+        }
+        // near a structure border: P_j from pass 1 at the stencil points
+        while (mixed) {
+            const int j = __ffs(mixed) - 1;
+            mixed &= mixed - 1u;
+            const float hs = a.half_sign[j];
+            const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
+            auto P = [&](int idx, float w, unsigned st) {
+                return L2ONLY ? p_at_l2(a, j, N, idx, w, st) : p_at(a, j, N, idx, w, st);
+            };
+            const float dPx = 0.5f * (P(ixp, Wxp, Sxp) - P(ixm, Wxm, Sxm));
+            const float dPy = 0.5f * (P(iyp, Wyp, Syp) - P(iym, Wym, Sym));
+            const float dPz = 0.5f * (P(ip, Wp, Sp) - P(im, Wm, Sm));
+            const float aj = fmaf(hs, fmaf(dPz, nzv, fmaf(dPy, nyv, __fmul_rn(dPx, nxv))), gn);
+            const float rj = fmaf(hs, inside - P(ic, w0, Sc), r0);
+            num = fmaf(a.lambda[j] * aj, rj, num);
+            den = fmaf(a.lambda[j] * aj, aj, den);
+        }
+    }
+    const float v = __fdividef(num, fmaf(r0, r0, den));
+    dux = __fmul_rn(v, nxv); duy = __fmul_rn(v, nyv); duz = __fmul_rn(v, nzv);
+}
 
 // Loads of one plane of pass 2 for one thread's column.
 template <bool CONTOUR, typename IT>
@@ -507,7 +573,6 @@ __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
         __syncthreads();
     }
     if (x < nx && y < ny) {
-        const float off = a.offset;
         float *__restrict__ du = a.du;
         const int col = y * nx + x;
         const int oxm = x > 0 ? -1 : 0, oxp = x < nx - 1 ? 1 : 0;
@@ -526,56 +591,13 @@ __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
             if (z + 1 < ze)        // prefetch the next plane
                 plane_load<CONTOUR, IT>(a, ic + nxy, z + 1 < nz - 1 ? ic + 2 * nxy : ic + nxy, oxm, oxp, oym,
                                         oyp, nxt);
-            const float Wp = cur.wp, Wxm = cur.wxm, Wxp = cur.wxp, Wym = cur.wym, Wyp = cur.wyp;
-            const float gxv = 0.5f * (Wxp - Wxm), gyv = 0.5f * (Wyp - Wym), gzv = 0.5f * (Wp - Wm);
-            const float T = cur.t;
-            const float w0 = Wc;
-            const float r0 = T - w0;
-            if (a.warped) a.warped[ic] = w0;
-            const float g2 = gxv * gxv + gyv * gyv + gzv * gzv;
-            float dux = 0.f, duy = 0.f, duz = 0.f;
+            const float Wp = cur.wp;
             const unsigned Sp = CONTOUR ? cur.sp : 0u;
-            if (g2 != 0.f) {
-                const float inv = g2 > 1e-30f ? rsqrtf(g2) : 1.f / sqrtf(g2);
-                const float gn = g2 * inv;
-                const float nxv = gxv * inv, nyv = gyv * inv, nzv = gzv * inv;
-                float num = gn * r0, den = gn * gn;
-                if (CONTOUR) {
-                    const unsigned Sxm = cur.sxm, Sxp = cur.sxp, Sym = cur.sym, Syp = cur.syp, sb = cur.sb;
-                    const float Toff = T + off;
-                    const unsigned A = (Sc & Sxm & Sxp & Sym & Syp & Sm & Sp) >> 8;
-                    const unsigned O = (Sc | Sxm | Sxp | Sym | Syp | Sm | Sp) & 0xffu;
-                    const unsigned kmask = (1u << a.k) - 1u;
-                    unsigned mixed = O & ~A & kmask;
-                    {
-                        const unsigned U = kmask & ~mixed, bU = A & U, nU = sb & U;
-                        const float J = w0 + off;
-                        const float cr = 1.f + tab.lam[U] + tab.h1[bU];
-                        float cn = r0 * cr;
-                        cn = fmaf(Toff - J, tab.h3[nU & bU], cn);
-                        cn = fmaf(Toff, tab.h1[nU & ~bU], cn);
-                        cn = fmaf(-J, tab.h3[bU & ~nU], cn);
-                        num = gn * cn;
-                        den = gn * gn * (1.f + tab.lam[U] + tab.h2[bU]);
-                    }
-                    // near a structure border: P_j from pass 1 at the stencil points
-                    while (mixed) {
-                        const int j = __ffs(mixed) - 1;
-                        mixed &= mixed - 1u;
-                        const float hs = a.half_sign[j];
-                        const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
-                        const float dPx = 0.5f * (p_at(a, j, N, ic + oxp, Wxp, Sxp) - p_at(a, j, N, ic + oxm, Wxm, Sxm));
-                        const float dPy = 0.5f * (p_at(a, j, N, ic + oyp, Wyp, Syp) - p_at(a, j, N, ic + oym, Wym, Sym));
-                        const float dPz = 0.5f * (p_at(a, j, N, ip, Wp, Sp) - p_at(a, j, N, im, Wm, Sm));
-                        const float aj = gn + hs * (dPx * nxv + dPy * nyv + dPz * nzv);
-                        const float rj = r0 + hs * (inside - p_at(a, j, N, ic, w0, Sc));
-                        num = fmaf(a.lambda[j] * aj, rj, num);
-                        den = fmaf(a.lambda[j] * aj, aj, den);
-                    }
-                }
-                const float v = __fdividef(num, den + r0 * r0);
-                dux = v * nxv; duy = v * nyv; duz = v * nzv;
-            }
+            if (a.warped) a.warped[ic] = Wc;
+            float dux, duy, duz, r0;
+            force_voxel<CONTOUR>(a, tab, N, Wc, cur.wxm, cur.wxp, cur.wym, cur.wyp, Wm, Wp, cur.t, Sc, cur.sxm,
+                                 cur.sxp, cur.sym, cur.syp, Sm, Sp, CONTOUR ? cur.sb : 0u, ic, ic + oxm, ic + oxp,
+                                 ic + oym, ic + oyp, im, ip, dux, duy, duz, r0);
             du[ic] = dux;
             du[N + ic] = duy;
             du[2 * N + ic] = duz;
@@ -590,6 +612,137 @@ __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
             ic += nxy;
         };
         // two planes per turn, the prefetch buffers alternating (no copies)
+        for (; z + 1 < ze;) {
+            step(bufA, bufB);
+            step(bufB, bufA);
+        }
+        if (z < ze) step(bufA, bufB);
+    }
+    if (a.partial) {
+        block_partial<NT>(ssd, cnt, sqrtf(mx), a.partial,
+                          (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+        if (a.fin.done) finish_if_last(a.partial, gridDim.x * gridDim.y * gridDim.z, a.fin);
+    }
+}
+
+
+// Pass 2 with two voxels per thread (columns x, x+1; x even): the stencil
+// loads, the static-side loads and the du stores move as pairs, which halves
+// their instruction count and address arithmetic.  Needs an even nx.
+template <typename IT>
+struct ImgPair;
+template <>
+struct ImgPair<float> {
+    static __device__ __forceinline__ void ld(const float *p, float &a, float &b) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        a = v.x; b = v.y;
+    }
+};
+template <>
+struct ImgPair<__half> {
+    static __device__ __forceinline__ void ld(const __half *p, float &a, float &b) {
+        const __half2 v = __ldg(reinterpret_cast<const __half2 *>(p));
+        a = __low2float(v); b = __high2float(v);
+    }
+};
+template <>
+struct ImgPair<__nv_bfloat16> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float &a, float &b) {
+        const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
+        a = __low2float(v); b = __high2float(v);
+    }
+};
+
+struct PlaneLoads2 {
+    float2 wp, wym, wyp;       // I0~ pairs at z+1, y-1, y+1
+    float wxm, wxp;            // I0~ at x-1 and x+2 (clamped)
+    float t0, t1;              // T0 pair
+    unsigned sp, sym, syp;     // corner-bit word pairs (low half: x)
+    unsigned sxm, sxp;         // corner-bit words at x-1 and x+2
+    unsigned sb, ur;           // static bits / UROI byte pairs
+};
+
+template <bool CONTOUR, typename IT>
+__device__ __forceinline__ void plane_load2(const ForceArgs &a, int ic, int ip, int oxm, int oxp, int oym, int oyp,
+                                            PlaneLoads2 &L) {
+    const float *__restrict__ W = a.wfield;
+    L.wp = __ldg(reinterpret_cast<const float2 *>(W + ip));
+    L.wym = __ldg(reinterpret_cast<const float2 *>(W + ic + oym));
+    L.wyp = __ldg(reinterpret_cast<const float2 *>(W + ic + oyp));
+    L.wxm = __ldg(W + ic + oxm);
+    L.wxp = __ldg(W + ic + oxp);
+    ImgPair<IT>::ld(static_cast<const IT *>(a.T0) + ic, L.t0, L.t1);
+    L.ur = a.uroi ? (unsigned)__ldg(reinterpret_cast<const unsigned short *>(a.uroi + ic)) : 0x0101u;
+    if (CONTOUR) {
+        const uint16_t *__restrict__ S = a.wstate;
+        L.sp = __ldg(reinterpret_cast<const unsigned *>(S + ip));
+        L.sym = __ldg(reinterpret_cast<const unsigned *>(S + ic + oym));
+        L.syp = __ldg(reinterpret_cast<const unsigned *>(S + ic + oyp));
+        L.sxm = __ldg(S + ic + oxm);
+        L.sxp = __ldg(S + ic + oxp);
+        L.sb = __ldg(reinterpret_cast<const unsigned short *>(a.sbits + ic));
+    } else {
+        L.sp = L.sym = L.syp = L.sxm = L.sxp = L.sb = 0u;
+    }
+}
+
+template <bool CONTOUR, typename IT>
+__global__ void __launch_bounds__(NT, 2) k_force_pass2(ForceArgs a, int zchunk) {
+    if (a.stop_flag && *a.stop_flag) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = 2 * (blockIdx.x * TX + threadIdx.x), y = blockIdx.y * TY + threadIdx.y;
+    const int nxy = nx * ny, N = nxy * nz;
+    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
+    float ssd = 0.f, mx = 0.f;
+    int cnt = 0;
+    __shared__ ContourTables tab;
+    if (CONTOUR) {
+        build_tables(a, tab, threadIdx.y * TX + threadIdx.x);
+        __syncthreads();
+    }
+    if (x < nx && y < ny) {
+        float *__restrict__ du = a.du;
+        const int col = y * nx + x;
+        const int oxm = x > 0 ? -1 : 0, oxp = x + 2 < nx ? 2 : 1;
+        const int oym = y > 0 ? -nx : 0, oyp = y < ny - 1 ? nx : 0;
+        int ic = zb * nxy + col;
+        int im = (zb > 0 ? zb - 1 : 0) * nxy + col;
+        float2 Wm = __ldg(reinterpret_cast<const float2 *>(a.wfield + im));
+        float2 Wc = __ldg(reinterpret_cast<const float2 *>(a.wfield + ic));
+        unsigned Sm = 0, Sc = 0;
+        if (CONTOUR) {
+            Sm = __ldg(reinterpret_cast<const unsigned *>(a.wstate + im));
+            Sc = __ldg(reinterpret_cast<const unsigned *>(a.wstate + ic));
+        }
+        PlaneLoads2 bufA, bufB;
+        plane_load2<CONTOUR, IT>(a, ic, zb < nz - 1 ? ic + nxy : ic, oxm, oxp, oym, oyp, bufA);
+        int z = zb;
+        auto step = [&](const PlaneLoads2 &cur, PlaneLoads2 &nxt) {
+            const int ip = z < nz - 1 ? ic + nxy : ic;
+            if (z + 1 < ze)
+                plane_load2<CONTOUR, IT>(a, ic + nxy, z + 1 < nz - 1 ? ic + 2 * nxy : ic + nxy, oxm, oxp, oym, oyp,
+                                         nxt);
+            if (a.warped) { a.warped[ic] = Wc.x; a.warped[ic + 1] = Wc.y; }
+            float d0x, d0y, d0z, r00, d1x, d1y, d1z, r01;
+            force_voxel<CONTOUR>(a, tab, N, Wc.x, cur.wxm, Wc.y, cur.wym.x, cur.wyp.x, Wm.x, cur.wp.x, cur.t0,
+                                 Sc & 0xffffu, cur.sxm, Sc >> 16, cur.sym & 0xffffu, cur.syp & 0xffffu,
+                                 Sm & 0xffffu, cur.sp & 0xffffu, cur.sb & 0xffu, ic, ic + oxm, ic + 1, ic + oym,
+                                 ic + oyp, im, ip, d0x, d0y, d0z, r00);
+            force_voxel<CONTOUR>(a, tab, N, Wc.y, Wc.x, cur.wxp, cur.wym.y, cur.wyp.y, Wm.y, cur.wp.y, cur.t1,
+                                 Sc >> 16, Sc & 0xffffu, cur.sxp, cur.sym >> 16, cur.syp >> 16, Sm >> 16,
+                                 cur.sp >> 16, (cur.sb >> 8) & 0xffu, ic + 1, ic, ic + oxp, ic + 1 + oym,
+                                 ic + 1 + oyp, im + 1, ip + 1, d1x, d1y, d1z, r01);
+            *reinterpret_cast<float2 *>(du + ic) = make_float2(d0x, d1x);
+            *reinterpret_cast<float2 *>(du + N + ic) = make_float2(d0y, d1y);
+            *reinterpret_cast<float2 *>(du + 2 * N + ic) = make_float2(d0z, d1z);
+            if (cur.ur & 0xffu) { ssd = fmaf(r00, r00, ssd); cnt += 1; }
+            if (cur.ur >> 8) { ssd = fmaf(r01, r01, ssd); cnt += 1; }
+            mx = fmaxf(mx, fmaxf(d0x * d0x + d0y * d0y + d0z * d0z, d1x * d1x + d1y * d1y + d1z * d1z));
+            Wm = Wc; Wc = cur.wp; im = ic;
+            Sm = Sc; Sc = cur.sp;
+            ++z;
+            ic += nxy;
+        };
         for (; z + 1 < ze;) {
             step(bufA, bufB);
             step(bufB, bufA);
@@ -904,11 +1057,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nb, int *er
     return ok != 0;
 }
 
-__device__ __forceinline__ float p_at_cg(const ForceArgs &a, int j, int N, int idx, float w, unsigned st) {
-    const unsigned andb = st >> 8, orb = st & 0xffu;
-    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldcg(a.pfield + j * N + idx);
-    return ((andb >> j) & 1u) ? w + a.offset : 0.f;
-}
 
 // One pass of the separable Gaussian along axis `stride` (1, nx or nx*ny)
 // over all three components: out = sum_j w_j in[clamp(p + j - R)].
@@ -941,7 +1089,6 @@ __global__ void __launch_bounds__(NT, 2) k_level_coop(const __grid_constant__ Le
         build_tables(a, tab, tid);
         __syncthreads();
     }
-    const float off = a.offset;
     for (int n = 0;; ++n) {
         // ---- pass 1: warp
         for (int i = gt; i < N; i += gs) {
@@ -965,54 +1112,18 @@ __global__ void __launch_bounds__(NT, 2) k_level_coop(const __grid_constant__ Le
             const float Wym = __ldcg(W + i + oym), Wyp = __ldcg(W + i + oyp);
             const float Wm = __ldcg(W + i + ozm), Wp = __ldcg(W + i + ozp);
             const float T = ld_img<IT>(static_cast<const IT *>(a.T0) + i);
-            const float gxv = 0.5f * (Wxp - Wxm), gyv = 0.5f * (Wyp - Wym), gzv = 0.5f * (Wp - Wm);
-            const float r0 = T - w0;
-            const float g2 = gxv * gxv + gyv * gyv + gzv * gzv;
-            float dux = 0.f, duy = 0.f, duz = 0.f;
-            if (g2 != 0.f) {
-                const float inv = g2 > 1e-30f ? rsqrtf(g2) : 1.f / sqrtf(g2);
-                const float gn = g2 * inv;
-                const float nxv = gxv * inv, nyv = gyv * inv, nzv = gzv * inv;
-                float num = gn * r0, den = gn * gn;
-                if (CONTOUR) {
-                    const uint16_t *S = a.wstate;
-                    const unsigned Sc = __ldcg(S + i), Sxm = __ldcg(S + i + oxm), Sxp = __ldcg(S + i + oxp);
-                    const unsigned Sym = __ldcg(S + i + oym), Syp = __ldcg(S + i + oyp);
-                    const unsigned Sm = __ldcg(S + i + ozm), Sp = __ldcg(S + i + ozp);
-                    const unsigned sb = __ldg(a.sbits + i);
-                    const float Toff = T + off;
-                    const unsigned A = (Sc & Sxm & Sxp & Sym & Syp & Sm & Sp) >> 8;
-                    const unsigned O = (Sc | Sxm | Sxp | Sym | Syp | Sm | Sp) & 0xffu;
-                    const unsigned kmask = (1u << a.k) - 1u;
-                    unsigned mixed = O & ~A & kmask;
-                    {
-                        const unsigned U = kmask & ~mixed, bU = A & U, nU = sb & U;
-                        const float J = w0 + off;
-                        const float cr = 1.f + tab.lam[U] + tab.h1[bU];
-                        float cn = r0 * cr;
-                        cn = fmaf(Toff - J, tab.h3[nU & bU], cn);
-                        cn = fmaf(Toff, tab.h1[nU & ~bU], cn);
-                        cn = fmaf(-J, tab.h3[bU & ~nU], cn);
-                        num = gn * cn;
-                        den = gn * gn * (1.f + tab.lam[U] + tab.h2[bU]);
-                    }
-                    while (mixed) {
-                        const int j = __ffs(mixed) - 1;
-                        mixed &= mixed - 1u;
-                        const float hs = a.half_sign[j];
-                        const float inside = ((sb >> j) & 1u) ? Toff : 0.f;
-                        const float dPx = 0.5f * (p_at_cg(a, j, N, i + oxp, Wxp, Sxp) - p_at_cg(a, j, N, i + oxm, Wxm, Sxm));
-                        const float dPy = 0.5f * (p_at_cg(a, j, N, i + oyp, Wyp, Syp) - p_at_cg(a, j, N, i + oym, Wym, Sym));
-                        const float dPz = 0.5f * (p_at_cg(a, j, N, i + ozp, Wp, Sp) - p_at_cg(a, j, N, i + ozm, Wm, Sm));
-                        const float aj = gn + hs * (dPx * nxv + dPy * nyv + dPz * nzv);
-                        const float rj = r0 + hs * (inside - p_at_cg(a, j, N, i, w0, Sc));
-                        num = fmaf(a.lambda[j] * aj, rj, num);
-                        den = fmaf(a.lambda[j] * aj, aj, den);
-                    }
-                }
-                const float v = __fdividef(num, den + r0 * r0);
-                dux = v * nxv; duy = v * nyv; duz = v * nzv;
+            unsigned Sc = 0, Sxm = 0, Sxp = 0, Sym = 0, Syp = 0, Sm = 0, Sp = 0, sb = 0;
+            if (CONTOUR) {
+                const uint16_t *S = a.wstate;
+                Sc = __ldcg(S + i); Sxm = __ldcg(S + i + oxm); Sxp = __ldcg(S + i + oxp);
+                Sym = __ldcg(S + i + oym); Syp = __ldcg(S + i + oyp);
+                Sm = __ldcg(S + i + ozm); Sp = __ldcg(S + i + ozp);
+                sb = __ldg(a.sbits + i);
             }
+            float dux, duy, duz, r0;
+            force_voxel<CONTOUR, true>(a, tab, N, w0, Wxm, Wxp, Wym, Wyp, Wm, Wp, T, Sc, Sxm, Sxp, Sym, Syp, Sm, Sp,
+                                       sb, i, i + oxm, i + oxp, i + oym, i + oyp, i + ozm, i + ozp, dux, duy, duz,
+                                       r0);
             a.du[i] = dux;
             a.du[N + i] = duy;
             a.du[2 * N + i] = duz;
@@ -1217,12 +1328,16 @@ static cudaError_t launch_force_t(const ForceArgs &a, int zchunk, dim3 grid, dim
         dim3 g(grid.x, grid.y, (a.nz + zc - 1) / zc);
         // pass 2 marches the caller's (longer) z chunks: fewer CTAs, so fewer
         // end-of-block fences before the fused reduction
+        const bool paired = a.nx % 2 == 0 && !a.single_voxel;
+        dim3 g2 = paired ? dim3((a.nx / 2 + TX - 1) / TX, grid.y, grid.z) : grid;
         if (contour) {
             k_warp_pass<true, IT><<<g, block, 0, s>>>(a, zc);
-            k_force_pass<true, IT><<<grid, block, 0, s>>>(a, zchunk);
+            if (paired) k_force_pass2<true, IT><<<g2, block, 0, s>>>(a, zchunk);
+            else k_force_pass<true, IT><<<grid, block, 0, s>>>(a, zchunk);
         } else {
             k_warp_pass<false, IT><<<g, block, 0, s>>>(a, zc);
-            k_force_pass<false, IT><<<grid, block, 0, s>>>(a, zchunk);
+            if (paired) k_force_pass2<false, IT><<<g2, block, 0, s>>>(a, zchunk);
+            else k_force_pass<false, IT><<<grid, block, 0, s>>>(a, zchunk);
         }
         note_launch(2);
         return cudaGetLastError();
@@ -1266,6 +1381,9 @@ cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaS
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
     dim3 block(TX, TY);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    if (nblocks_out && a.wfield != nullptr && (size_t)a.nx * a.ny * a.nz < (size_t)1 << 31 && a.nx % 2 == 0 &&
+        !a.single_voxel)
+        *nblocks_out = (int)(((a.nx / 2 + TX - 1) / TX) * grid.y * grid.z);   // paired pass 2
 
     if (a.img_dtype == CGDIR_F16) return launch_force_t<__half>(a, zchunk, grid, block, s, err);
     if (a.img_dtype == CGDIR_BF16) return launch_force_t<__nv_bfloat16>(a, zchunk, grid, block, s, err);

@@ -204,6 +204,7 @@ int fill_force_args(cgdir_ctx *ctx, ForceArgs &a, int k, const float *lambda, co
             return fail(ctx, CGDIR_EINVAL, "sign must be +1 or -1 for the primitives");
         a.half_sign[j] = sign ? 0.5f * (float)sign[j] : 0.5f;
     }
+    a.single_voxel = ctx->force_single ? 1 : 0;
     return CGDIR_OK;
 }
 
@@ -307,6 +308,12 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     const char *kern = std::getenv("CGDIR_KERNELS");
     c->plain_kernels = kern && std::strcmp(kern, "plain") == 0;
     c->fused_force = kern && std::strcmp(kern, "fused") == 0;
+    const char *fsv = std::getenv("CGDIR_FORCE_SINGLE");
+    c->force_single = fsv && std::strcmp(fsv, "1") == 0;
+    const char *fz = std::getenv("CGDIR_FORCE_ZCHUNK");
+    c->force_zchunk = fz ? std::atoi(fz) : 0;
+    const char *sz = std::getenv("CGDIR_SMOOTH_ZCHUNK");
+    c->smooth_zchunk = sz ? std::atoi(sz) : 0;
     const char *cm = std::getenv("CGDIR_COOP_MAX");
     c->coop_max_voxels = cm ? std::atol(cm) : 0;
     const char *sv = std::getenv("CGDIR_SMOOTH");
@@ -386,7 +393,7 @@ static SmoothChoice prim_smooth(const cgdir_ctx *ctx) {
 static int force_impl(cgdir_ctx *ctx, const ForceArgs &a, double *stats_host) {
     void *part = nullptr, *st = nullptr;
     ForceArgs b = a;
-    const int zc = force_default_zchunk(a.nx, a.ny, a.nz);
+    const int zc = force_zchunk_for(ctx, a.nx, a.ny, a.nz, a.contour && a.k > 0, a.img_dtype);
     if (b.contour && b.k > 0 && !ctx->plain_kernels && b.mtex == nullptr) {
         // the TMA kernel gathers interleaved {I0, bits} texels
         const size_t N = (size_t)a.nx * a.ny * a.nz;

@@ -98,6 +98,9 @@ struct cgdir_ctx {
     bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
     bool fused_force = false;     // CGDIR_KERNELS=fused: one-pass TMA force kernel instead of two passes
     int smooth_variant = 0;       // SMOOTH_AUTO / MARCH / TILE (CGDIR_SMOOTH=auto|march|tile)
+    bool force_single = false;    // CGDIR_FORCE_SINGLE=1: force pass 2 one voxel per thread
+    int force_zchunk = 0;         // CGDIR_FORCE_ZCHUNK: force-pass z chunk for every level (0 = tuned / default)
+    int smooth_zchunk = 0;        // CGDIR_SMOOTH_ZCHUNK: z-march smoothing z chunk (0 = tuned / default)
     long coop_max_voxels = 0;     // levels below the finest with at most this many voxels run
                                   // the cooperative level kernel (CGDIR_COOP_MAX)
     int *err_word = nullptr;      // device word set by a kernel whose bounded wait ran out
