@@ -40,8 +40,10 @@
  *    gives the message of the last failure on a context.  No exception and
  *    no abort crosses this boundary.  A CGDIR_ECUDA failure leaves the
  *    context usable unless the CUDA context itself is lost.
- *  - Threading: a context is not thread-safe; use one per host thread.  All
- *    work of a context is ordered on its stream.
+ *  - Threading: a context is not thread-safe; use one per host thread.  The
+ *    work of cgdir_register and of the primitives is ordered on the
+ *    context's stream; batches and served requests also run on private
+ *    streams of the context (see cgdir_register_batch, cgdir_submit).
  */
 #ifndef CGDIR_H
 #define CGDIR_H
@@ -166,9 +168,19 @@ typedef struct {
    update, no initial DVF. */
 void cgdir_default_params(cgdir_params *p);
 
-/* Create a context on cfg->device ordering all work on cfg->stream.
+/* Create a context on cfg->device ordering its work on cfg->stream.
    *out receives the handle (NULL on failure).  Errors: EINVAL (bad device,
-   NULL out/cfg), ECUDA. */
+   NULL out/cfg), ECUDA.
+   Kernel-choice overrides read from the environment at creation (for tests
+   and measurement; the defaults need none of them):
+     CGDIR_KERNELS=plain|fused   plain-load kernels everywhere / the one-pass
+                                 TMA force and fused smoothing kernels
+     CGDIR_GRAPHS=0              launch eagerly instead of replaying graphs
+     CGDIR_SMOOTH=march|tile|split, CGDIR_SMOOTH_ZCHUNK=n   smoothing variant
+     CGDIR_FORCE_ZCHUNK=n, CGDIR_FORCE_SINGLE=1   force pass 2 z chunk / one
+                                 voxel per thread
+     CGDIR_COOP_MAX=n            levels below the finest with at most n voxels
+                                 run as one cooperative launch */
 int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg);
 
 /* Release every device buffer, cached graph and (if owned) stream of ctx.
