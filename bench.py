@@ -284,7 +284,7 @@ def run_cgdir(args):
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs, CUDA events on the ctx stream
-    ctx.profile([cg.CGDIR_K_FORCE])
+    ctx.profile([cg.CGDIR_K_FORCE], levels=[L - 1])       # the roofline's launches only
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     barrier()

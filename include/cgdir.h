@@ -407,6 +407,13 @@ typedef struct {
    each launch; 0 switches timing off.  Clears earlier totals. */
 int cgdir_profile(cgdir_ctx *ctx, unsigned kernel_mask);
 
+/* Restrict the timing switched on by cgdir_profile to the pyramid levels
+   of level_mask (bit l = level l, 0 = coarsest); cgdir_profile selects all
+   levels.  Each timed launch adds two event nodes to the graph, so timing
+   only the levels of interest keeps the registration's own time close to
+   the untimed one.  Clears earlier totals. */
+int cgdir_profile_levels(cgdir_ctx *ctx, unsigned level_mask);
+
 /* Copy up to `cap` accumulated (kernel, level) totals into out; returns the
    number of entries written (negative status on error). */
 int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap);

@@ -80,6 +80,7 @@ _SIGNATURES = {
     "cgdir_launch_count": (ctypes.c_ulonglong, []),
     "cgdir_profile": (c_int, [c_void_p, c_uint]),
     "cgdir_profile_read": (c_int, [c_void_p, POINTER(cgdir_kernel_time), c_int]),
+    "cgdir_profile_levels": (c_int, [c_void_p, c_uint]),
     "cgdir_default_params": (None, [POINTER(cgdir_params)]),
     "cgdir_create": (c_int, [POINTER(c_void_p), POINTER(cgdir_config)]),
     "cgdir_destroy": (None, [c_void_p]),
@@ -328,12 +329,18 @@ class Context:
     def mem_in_use(self) -> int:
         return int(load().cgdir_mem_in_use(self._h))
 
-    def profile(self, kernels: Sequence[int] = ()):
-        """Time the given kernel classes (CGDIR_K_*) in later registrations."""
+    def profile(self, kernels: Sequence[int] = (), levels: Optional[Sequence[int]] = None):
+        """Time the given kernel classes (CGDIR_K_*) in later registrations,
+        at the given pyramid levels (default: all)."""
         mask = 0
         for k in kernels:
             mask |= 1 << int(k)
         self._check(load().cgdir_profile(self._h, mask), "cgdir_profile")
+        if levels is not None:
+            lm = 0
+            for l in levels:
+                lm |= 1 << int(l)
+            self._check(load().cgdir_profile_levels(self._h, lm), "cgdir_profile_levels")
 
     def profile_read(self):
         buf = (cgdir_kernel_time * 256)()

@@ -70,7 +70,8 @@ size_t WsSet::bytes() const {
 }
 
 ProfScope::ProfScope(ProfList *l, unsigned mask, cudaStream_t s, int cls, int level) : stream(s) {
-    if (!(mask & (1u << cls))) return;
+    // low 16 bits: kernel classes; high 16 bits: pyramid levels
+    if (!(mask & (1u << cls)) || level < 0 || level >= 16 || !((mask >> 16) & (1u << level))) return;
     const size_t need = 2 * (l->recs.size() + 1);
     while (l->pool.size() < need) {
         cudaEvent_t e;
@@ -266,7 +267,16 @@ int cgdir_sync(cgdir_ctx *ctx) {
 
 int cgdir_profile(cgdir_ctx *ctx, unsigned kernel_mask) {
     if (!ctx) return CGDIR_EINVAL;
-    ctx->prof_mask = kernel_mask & ((1u << CGDIR_K_COUNT) - 1u);
+    const unsigned k = kernel_mask & ((1u << CGDIR_K_COUNT) - 1u);
+    ctx->prof_mask = k ? (k | 0xffff0000u) : 0u;
+    ctx->prof.clear();
+    return CGDIR_OK;
+}
+
+int cgdir_profile_levels(cgdir_ctx *ctx, unsigned level_mask) {
+    if (!ctx) return CGDIR_EINVAL;
+    const unsigned lv = level_mask & ((1u << CGDIR_MAX_LEVELS) - 1u);
+    if (ctx->prof_mask & 0xffffu) ctx->prof_mask = (ctx->prof_mask & 0xffffu) | (lv << 16);
     ctx->prof.clear();
     return CGDIR_OK;
 }
