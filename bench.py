@@ -31,10 +31,15 @@ sys.path.insert(0, ROOT)
 METRIC = "voxel-iters/s and p50/p99 latency per registration, batched vs plain FP32"
 UNIT = "voxel-iter/s"
 WORKLOAD = {"name": "headneck256", "levels": 3, "iters": [100, 50, 25]}
+# other single-registration workloads (--workload): the pelvic CT-to-CBCT-like
+# case, 512 x 512 x 160, 6 structures (built on the GPU: host generation of
+# 42 M voxels takes minutes)
+WORKLOADS = {"headneck256": dict(WORKLOAD), "pelvis512": {"name": "pelvis512", "levels": 3, "iters": [100, 50, 25]}}
 # bounded sample of the same workload for the CPU oracle: same case, same
 # pyramid, iterations cut to 8 / 4 / 2 (about 16.5 M voxel-iterations)
 ORACLE_SAMPLE_ITERS = [8, 4, 2]
 FORCE_BYTES_PER_VOXEL = {True: 35, False: 33}   # contour terms on / off, FP32 images
+FORCE_BYTES_PER_VOXEL_16 = {True: 31, False: 29}   # the same with 16-bit images
 
 
 def parse():
@@ -58,6 +63,10 @@ def parse():
                          "under a 160 GB device budget, p50/p99 latency against plain FP32 one at "
                          "a time")
     ap.add_argument("--batch-n", type=int, default=32, help="cases in the batch / serving mix")
+    ap.add_argument("--workload", default="headneck256", choices=sorted(WORKLOADS),
+                    help="single-registration workload (default: the 256x256x96 head-and-neck case)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="image storage type of the registration (arithmetic stays FP32)")
     ap.add_argument("--rates", default="1,2,4,8,16,32,64", help="serve: arrival rates (requests/s)")
     return ap.parse_args()
 
@@ -91,9 +100,10 @@ def whole_job_value(world: int, vox_iters_per_step: int, steps: int, max_total_m
     return world * vox_iters_per_step * steps / (max_total_ms / 1e3)
 
 
-def workload_config(case, n_gpus):
+def workload_config(case, n_gpus, storage="f32"):
     nz, ny, nx = case.shape
-    return {"workload": f"{WORKLOAD['name']}: {nx}x{ny}x{nz} float32 CT, {case.k} uint8 structure "
+    img = {"f32": "float32", "f16": "float16", "bf16": "bfloat16"}[storage]
+    return {"workload": f"{WORKLOAD['name']}: {nx}x{ny}x{nz} {img} CT, {case.k} uint8 structure "
                         f"masks, {WORKLOAD['levels']}-level pyramid "
                         f"{'/'.join(map(str, WORKLOAD['iters']))} iterations, FIXED stop",
             "shape_zyx": [nz, ny, nx], "masks": case.k, "levels": WORKLOAD["levels"],
@@ -259,17 +269,29 @@ def run_cgdir(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case = phantom.make_case(WORKLOAD["name"], index=replica_case_index(rank))
+    WORKLOAD.update(WORKLOADS[args.workload])
+    if args.workload == "headneck256":
+        case = phantom.make_case(WORKLOAD["name"], index=replica_case_index(rank))
+    else:                                     # built on the GPU, host copies for the oracle
+        dc = phantom.make_case_device(WORKLOAD["name"], index=replica_case_index(rank), device=dev)
+        dc.static, dc.moving = dc.static.cpu().numpy(), dc.moving.cpu().numpy()
+        dc.static_masks, dc.moving_masks = dc.static_masks.cpu().numpy(), dc.moving_masks.cpu().numpy()
+        dc.u_gt = dc.body = None
+        case = dc
+        torch.cuda.empty_cache()
     L, iters = WORKLOAD["levels"], WORKLOAD["iters"]
     vox_iters = phantom.voxel_iters(case.shape, L, iters)
     N = int(np.prod(case.shape))
+    img_t = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.storage]
+    img_code = {"f32": cg.CGDIR_F32, "f16": cg.CGDIR_F16, "bf16": cg.CGDIR_BF16}[args.storage]
 
-    S = torch.from_numpy(case.static).to(dev)
-    M = torch.from_numpy(case.moving).to(dev)
+    S = torch.from_numpy(case.static).to(dev).to(img_t)
+    M = torch.from_numpy(case.moving).to(dev).to(img_t)
     SM = [torch.from_numpy(m).to(dev) for m in case.static_masks]
     MM = [torch.from_numpy(m).to(dev) for m in case.moving_masks]
     dvf = torch.empty((3,) + case.shape, dtype=torch.float32, device=dev)
-    kw = dict(levels=L, iters=iters, lam=case.lam, sign=case.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    kw = dict(levels=L, iters=iters, lam=case.lam, sign=case.signs, stop_mode=cg.CGDIR_STOP_FIXED,
+              storage_dtype=img_code)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
     def barrier():
@@ -278,7 +300,7 @@ def run_cgdir(args):
 
     ctx = cg.Context(local)
     stream = torch.cuda.current_stream(dev)
-    tuning = ctx.autotune(case.shape, case.k, L)          # per-level kernel schedule
+    tuning = ctx.autotune(case.shape, case.k, L, storage_dtype=img_code)   # per-level kernel schedule
     for _ in range(args.warmup):
         ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
     torch.cuda.synchronize()
@@ -316,7 +338,8 @@ def run_cgdir(args):
     # ---- end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        Sh, Mh = torch.from_numpy(case.static).pin_memory(), torch.from_numpy(case.moving).pin_memory()
+        Sh = torch.from_numpy(case.static).to(img_t).pin_memory()
+        Mh = torch.from_numpy(case.moving).to(img_t).pin_memory()
         SMh = [torch.from_numpy(m).pin_memory() for m in case.static_masks]
         MMh = [torch.from_numpy(m).pin_memory() for m in case.moving_masks]
         dvf_h = torch.empty((3,) + case.shape, dtype=torch.float32).pin_memory()
@@ -330,7 +353,7 @@ def run_cgdir(args):
             _, st = ctx.register(Sh, Mh, SMh, MMh, dvf_out=dvf_h, **kw)
             et.append(time.perf_counter() - t0)
         t_max = reduce_max(sum(et), dev)
-        h2d = 2 * N * 4 + 2 * case.k * N
+        h2d = 2 * N * S.element_size() + 2 * case.k * N
         d2h = 3 * N * 4 + L * (max(iters) + 1) * 8 + 4 * 8 * 4
         e2e = {"value": whole_job_value(world, vox_iters, args.steps, 1e3 * t_max), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -341,12 +364,13 @@ def run_cgdir(args):
     roofline = None
     if fine and fine[0]["launches"]:
         avg_ms = fine[0]["total_ms"] / fine[0]["launches"]
-        bytes_per_launch = FORCE_BYTES_PER_VOXEL[True] * N
+        bytes_per_launch = (FORCE_BYTES_PER_VOXEL if args.storage == "f32" else FORCE_BYTES_PER_VOXEL_16)[True] * N
         peak, peak_src = measured_peaks()
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": "force step = k_warp_pass + k_force_pass (finest level, contour terms on)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": force_traffic_record(case),
+                    "traffic": force_traffic_record(case) if (args.workload, args.storage) == ("headneck256", "f32")
+                    else None,
                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                     "launches": fine[0]["launches"], "peak_source": peak_src}
 
@@ -360,8 +384,9 @@ def run_cgdir(args):
         lat = sorted(step_ms)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_total_ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic", "config": workload_config(case, world),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.storage == "f32" else f"{args.storage} images, f32 arithmetic",
+                "data": "synthetic", "config": workload_config(case, world, args.storage),
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "per": "registration"},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
