@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="image storage type of the registration (arithmetic stays FP32)")
     ap.add_argument("--rates", default="1,2,4,8,16,32,64", help="serve: arrival rates (requests/s)")
+    ap.add_argument("--inflight", type=int, default=64, help="serve: requests in flight at most")
     return ap.parse_args()
 
 
@@ -597,7 +598,7 @@ def run_serve(args):
     rows = []
     l0 = cg.launch_count()
     with cg.Context(0, mem_budget_bytes=MIX["budget_gb"] << 30) as sctx, cg.Context(0) as pctx:
-        sctx.set_max_inflight(64)
+        sctx.set_max_inflight(args.inflight)
         sctx.set_autotune(True)
         pctx.set_autotune(True)
         everyone = (np.zeros(len(cases)), np.arange(len(cases)))
@@ -623,7 +624,7 @@ def run_serve(args):
             "steps": len(rates), "warmup": 2, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 images, f32 arithmetic",
             "data": "synthetic", "config": dict(mix_config(cases), budget_gb=MIX["budget_gb"],
-                                                 max_inflight=64, arrivals="Poisson, seeded"),
+                                                 max_inflight=args.inflight, arrivals="Poisson, seeded"),
             "latency_ms": {"p50": top["served_f16"]["p50_ms"], "p99": top["served_f16"]["p99_ms"],
                            "per": "registration, arrival to completion", "at_rate": top["rate_per_s"]},
             "gpu_launches": int(launches), "clocks": clk.summary(), "rates": rows}

@@ -3,7 +3,10 @@
 configuration and image storage type (FP32 / FP16 / BF16; the oracle always
 runs on the FP32 images).  Test infrastructure, run by hand on a GPU machine:
 
-    python tests/accuracy_table.py > gpurun_out/accuracy.json
+    python tests/accuracy_table.py [--full] > gpurun_out/accuracy.json
+
+(--full runs the 512 x 512 x 160 case for its whole 100/50/25 iterations:
+about 7 minutes of the oracle on 16 host cores.)
 
 Prints one JSON object: per case the RMS difference over the whole volume
 and over the body, in voxels, beside the RMS of the ground-truth DVF.
@@ -27,8 +30,9 @@ def main():
     import phantom
 
     dev = torch.device("cuda", 0)
+    full = "--full" in sys.argv            # the pelvic case at its full 100/50/25 iterations
     runs = [("phantom64", None, 1, [100]), ("headneck256", None, 3, [100, 50, 25]),
-            ("pelvis512", None, 3, [10, 5, 2])]
+            ("pelvis512", None, 3, [100, 50, 25] if full else [10, 5, 2])]
     out = {}
     with cg.Context(0) as ctx:
         for name, shape, levels, iters in runs:
