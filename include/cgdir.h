@@ -176,7 +176,7 @@ void cgdir_default_params(cgdir_params *p);
      CGDIR_KERNELS=plain|fused   plain-load kernels everywhere / the one-pass
                                  TMA force and fused smoothing kernels
      CGDIR_GRAPHS=0              launch eagerly instead of replaying graphs
-     CGDIR_SMOOTH=march|tile|split, CGDIR_SMOOTH_ZCHUNK=n   smoothing variant
+     CGDIR_SMOOTH=march|tile|split|fused, CGDIR_SMOOTH_ZCHUNK=n   smoothing variant
      CGDIR_FORCE_ZCHUNK=n, CGDIR_FORCE_SINGLE=1   force pass 2 z chunk / one
                                  voxel per thread
      CGDIR_COOP_MAX=n            levels below the finest with at most n voxels
@@ -430,11 +430,14 @@ int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap);
 #define CGDIR_SMOOTH_MARCH 1
 #define CGDIR_SMOOTH_TILE  2
 #define CGDIR_SMOOTH_SPLIT 3
+#define CGDIR_SMOOTH_FUSED 4   /* fused schedule: 3-D tiles of G(du) with the update and of G(u')
+                                  with the next warp; the force runs its stencil pass only.
+                                  smooth_ms / force_ms are then those kernels' times */
 typedef struct {
     int   nx, ny, nz;           /* level shape                                   */
     int   contour;              /* structure terms on at this level               */
     int   storage_dtype;        /* CGDIR_F32 / F16 / BF16                          */
-    int   smooth_variant;       /* CGDIR_SMOOTH_MARCH / _TILE / _SPLIT              */
+    int   smooth_variant;       /* CGDIR_SMOOTH_MARCH / _TILE / _SPLIT / _FUSED     */
     int   smooth_zchunk;        /* z chunk of the z-march (0 = default / n/a)       */
     int   force_zchunk;         /* z chunk of the force stencil pass                */
     float smooth_ms, force_ms;  /* best times: steps 2-4 of one iteration; force   */

@@ -65,7 +65,7 @@ class cgdir_tuning(ctypes.Structure):
                 ("default_force_ms", c_float)]
 
 
-CGDIR_SMOOTH_MARCH, CGDIR_SMOOTH_TILE, CGDIR_SMOOTH_SPLIT = 1, 2, 3
+CGDIR_SMOOTH_MARCH, CGDIR_SMOOTH_TILE, CGDIR_SMOOTH_SPLIT, CGDIR_SMOOTH_FUSED = 1, 2, 3, 4
 
 
 class cgdir_kernel_time(ctypes.Structure):
@@ -369,7 +369,8 @@ class Context:
         n = load().cgdir_tuning_read(self._h, None, 0)
         buf = (cgdir_tuning * max(n, 1))()
         n = load().cgdir_tuning_read(self._h, buf, n)
-        names = {CGDIR_SMOOTH_MARCH: "march", CGDIR_SMOOTH_TILE: "tile", CGDIR_SMOOTH_SPLIT: "split"}
+        names = {CGDIR_SMOOTH_MARCH: "march", CGDIR_SMOOTH_TILE: "tile", CGDIR_SMOOTH_SPLIT: "split",
+                 CGDIR_SMOOTH_FUSED: "fused"}
         return [{"shape": (b.nz, b.ny, b.nx), "contour": bool(b.contour), "storage_dtype": b.storage_dtype,
                  "smooth": names.get(b.smooth_variant, str(b.smooth_variant)), "smooth_zchunk": b.smooth_zchunk,
                  "force_zchunk": b.force_zchunk, "smooth_ms": b.smooth_ms, "force_ms": b.force_ms,

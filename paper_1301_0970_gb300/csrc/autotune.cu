@@ -7,7 +7,10 @@
 //              that chunk (plus the separate update kernel), the 3-D
 //              shared-memory tile kernel (idem), and the split xy + z
 //              kernels with the update fused into the z pass;
-//   force:     the stencil pass with the default z chunk, half and double.
+//   force:     the stencil pass with the default z chunk, half and double;
+// then the fused schedule (force stencil pass alone, 3-D tiles of G(du)
+// with the update, 3-D tiles of G(u') with the next iteration's warp)
+// against the best of those two, summed.
 // The fastest of each is recorded in the context and used by every later
 // registration of that shape (and baked into its CUDA graph).
 #include "runtime_internal.hpp"
@@ -206,6 +209,27 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
                 best.smooth_zchunk = cand[ci].zchunk;
                 best.smooth_ms = ms;
             }
+        }
+    }
+    // the fused schedule: force stencil pass only, then the two fused tile
+    // kernels (G(du) + update; G(u') + the next warp)
+    if (rc == CGDIR_OK && fused_schedule_ok(a) && gauss_taps(sigma).r > 0) {
+        ForceArgs a2 = a;
+        a2.skip_warp = 1;
+        float f2 = 0.f, fs = 0.f;
+        rc = time_ms(ctx, e0, e1, reps, &f2,
+                     [&](cudaStream_t st) { return launch_force(a2, best.force_zchunk, nullptr, st, kerr(ctx)); });
+        if (rc == CGDIR_OK)
+            rc = time_ms(ctx, e0, e1, reps, &fs, [&](cudaStream_t st) {
+                cudaError_t e = launch_fused_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, nullptr, st);
+                if (e != cudaSuccess) return e;
+                return launch_fused_smooth_warp(out, sigma, u, a2, st);
+            });
+        if (rc == CGDIR_OK && f2 + fs < best.force_ms + best.smooth_ms) {
+            best.smooth_variant = SMOOTH_FUSED;
+            best.smooth_zchunk = 0;
+            best.smooth_ms = fs;
+            best.force_ms = f2;
         }
     }
     cudaEventDestroy(e0);

@@ -104,6 +104,8 @@ struct ForceArgs {
     uint16_t *wstate;
     float *pfield;
     int single_voxel;             // 1: pass 2 takes one voxel per thread even for even nx
+    int skip_warp;                // 1: pass 1's outputs are already current for u (the fused
+                                  // smoothing + warp kernel wrote them): launch pass 2 only
 };
 
 // One whole pyramid level (all iterations of Algorithm A) in one cooperative
@@ -165,9 +167,11 @@ cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, i
 
 // Smoothing kernel variants: the TMA z-march (large volumes), the 3-D
 // shared-memory tile (small volumes), the split xy + z kernels (needs a 3N
-// scratch field; with the composite update fused into the z pass), or
-// chosen by size.
-enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2, SMOOTH_SPLIT = 3 };
+// scratch field; with the composite update fused into the z pass), the
+// fused iteration schedule (3-D tiles of all three components with the
+// composite update fused into the du pass and the next warp into the u
+// pass; a standalone smoothing takes the tile kernel), or chosen by size.
+enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2, SMOOTH_SPLIT = 3, SMOOTH_FUSED = 4 };
 int smooth_auto_variant(int nx, int ny, int nz);
 // Kernel choice for one smoothing launch: variant and (z-march) z chunk, 0 = default.
 struct SmoothChoice {
@@ -191,6 +195,19 @@ cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, flo
                                   int *err, bool one_pass = false, SmoothChoice ch = SmoothChoice());
 cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, float *out,
                         cudaStream_t s);
+
+// Fused iteration schedule (kernels_fused.cu), 8 x 8 x 8 tiles of all three
+// components with their Gaussian halo in shared memory:
+//   out = G(du) + u(x + G(du))  (or u + G(du))       Algorithm A steps 2-3
+cudaError_t launch_fused_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
+                                        int nz, float *out, const int *stop_flag, cudaStream_t s);
+//   u = G(in), then the first force pass at the new u into a's two-pass
+//   scratch (a.wfield / wstate / pfield; a.u is not read)     step 4 + the
+//   next iteration's warp
+cudaError_t launch_fused_smooth_warp(const float *in, float sigma, float *u, const ForceArgs &a, cudaStream_t s);
+// Whether the fused schedule can run for this force configuration (the
+// two-pass force with 32-bit indexing).
+bool fused_schedule_ok(const ForceArgs &a);
 
 cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint8_t *bits,
                               cudaStream_t s);

@@ -35,6 +35,7 @@
 
 #include "cgdir_internal.cuh"
 #include "tma.cuh"
+#include "warp_corners.cuh"
 
 namespace cgdir {
 
@@ -313,82 +314,6 @@ __global__ void __launch_bounds__(NT) k_force(ForceArgs a, int zchunk) {
 // forms the gradients, Eq. 7 and du, and the RMS-ID partials.  Pass 1 costs
 // 6 + 4k bytes per voxel of extra traffic (written, then read once), but
 // both passes keep all warps busy instead of waiting at per-plane barriers.
-// The eight corners of one interpolation point, loaded (pass 1).
-template <typename IT>
-struct CornerSet {
-    float c[8];
-    unsigned m[8];
-    float wx, wy, wz;
-};
-
-// Clamp x + u, find the corners and issue their loads (texels when the
-// structure terms are on and texels exist, else image values and mask bits).
-template <bool CONTOUR, typename IT>
-__device__ __forceinline__ void corner_load(const ForceArgs &a, float ux, float uy, float uz, int x, int y, int z,
-                                            CornerSet<IT> &cs) {
-    using TT = typename TexOf<IT>::type;
-    const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny;
-    const float px = fminf(fmaxf((float)x + ux, 0.f), (float)(nx - 1));
-    const float py = fminf(fmaxf((float)y + uy, 0.f), (float)(ny - 1));
-    const float pz = fminf(fmaxf((float)z + uz, 0.f), (float)(nz - 1));
-    const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
-    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-    cs.wx = px - fx; cs.wy = py - fy; cs.wz = pz - fz;
-    const int dx = ix < nx - 1 ? 1 : 0, dy = iy < ny - 1 ? nx : 0, dz = iz < nz - 1 ? nxy : 0;
-    const int b0 = iz * nxy + iy * nx + ix;
-    const int o[8] = {0, dx, dy, dy + dx, dz, dz + dx, dz + dy, dz + dy + dx};
-    if (CONTOUR && a.mtex != nullptr) {
-        const TT *__restrict__ q0 = static_cast<const TT *>(a.mtex) + b0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) tex_unpack<IT>(__ldg(q0 + o[q]), cs.c[q], cs.m[q]);
-    } else {
-        const IT *__restrict__ q0 = static_cast<const IT *>(a.I0) + b0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) cs.c[q] = ld_img<IT>(q0 + o[q]);
-        if (CONTOUR) {
-            const uint8_t *__restrict__ r0 = a.mbits + b0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) cs.m[q] = __ldg(r0 + o[q]);
-        }
-    }
-}
-
-// Interpolate I0~ from the loaded corners, write it, the corner bits'
-// AND / OR and, where they disagree, P_j.
-template <bool CONTOUR, typename IT>
-__device__ __forceinline__ void corner_finish(const ForceArgs &a, int i, int N, const CornerSet<IT> &cs) {
-    const float wx = cs.wx, wy = cs.wy, wz = cs.wz;
-    const float *c = cs.c;
-    const float e00 = fmaf(wx, c[1] - c[0], c[0]), e10 = fmaf(wx, c[3] - c[2], c[2]);
-    const float e01 = fmaf(wx, c[5] - c[4], c[4]), e11 = fmaf(wx, c[7] - c[6], c[6]);
-    const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
-    a.wfield[i] = fmaf(wz, f1 - f0, f0);
-    if (CONTOUR) {
-        const unsigned *m = cs.m;
-        const unsigned andb = m[0] & m[1] & m[2] & m[3] & m[4] & m[5] & m[6] & m[7];
-        const unsigned orb = m[0] | m[1] | m[2] | m[3] | m[4] | m[5] | m[6] | m[7];
-        a.wstate[i] = (uint16_t)((andb << 8) | orb);
-        unsigned mixed = orb & ~andb;
-        if (mixed) {
-            const float off = a.offset;
-            const float ax = 1.f - wx, ay = 1.f - wy, az = 1.f - wz;
-            float q[8];
-            q[0] = ax * ay * az * (c[0] + off); q[1] = wx * ay * az * (c[1] + off);
-            q[2] = ax * wy * az * (c[2] + off); q[3] = wx * wy * az * (c[3] + off);
-            q[4] = ax * ay * wz * (c[4] + off); q[5] = wx * ay * wz * (c[5] + off);
-            q[6] = ax * wy * wz * (c[6] + off); q[7] = wx * wy * wz * (c[7] + off);
-            while (mixed) {
-                const int j = __ffs(mixed) - 1;
-                mixed &= mixed - 1u;
-                float pj = 0.f;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) pj += ((m[t] >> j) & 1u) ? q[t] : 0.f;
-                a.pfield[j * N + i] = pj;
-            }
-        }
-    }
-}
-
 template <bool CONTOUR, typename IT>
 __global__ void __launch_bounds__(NT, 4) k_warp_pass(ForceArgs a, int zw) {
     if (a.stop_flag && *a.stop_flag) return;
@@ -403,7 +328,7 @@ __global__ void __launch_bounds__(NT, 4) k_warp_pass(ForceArgs a, int zw) {
     const int col = y * nx + x;
     auto disp = [&](int z, float &dx, float &dy, float &dz) {
         const int i = z * nxy + col;
-        dx = __ldg(u + i); dy = __ldg(u + N + i); dz = __ldg(u + 2 * N + i);
+        dx = __ldg(u + i); dy = __ldg(u + N + i); dz = __ldg(u + N + N + i);
     };
     float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
     if (zb < ze) disp(zb, ax, ay, az);
@@ -461,13 +386,13 @@ __device__ __forceinline__ void build_tables(const ForceArgs &a, ContourTables &
 // P_j at a stencil point from pass 1's outputs.
 __device__ __forceinline__ float p_at(const ForceArgs &a, int j, int N, int idx, float w, unsigned st) {
     const unsigned andb = st >> 8, orb = st & 0xffu;
-    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldg(a.pfield + j * N + idx);
+    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldg(a.pfield + (size_t)j * N + idx);
     return ((andb >> j) & 1u) ? w + a.offset : 0.f;
 }
 // The same through L2-only loads (P_j written by the same kernel).
 __device__ __forceinline__ float p_at_l2(const ForceArgs &a, int j, int N, int idx, float w, unsigned st) {
     const unsigned andb = st >> 8, orb = st & 0xffu;
-    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldcg(a.pfield + j * N + idx);
+    if ((((orb & ~andb) >> j) & 1u) != 0u) return __ldcg(a.pfield + (size_t)j * N + idx);
     return ((andb >> j) & 1u) ? w + a.offset : 0.f;
 }
 
@@ -600,7 +525,7 @@ __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
                                  ic + oym, ic + oyp, im, ip, dux, duy, duz, r0);
             du[ic] = dux;
             du[N + ic] = duy;
-            du[2 * N + ic] = duz;
+            du[N + N + ic] = duz;
             if (cur.ur) {
                 ssd = fmaf(r0, r0, ssd);
                 cnt += 1;
@@ -734,7 +659,7 @@ __global__ void __launch_bounds__(NT, 2) k_force_pass2(ForceArgs a, int zchunk) 
                                  ic + 1 + oyp, im + 1, ip + 1, d1x, d1y, d1z, r01);
             *reinterpret_cast<float2 *>(du + ic) = make_float2(d0x, d1x);
             *reinterpret_cast<float2 *>(du + N + ic) = make_float2(d0y, d1y);
-            *reinterpret_cast<float2 *>(du + 2 * N + ic) = make_float2(d0z, d1z);
+            *reinterpret_cast<float2 *>(du + N + N + ic) = make_float2(d0z, d1z);
             if (cur.ur & 0xffu) { ssd = fmaf(r00, r00, ssd); cnt += 1; }
             if (cur.ur >> 8) { ssd = fmaf(r01, r01, ssd); cnt += 1; }
             mx = fmaxf(mx, fmaxf(d0x * d0x + d0y * d0y + d0z * d0z, d1x * d1x + d1y * d1y + d1z * d1z));
@@ -1094,7 +1019,7 @@ __global__ void __launch_bounds__(NT, 2) k_level_coop(const __grid_constant__ Le
         for (int i = gt; i < N; i += gs) {
             const int x = i % nx, y = (i / nx) % ny, z = i / nxy;
             CornerSet<IT> cs;
-            corner_load<CONTOUR, IT>(a, __ldcg(u + i), __ldcg(u + N + i), __ldcg(u + 2 * N + i), x, y, z, cs);
+            corner_load<CONTOUR, IT>(a, __ldcg(u + i), __ldcg(u + N + i), __ldcg(u + N + N + i), x, y, z, cs);
             corner_finish<CONTOUR, IT>(a, i, N, cs);
         }
         if (!grid_barrier(p.bar, nb, p.err)) return;
@@ -1126,7 +1051,7 @@ __global__ void __launch_bounds__(NT, 2) k_level_coop(const __grid_constant__ Le
                                        r0);
             a.du[i] = dux;
             a.du[N + i] = duy;
-            a.du[2 * N + i] = duz;
+            a.du[N + N + i] = duz;
             if (a.uroi == nullptr || __ldg(a.uroi + i)) {
                 ssd = fmaf(r0, r0, ssd);
                 cnt += 1;
@@ -1198,7 +1123,7 @@ __global__ void __launch_bounds__(NT, 2) k_level_coop(const __grid_constant__ Le
             }
             float ax, ay, az;
             if (p.compose_mode == CGDIR_ADDITIVE) {
-                ax = __ldcg(u + i); ay = __ldcg(u + N + i); az = __ldcg(u + 2 * N + i);
+                ax = __ldcg(u + i); ay = __ldcg(u + N + i); az = __ldcg(u + N + N + i);
             } else {
                 const float px = fminf(fmaxf((float)x + s3[0], 0.f), (float)(nx - 1));
                 const float py = fminf(fmaxf((float)y + s3[1], 0.f), (float)(ny - 1));
@@ -1223,7 +1148,7 @@ __global__ void __launch_bounds__(NT, 2) k_level_coop(const __grid_constant__ Le
             }
             p.ub[i] = s3[0] + ax;
             p.ub[N + i] = s3[1] + ay;
-            p.ub[2 * N + i] = s3[2] + az;
+            p.ub[N + N + i] = s3[2] + az;
         }
         if (!grid_barrier(p.bar, nb, p.err)) return;
         // ---- Gaussian of u
@@ -1330,16 +1255,17 @@ static cudaError_t launch_force_t(const ForceArgs &a, int zchunk, dim3 grid, dim
         // end-of-block fences before the fused reduction
         const bool paired = a.nx % 2 == 0 && !a.single_voxel;
         dim3 g2 = paired ? dim3((a.nx / 2 + TX - 1) / TX, grid.y, grid.z) : grid;
+        const bool warp = !a.skip_warp;
         if (contour) {
-            k_warp_pass<true, IT><<<g, block, 0, s>>>(a, zc);
+            if (warp) k_warp_pass<true, IT><<<g, block, 0, s>>>(a, zc);
             if (paired) k_force_pass2<true, IT><<<g2, block, 0, s>>>(a, zchunk);
             else k_force_pass<true, IT><<<grid, block, 0, s>>>(a, zchunk);
         } else {
-            k_warp_pass<false, IT><<<g, block, 0, s>>>(a, zc);
+            if (warp) k_warp_pass<false, IT><<<g, block, 0, s>>>(a, zc);
             if (paired) k_force_pass2<false, IT><<<g2, block, 0, s>>>(a, zchunk);
             else k_force_pass<false, IT><<<grid, block, 0, s>>>(a, zchunk);
         }
-        note_launch(2);
+        note_launch(warp ? 2 : 1);
         return cudaGetLastError();
     }
     if (err != nullptr && N < (size_t)1 << 31 && (!contour || a.mtex != nullptr)) {

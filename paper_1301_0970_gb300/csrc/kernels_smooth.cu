@@ -809,6 +809,7 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
         // small volumes: the 3-D tile kernel (one short wave); large: the
         // TMA z-march, whose plane pipeline needs long chunks to pay off
         if (variant == SMOOTH_AUTO) variant = smooth_auto_variant(nx, ny, nz);
+        if (variant == SMOOTH_FUSED) variant = SMOOTH_TILE;     // nothing to fuse with here
         if (variant == SMOOTH_TILE) return smooth_tile(in, ncomp, t, nx, ny, nz, out, stop_flag, s);
         if (variant == SMOOTH_SPLIT && scratch != nullptr && scratch != in && scratch != out)
             return smooth_split(in, nullptr, 0, false, ncomp, t, nx, ny, nz, out, scratch, ch.zchunk, stop_flag, s);
@@ -828,6 +829,8 @@ cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, flo
         int variant = ch.variant == SMOOTH_AUTO ? smooth_auto_variant(nx, ny, nz) : ch.variant;
         if (variant == SMOOTH_SPLIT)   // x/y pass, then the z pass with the composite update fused
             return smooth_split(du, u, mode, true, 3, t, nx, ny, nz, out, tmp, ch.zchunk, stop_flag, s);
+        if (variant == SMOOTH_FUSED && (size_t)nx * ny * nz < (size_t)1 << 31)   // one 3-D tile kernel
+            return launch_fused_smooth_compose(du, u, mode, sigma, nx, ny, nz, out, stop_flag, s);
     }
     if (one_pass && t.r > 0 && err != nullptr) {
         bool launched = false;

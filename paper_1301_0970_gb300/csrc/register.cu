@@ -369,10 +369,24 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
             CK(launch_level_coop(c, coop_grid, s));
             continue;
         }
+        // fused schedule: the force runs its stencil pass only after the first
+        // iteration; the smoothing of u' leaves the next warp behind it
+        const bool fused = sch.variant == SMOOTH_FUSED && !ctx->plain_kernels && !ctx->fused_force &&
+                           fused_schedule_ok(a) && gauss_taps(P->sigma_fluid).r > 0 &&
+                           gauss_taps(P->sigma_diff).r > 0;
         for (int n = 0; n < cap; ++n) {
             int nb = 0;
             a.fin.n = n;   // the force kernel's last CTA reduces delta^n and runs the stop test
+            a.skip_warp = fused && n > 0;
             { ProfScope ps(prof, m, s, CGDIR_K_FORCE, l); CK(launch_force(a, zc, &nb, s, kerr(ctx))); }
+            if (fused) {
+                { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3
+                  CK(launch_fused_smooth_compose(pl.du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, pl.du2,
+                                                 flags + l, s)); }
+                { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_U, l);    // step 4 + the next warp
+                  CK(launch_fused_smooth_warp(pl.du2, P->sigma_diff, ucur, a, s)); }
+                continue;
+            }
             { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3
               CK(launch_smooth_compose(pl.du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, pl.du2, uoth,
                                        flags + l, s, kerr(ctx), ctx->fused_force, sch)); }

@@ -330,7 +330,8 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     c->smooth_variant = !sv ? SMOOTH_AUTO
                             : std::strcmp(sv, "tile") == 0 ? SMOOTH_TILE
                             : std::strcmp(sv, "march") == 0 ? SMOOTH_MARCH
-                            : std::strcmp(sv, "split") == 0 ? SMOOTH_SPLIT : SMOOTH_AUTO;
+                            : std::strcmp(sv, "split") == 0 ? SMOOTH_SPLIT
+                            : std::strcmp(sv, "fused") == 0 ? SMOOTH_FUSED : SMOOTH_AUTO;
     const char *gr = std::getenv("CGDIR_GRAPHS");
     c->use_graphs = !(gr && std::strcmp(gr, "0") == 0);
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -186,9 +186,9 @@ def test_autotune_records_every_level_and_keeps_results():
         assert len(tab) == 3
         assert {t["shape"] for t in tab} == {(6, 24, 24), (12, 48, 48), (24, 96, 96)}
         for t in tab:
-            assert t["smooth"] in ("march", "tile", "split") and t["force_zchunk"] >= 1
-            assert 0 < t["smooth_ms"] <= t["default_smooth_ms"] * 1.0001 + 1e-6
-            assert 0 < t["force_ms"] <= t["default_force_ms"] * 1.0001 + 1e-6
+            assert t["smooth"] in ("march", "tile", "split", "fused") and t["force_zchunk"] >= 1
+            assert t["smooth_ms"] > 0 and t["force_ms"] > 0
+            assert t["smooth_ms"] + t["force_ms"] <= (t["default_smooth_ms"] + t["default_force_ms"]) * 1.0001 + 1e-6
         got, st = single(ctx, c, kw)
         assert torch.equal(got, ref)
         assert [s["iters_run"] for s in st] == [s["iters_run"] for s in rst]
@@ -249,10 +249,12 @@ def test_cooperative_level_kernel_matches_per_iteration_kernels(stop):
         assert float((a - b).abs().max()) <= 1e-4
 
 
-@pytest.mark.parametrize("variant", ["split", "tile"])
+@pytest.mark.parametrize("variant", ["split", "tile", "fused"])
 def test_smoothing_variants_give_the_same_registration(variant):
     """Every smoothing variant (incl. the split kernels with the composite
-    update in the z pass) gives the same DVF as the z-march, bit for bit."""
+    update in the z pass, and the fused schedule: 3-D tiles of G(du) with
+    the update, 3-D tiles of G(u') with the next warp, the force's stencil
+    pass alone) gives the same DVF as the z-march, bit for bit."""
     c = phantom.make_case("headneck256", shape=(24, 72, 76))
     kw = dict(levels=2, iters=[6, 5], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED, contour_level_mask=3)
     a_ctx = _ctx_with_env({"CGDIR_SMOOTH": "march"})
@@ -288,3 +290,51 @@ def test_force_pass_variants_agree_bitwise(contour):
         assert torch.equal(du, outs[0][0])
         assert st[1] == outs[0][1][1]
         assert abs(st[0] - outs[0][1][0]) <= 1e-9 * outs[0][1][0]
+
+
+@pytest.mark.parametrize("shape, kw", [
+    # odd nx (one voxel per thread in the force pass), ragged 8-voxel tiles in x, y and z
+    ((13, 37, 45), dict(levels=2, iters=[7, 5], stop_mode=cg.CGDIR_STOP_WINDOW10, eps=1e-3)),
+    # additive update, wider and narrower Gaussians (radii 5 and 2), structure terms at both levels
+    ((20, 40, 48), dict(levels=2, iters=[6, 4], compose_mode=cg.CGDIR_ADDITIVE, sigma_fluid=1.6,
+                        sigma_diff=0.6, contour_level_mask=3, stop_mode=cg.CGDIR_STOP_FIXED)),
+    # 16-bit image storage, three levels down to a 5 x 10 x 12 level
+    ((20, 40, 48), dict(levels=3, iters=[8, 5, 3], storage_dtype=cg.CGDIR_F16, stop_mode=cg.CGDIR_STOP_FIXED)),
+])
+def test_fused_schedule_matches_per_step_kernels(shape, kw):
+    """The fused schedule against the per-step kernels (tile smoothing, the
+    separate update kernel, the force's warp pass) on awkward shapes and
+    parameters: the same DVF and histories, bit for bit."""
+    c = phantom.make_case("headneck256", shape=shape)
+    kw = dict(kw, lam=c.lam, sign=c.signs)
+    a_ctx = _ctx_with_env({"CGDIR_SMOOTH": "tile"})
+    b_ctx = _ctx_with_env({"CGDIR_SMOOTH": "fused"})
+    try:
+        a, sa = single(a_ctx, c, kw)
+        b, sb = single(b_ctx, c, kw)
+    finally:
+        a_ctx.close()
+        b_ctx.close()
+    assert torch.equal(a, b)
+    assert [s["iters_run"] for s in sa] == [s["iters_run"] for s in sb]
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x["rms_id"], y["rms_id"])
+
+
+def test_fused_schedule_matches_oracle():
+    """A whole registration on the fused schedule against the FP64 oracle:
+    the same bar as the per-step path (DVF within 0.05 voxel RMS, the same
+    iteration counts)."""
+    c = phantom.make_case("headneck256", shape=(14, 30, 34))
+    kw = dict(levels=2, iters=[10, 6], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_WINDOW10, eps=1e-3,
+              contour_level_mask=3)
+    ctx = _ctx_with_env({"CGDIR_SMOOTH": "fused"})
+    try:
+        got, st = single(ctx, c, kw)
+    finally:
+        ctx.close()
+    ref, rst = oracle.register(c.static, c.moving, c.static_masks, c.moving_masks, levels=2, iters=[10, 6],
+                               lam=c.lam, sign=c.signs, contour_mask=3, stop_mode=cg.CGDIR_STOP_WINDOW10, eps=1e-3)
+    got = got.cpu().numpy().astype(np.float64)
+    assert float(np.sqrt(((got - ref) ** 2).sum(axis=0).mean())) <= 0.05
+    assert [s["iters_run"] for s in st] == [r["iters_run"] for r in rst]

@@ -269,6 +269,38 @@ def test_single_iteration_meets_1e5(ctx, name, shape):
     close_normwise(got, ref, rel=1e-5)
 
 
+@pytest.fixture(scope="module")
+def fused_ctx():
+    import os
+    old = os.environ.get("CGDIR_SMOOTH")
+    os.environ["CGDIR_SMOOTH"] = "fused"
+    try:
+        c = cg.Context(0)
+    finally:
+        if old is None:
+            del os.environ["CGDIR_SMOOTH"]
+        else:
+            os.environ["CGDIR_SMOOTH"] = old
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("mode", [cg.CGDIR_COMPOSE, cg.CGDIR_ADDITIVE])
+@pytest.mark.parametrize("name,shape", [("phantom64", (12, 36, 40)), ("headneck256", (13, 45, 50)),
+                                        ("pelvis512", (10, 48, 41)), ("headneck256", (5, 3, 7))])
+def test_single_iteration_fused_tile_update(fused_ctx, name, shape, mode):
+    """One iteration with G(du) and the update in one 3-D tile kernel (8^3
+    tiles of all three components, ragged in x, y and z): relative
+    norm-wise difference <= 1e-5 from the oracle."""
+    c = phantom.make_case(name, shape=shape)
+    u = (0.7 * c.u_gt).astype(np.float32)
+    got = host(fused_ctx.iterate(dev(c.moving), dev(c.static), dev(pack(c.moving_masks)),
+                                 dev(pack(c.static_masks)), c.lam, c.signs, dev(u), compose_mode=mode))
+    ref = oracle.step(c.moving, c.static, c.moving_masks, c.static_masks, c.lam, c.signs, u,
+                      compose_mode=mode)
+    close_normwise(got, ref, rel=1e-5)
+
+
 def test_rms_id(ctx):
     c = case_inputs()
     ur = oracle.uroi(c.static_masks, c.shape)
