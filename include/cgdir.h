@@ -312,9 +312,19 @@ int cgdir_smooth(cgdir_ctx *ctx, const float *in, int ncomp, float sigma, int nx
 
 /* Composite update (Algorithm A step 3): out = du + u(x + du(x)) (mode
    CGDIR_COMPOSE) or u + du (CGDIR_ADDITIVE), then, if sigma > 0, the
-   Gaussian of step 4 -- both in one pass.  out must not alias u or du. */
+   Gaussian of step 4.  out must not alias u or du. */
 int cgdir_compose(cgdir_ctx *ctx, const float *u, const float *du, int mode, float sigma,
                   int nx, int ny, int nz, float *out);
+
+/* Fluid smoothing and composite update (Algorithm A steps 2-3):
+   out = G(du) + u(x + G(du)(x)) (mode CGDIR_COMPOSE) or u + G(du)
+   (CGDIR_ADDITIVE), G the Gaussian of sigma voxels (0 <= sigma <= 2; 0 is
+   no smoothing).  The kernels are the ones a registration on this context
+   uses (the context's smoothing variant: under CGDIR_SMOOTH=fused, one 3-D
+   tile kernel).  Fields [3][nz][ny][nx] FP32 in device memory; out must not
+   alias u or du.  Errors: EINVAL, ENOMEM, ECUDA. */
+int cgdir_smooth_compose(cgdir_ctx *ctx, const float *du, const float *u, int mode, float sigma,
+                         int nx, int ny, int nz, float *out);
 
 /* One iteration, Algorithm A steps 1-4 (force, smooth du, compose, smooth u)
    from u_in to u_out (must not alias).  du_out (may be NULL) receives the

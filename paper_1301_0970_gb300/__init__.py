@@ -113,6 +113,8 @@ _SIGNATURES = {
     "cgdir_smooth": (c_int, [c_void_p, c_void_p, c_int, c_float, c_int, c_int, c_int, c_void_p]),
     "cgdir_compose": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_float, c_int, c_int, c_int,
                               c_void_p]),
+    "cgdir_smooth_compose": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_float, c_int, c_int, c_int,
+                                     c_void_p]),
     "cgdir_iterate": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                               POINTER(c_float), POINTER(c_int8), c_float, c_int, c_float, c_float,
                               c_int, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -500,6 +502,13 @@ class Context:
         out = _torch().empty_like(u) if out is None else out
         self._check(load().cgdir_compose(self._h, _ptr(u), _ptr(du), mode, sigma, *_dims(u), _ptr(out)),
                     "cgdir_compose")
+        return out
+
+    def smooth_compose(self, du, u, mode=CGDIR_COMPOSE, sigma=1.0, out=None):
+        """Algorithm A steps 2-3: G(du) + u(x + G(du)) (or u + G(du))."""
+        out = _torch().empty_like(u) if out is None else out
+        self._check(load().cgdir_smooth_compose(self._h, _ptr(du), _ptr(u), mode, sigma, *_dims(u), _ptr(out)),
+                    "cgdir_smooth_compose")
         return out
 
     def iterate(self, I0, T0, mbits, sbits, lam, sign, u, *, offset=1000.0, contour=True, uroi=None,

@@ -221,9 +221,9 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
                      [&](cudaStream_t st) { return launch_force(a2, best.force_zchunk, nullptr, st, kerr(ctx)); });
         if (rc == CGDIR_OK)
             rc = time_ms(ctx, e0, e1, reps, &fs, [&](cudaStream_t st) {
-                cudaError_t e = launch_fused_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, nullptr, st);
+                cudaError_t e = launch_fused_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, nullptr, kerr(ctx), st);
                 if (e != cudaSuccess) return e;
-                return launch_fused_smooth_warp(out, sigma, u, a2, st);
+                return launch_fused_smooth_warp(out, sigma, u, a2, kerr(ctx), st);
             });
         if (rc == CGDIR_OK && f2 + fs < best.force_ms + best.smooth_ms) {
             best.smooth_variant = SMOOTH_FUSED;

@@ -199,12 +199,14 @@ cudaError_t launch_warp(const float *f, const float *u, int nx, int ny, int nz, 
 // Fused iteration schedule (kernels_fused.cu), 8 x 8 x 8 tiles of all three
 // components with their Gaussian halo in shared memory:
 //   out = G(du) + u(x + G(du))  (or u + G(du))       Algorithm A steps 2-3
+// err: device word set to 1 if the bounded wait for the tile's TMA copy ran out.
 cudaError_t launch_fused_smooth_compose(const float *du, const float *u, int mode, float sigma, int nx, int ny,
-                                        int nz, float *out, const int *stop_flag, cudaStream_t s);
+                                        int nz, float *out, const int *stop_flag, int *err, cudaStream_t s);
 //   u = G(in), then the first force pass at the new u into a's two-pass
 //   scratch (a.wfield / wstate / pfield; a.u is not read)     step 4 + the
 //   next iteration's warp
-cudaError_t launch_fused_smooth_warp(const float *in, float sigma, float *u, const ForceArgs &a, cudaStream_t s);
+cudaError_t launch_fused_smooth_warp(const float *in, float sigma, float *u, const ForceArgs &a, int *err,
+                                     cudaStream_t s);
 // Whether the fused schedule can run for this force configuration (the
 // two-pass force with 32-bit indexing).
 bool fused_schedule_ok(const ForceArgs &a);

@@ -439,11 +439,26 @@ __global__ void __launch_bounds__(NT) k_smooth_tile(const float *__restrict__ in
     const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = tz * QZ;
     const size_t nxy = (size_t)nx * ny;
     const float *src = in + (size_t)comp * nxy * nz;
-    for (int p = tid; p < G::IN; p += NT) {
-        const int hx = p % AX, hy = (p / AX) % AY, hz = p / (AX * AY);
-        const int gx = clampi(x0 - R + hx, 0, nx - 1), gy = clampi(y0 - R + hy, 0, ny - 1),
-                  gz = clampi(z0 - R + hz, 0, nz - 1);
-        A[p] = __ldg(src + (size_t)gz * nxy + (size_t)gy * nx + gx);
+    // batches of loads in flight before their stores (a load-then-store loop
+    // would wait out one memory latency per element)
+    constexpr int kBatch = 16;
+    for (int p0 = 0; p0 < G::IN; p0 += kBatch * NT) {
+        float v[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int p = p0 + b * NT + tid;
+            if (p < G::IN) {
+                const int hx = p % AX, hy = (p / AX) % AY, hz = p / (AX * AY);
+                const int gx = clampi(x0 - R + hx, 0, nx - 1), gy = clampi(y0 - R + hy, 0, ny - 1),
+                          gz = clampi(z0 - R + hz, 0, nz - 1);
+                v[b] = __ldg(src + (size_t)gz * nxy + (size_t)gy * nx + gx);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int p = p0 + b * NT + tid;
+            if (p < G::IN) A[p] = v[b];
+        }
     }
     __syncthreads();
     for (int p = tid; p < G::XO; p += NT) {            // x pass: [AZ][AY][QX]
@@ -830,7 +845,7 @@ cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, flo
         if (variant == SMOOTH_SPLIT)   // x/y pass, then the z pass with the composite update fused
             return smooth_split(du, u, mode, true, 3, t, nx, ny, nz, out, tmp, ch.zchunk, stop_flag, s);
         if (variant == SMOOTH_FUSED && (size_t)nx * ny * nz < (size_t)1 << 31)   // one 3-D tile kernel
-            return launch_fused_smooth_compose(du, u, mode, sigma, nx, ny, nz, out, stop_flag, s);
+            return launch_fused_smooth_compose(du, u, mode, sigma, nx, ny, nz, out, stop_flag, err, s);
     }
     if (one_pass && t.r > 0 && err != nullptr) {
         bool launched = false;

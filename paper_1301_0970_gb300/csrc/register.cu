@@ -382,9 +382,9 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
             if (fused) {
                 { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3
                   CK(launch_fused_smooth_compose(pl.du, ucur, P->compose_mode, P->sigma_fluid, lx, ly, lz, pl.du2,
-                                                 flags + l, s)); }
+                                                 flags + l, kerr(ctx), s)); }
                 { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_U, l);    // step 4 + the next warp
-                  CK(launch_fused_smooth_warp(pl.du2, P->sigma_diff, ucur, a, s)); }
+                  CK(launch_fused_smooth_warp(pl.du2, P->sigma_diff, ucur, a, kerr(ctx), s)); }
                 continue;
             }
             { ProfScope ps(prof, m, s, CGDIR_K_SMOOTH_DU, l);   // steps 2 + 3

@@ -487,6 +487,24 @@ int cgdir_compose(cgdir_ctx *ctx, const float *u, const float *du, int mode, flo
     return CGDIR_OK;
 }
 
+int cgdir_smooth_compose(cgdir_ctx *ctx, const float *du, const float *u, int mode, float sigma, int nx, int ny,
+                         int nz, float *out) {
+    if (!ctx) return CGDIR_EINVAL;
+    if (!u || !du || !out || out == u || out == du || !dims_ok(nx, ny, nz) || !sigma_ok(sigma) ||
+        (mode != CGDIR_COMPOSE && mode != CGDIR_ADDITIVE))
+        return fail(ctx, CGDIR_EINVAL, "smooth_compose: bad arguments");
+    DeviceGuard g(ctx->device);
+    if (gauss_radius(sigma) == 0) {
+        CK(launch_compose(u, du, mode, nx, ny, nz, out, nullptr, ctx->stream));
+        return CGDIR_OK;
+    }
+    void *tmp = nullptr;
+    TRY(ws_get(ctx, "field_tmp", 3 * (size_t)nx * ny * nz * sizeof(float), &tmp));
+    CK(launch_smooth_compose(du, u, mode, sigma, nx, ny, nz, out, (float *)tmp, nullptr, ctx->stream, kerr(ctx),
+                             ctx->fused_force, prim_smooth(ctx)));
+    return CGDIR_OK;
+}
+
 int cgdir_iterate(cgdir_ctx *ctx, const float *I0, const float *T0, const uint8_t *mbits,
                   const uint8_t *sbits, const uint8_t *uroi, int k, const float *lambda,
                   const int8_t *sign, float offset, int contour, float sigma_fluid, float sigma_diff,

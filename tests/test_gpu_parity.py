@@ -199,6 +199,49 @@ def test_compose(ctx, mode, sigma):
     close_elementwise(got, ref)
 
 
+def variant_ctx(variant):
+    import os
+    old = os.environ.get("CGDIR_SMOOTH")
+    os.environ["CGDIR_SMOOTH"] = variant
+    try:
+        return cg.Context(0)
+    finally:
+        if old is None:
+            del os.environ["CGDIR_SMOOTH"]
+        else:
+            os.environ["CGDIR_SMOOTH"] = old
+
+
+def smooth_wave(shape, amp):
+    """A smooth displacement-like field of amplitude amp plus a little noise."""
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij")
+    f = np.stack([np.sin(0.31 * x + 0.17 * y + 0.5), np.cos(0.23 * y - 0.29 * z), np.sin(0.19 * z + 0.13 * x)])
+    return (amp * f + RNG.uniform(-0.3, 0.3, size=f.shape)).astype(np.float32)
+
+
+@pytest.mark.parametrize("mode", [cg.CGDIR_COMPOSE, cg.CGDIR_ADDITIVE])
+@pytest.mark.parametrize("shape", [(9, 21, 45), (16, 24, 40), (13, 30, 36), (8, 8, 8)])
+def test_smooth_compose_all_variants(shape, mode):
+    """Algorithm A steps 2-3 (G(du) then the update) with every smoothing
+    variant: against the oracle, and the fused 3-D tile kernel equal to the
+    tile kernel + update kernel bit for bit.  |G(du)| reaches 3.5 voxels,
+    so the update's corners fall both inside the fused kernel's
+    shared-memory copy of u (2-voxel halo) and outside it (global loads);
+    nx % 4 != 0 takes the fused kernel's plain-load path."""
+    u, du = rand_field(shape, 4.0), smooth_wave(shape, 3.5)
+    ref = oracle.compose(u, oracle.gauss_field(du, 1.0), mode)
+    outs = {}
+    for variant in ("tile", "march", "split", "fused"):
+        c = variant_ctx(variant)
+        try:
+            outs[variant] = host(c.smooth_compose(dev(du), dev(u), mode, 1.0))
+        finally:
+            c.close()
+        close_elementwise(outs[variant], ref)
+    assert np.array_equal(outs["fused"], outs["tile"])
+    assert np.array_equal(outs["split"], outs["tile"])
+
+
 def case_inputs(shape=(12, 36, 40), masks=None, name="phantom64"):
     c = phantom.make_case(name, shape=shape, masks=masks)
     return c
