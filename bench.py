@@ -218,17 +218,23 @@ def force_traffic_record(case):
     summary (profiles/force_headneck256.md), if it was taken on the current
     kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "force_headneck256.md")
-    src = os.path.join(ROOT, "paper_1301_0970_gb300", "csrc", "kernels_force.cu")
     if not os.path.exists(path):
         return None
     sha, traffic = None, None
     for line in open(path):
-        if line.startswith("- kernels_force.cu sha1:"):
+        if line.startswith("- force kernel sources sha1"):
             sha = line.split(":", 1)[1].strip()
         if line.startswith("- dram bytes per launch (full size):"):
             traffic = float(line.split(":", 1)[1].strip())
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    return traffic if (sha == h and traffic) else None
+    return traffic if (sha == force_sources_sha1() and traffic) else None
+
+
+def force_sources_sha1():
+    """sha1 of the force kernels' sources (kernels_force.cu, then warp_corners.cuh)."""
+    h = hashlib.sha1()
+    for f in ("kernels_force.cu", "warp_corners.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1301_0970_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 # --------------------------------------------------------------------------- #
