@@ -93,12 +93,23 @@ __device__ void block_partial(float ssd_f, int cnt_i, float mx, double *partial,
     }
 }
 
-// Stopping test of Sec. 2.2 on delta^0..delta^n (same readings as the C ABI).
-__device__ int stop_test(const double *d, int n, int mode, double eps) {
-    if (mode == CGDIR_STOP_WINDOW10) return (n >= 10) && (d[n - 10] - d[n] <= eps);
+// Stopping test of Sec. 2.2 on delta^n = dn and the earlier deltas it needs
+// (same readings as the C ABI): WINDOW10 compares delta^(n-10), PAPER_LITERAL
+// the steps delta^(n-1) -> delta^n and delta^(n-11) -> delta^(n-10).
+struct PastDeltas {
+    double d1, d10, d11;                 // delta^(n-1), delta^(n-10), delta^(n-11) (where n allows)
+};
+__device__ __forceinline__ PastDeltas past_deltas(const double *d, int n, int mode) {
+    PastDeltas p{0.0, 0.0, 0.0};
+    if (mode == CGDIR_STOP_WINDOW10 && n >= 10) p.d10 = d[n - 10];
+    if (mode == CGDIR_STOP_PAPER_LITERAL && n >= 11) { p.d1 = d[n - 1]; p.d10 = d[n - 10]; p.d11 = d[n - 11]; }
+    return p;
+}
+__device__ int stop_test(double dn, const PastDeltas &p, int n, int mode, double eps) {
+    if (mode == CGDIR_STOP_WINDOW10) return (n >= 10) && (p.d10 - dn <= eps);
     if (mode == CGDIR_STOP_PAPER_LITERAL) {
         if (n < 11) return 0;
-        const double ln = d[n] - d[n - 1], lm = d[n - 10] - d[n - 11];
+        const double ln = dn - p.d1, lm = p.d10 - p.d11;
         return (lm - ln) <= eps;
     }
     return 0;
@@ -113,6 +124,9 @@ __device__ void finalize_block(const double *__restrict__ partial, int nblocks, 
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nt = blockDim.x * blockDim.y;
     double s = 0.0, c = 0.0, m = 0.0;
+    // the earlier deltas of the stop test, read now so their latency overlaps the sums
+    PastDeltas past{0.0, 0.0, 0.0};
+    if (tid == 0 && f.st.hist) past = past_deltas(f.st.hist, f.n, f.stop_mode);
     // four partials in flight per thread, summed in the same (ascending) order
     constexpr int U = 4;
     int b = tid;
@@ -148,7 +162,7 @@ __device__ void finalize_block(const double *__restrict__ partial, int nblocks, 
             const double d = C > 0 ? sqrt(S / C) : 0.0;
             if (f.n < st.hist_cap) st.hist[f.n] = d;
             *st.hist_len = f.n + 1;
-            if (stop_test(st.hist, f.n, f.stop_mode, f.eps)) {
+            if (stop_test(d, past, f.n, f.stop_mode, f.eps)) {
                 *st.stop_flag = 1; *st.iters_run = f.n; *st.stop_reason = CGDIR_REASON_CONVERGED;
             } else if (f.n >= f.cap) {
                 *st.stop_flag = 1; *st.iters_run = f.n; *st.stop_reason = CGDIR_REASON_CAP;
