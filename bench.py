@@ -69,6 +69,11 @@ def parse():
                     help="image storage type of the registration (arithmetic stays FP32)")
     ap.add_argument("--rates", default="1,2,4,8,16,32,64", help="serve: arrival rates (requests/s)")
     ap.add_argument("--inflight", type=int, default=64, help="serve: requests in flight at most")
+    ap.add_argument("--tuning-out", default=None,
+                    help="single: write the autotuned per-level schedule to this JSON file")
+    ap.add_argument("--tuning-in", default=None,
+                    help="single: load the per-level schedule from this JSON file instead of tuning "
+                         "(e.g. under a profiler, whose per-launch overhead would skew the tuner)")
     return ap.parse_args()
 
 
@@ -307,7 +312,15 @@ def run_cgdir(args):
 
     ctx = cg.Context(local)
     stream = torch.cuda.current_stream(dev)
-    tuning = ctx.autotune(case.shape, case.k, L, storage_dtype=img_code)   # per-level kernel schedule
+    if args.tuning_in:                                    # per-level kernel schedule
+        with open(args.tuning_in) as f:
+            ctx.load_tuning(json.load(f))
+        tuning = ctx.tuning()
+    else:
+        tuning = ctx.autotune(case.shape, case.k, L, storage_dtype=img_code)
+    if args.tuning_out:
+        with open(args.tuning_out, "w") as f:
+            json.dump(tuning, f)
     for _ in range(args.warmup):
         ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
     torch.cuda.synchronize()

@@ -465,6 +465,13 @@ int cgdir_autotune(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int levels, un
 int cgdir_set_autotune(cgdir_ctx *ctx, int on);
 /* Copy up to cap tuned shapes into out; returns how many there are. */
 int cgdir_tuning_read(const cgdir_ctx *ctx, cgdir_tuning *out, int cap);
+/* Install n tuned shapes (as cgdir_tuning_read returns them, e.g. saved by
+   an earlier process), replacing the context's entries for those shapes;
+   later registrations use them without timing anything.  Only the kernel
+   choices are used (results do not depend on them); the times are kept for
+   reporting.  Errors: EINVAL (bad shape, variant or z chunk; nothing is
+   installed then). */
+int cgdir_tuning_load(cgdir_ctx *ctx, const cgdir_tuning *in, int n);
 
 #ifdef __cplusplus
 }

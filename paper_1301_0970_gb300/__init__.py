@@ -94,6 +94,7 @@ _SIGNATURES = {
     "cgdir_autotune": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_uint, c_int, c_float]),
     "cgdir_set_autotune": (c_int, [c_void_p, c_int]),
     "cgdir_tuning_read": (c_int, [c_void_p, POINTER(cgdir_tuning), c_int]),
+    "cgdir_tuning_load": (c_int, [c_void_p, POINTER(cgdir_tuning), c_int]),
     "cgdir_register_batch": (c_int, [c_void_p, c_int, POINTER(cgdir_volume), POINTER(cgdir_volume),
                                      POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
                                      POINTER(c_void_p), c_int, POINTER(cgdir_level_stats)]),
@@ -378,6 +379,21 @@ class Context:
                  "force_zchunk": b.force_zchunk, "smooth_ms": b.smooth_ms, "force_ms": b.force_ms,
                  "default_smooth_ms": b.default_smooth_ms, "default_force_ms": b.default_force_ms}
                 for b in buf[:n]]
+
+    def load_tuning(self, table):
+        """Install a tuning table as tuning() returns it (e.g. saved as JSON by
+        an earlier process); registrations of those shapes then use it."""
+        codes = {"march": CGDIR_SMOOTH_MARCH, "tile": CGDIR_SMOOTH_TILE, "split": CGDIR_SMOOTH_SPLIT,
+                 "fused": CGDIR_SMOOTH_FUSED}
+        buf = (cgdir_tuning * max(len(table), 1))()
+        for b, t in zip(buf, table):
+            b.nz, b.ny, b.nx = t["shape"]
+            b.contour, b.storage_dtype = int(bool(t["contour"])), int(t["storage_dtype"])
+            b.smooth_variant, b.smooth_zchunk = codes[t["smooth"]], int(t["smooth_zchunk"])
+            b.force_zchunk = int(t["force_zchunk"])
+            b.smooth_ms, b.force_ms = t["smooth_ms"], t["force_ms"]
+            b.default_smooth_ms, b.default_force_ms = t["default_smooth_ms"], t["default_force_ms"]
+        self._check(load().cgdir_tuning_load(self._h, buf, len(table)), "cgdir_tuning_load")
 
     # ---- whole registration ------------------------------------------------
     def register(self, static, moving, static_masks=None, moving_masks=None, **kw):

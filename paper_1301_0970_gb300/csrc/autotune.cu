@@ -300,4 +300,29 @@ int cgdir_tuning_read(const cgdir_ctx *ctx, cgdir_tuning *out, int cap) {
     return n;
 }
 
+int cgdir_tuning_load(cgdir_ctx *ctx, const cgdir_tuning *in, int n) {
+    if (!ctx || n < 0 || (n > 0 && !in)) return CGDIR_EINVAL;
+    ctx->err.clear();
+    for (int i = 0; i < n; ++i) {
+        const cgdir_tuning &t = in[i];
+        if (!dims_ok(t.nx, t.ny, t.nz) || (t.contour != 0 && t.contour != 1) || t.storage_dtype < CGDIR_F32 ||
+            t.storage_dtype > CGDIR_BF16 || t.smooth_variant < CGDIR_SMOOTH_MARCH ||
+            t.smooth_variant > CGDIR_SMOOTH_FUSED || t.smooth_zchunk < 0 || t.smooth_zchunk > t.nz ||
+            t.force_zchunk < 1 || t.force_zchunk > t.nz)
+            return fail(ctx, CGDIR_EINVAL, "tuning_load: bad entry");
+    }
+    for (int i = 0; i < n; ++i) {
+        const cgdir_tuning &t = in[i];
+        TunedLevel v;
+        v.smooth_variant = t.smooth_variant;
+        v.smooth_zchunk = t.smooth_zchunk;
+        v.force_zchunk = t.force_zchunk;
+        v.smooth_ms = t.smooth_ms; v.force_ms = t.force_ms;
+        v.default_smooth_ms = t.default_smooth_ms; v.default_force_ms = t.default_force_ms;
+        ctx->tuned[TuneKey{t.nx, t.ny, t.nz, t.contour, t.storage_dtype}] = v;
+    }
+    ++ctx->tune_gen;
+    return CGDIR_OK;
+}
+
 }  // extern "C"

@@ -194,6 +194,31 @@ def test_autotune_records_every_level_and_keeps_results():
         assert [s["iters_run"] for s in st] == [s["iters_run"] for s in rst]
 
 
+def test_tuning_table_round_trip():
+    """A tuning table read from one context (and through JSON) installs in
+    another: the same choices, the same DVF bit for bit, no timing run; bad
+    entries are refused and install nothing."""
+    import json
+    c = phantom.make_case("phantom64", shape=(16, 40, 44))
+    kw = dict(levels=2, iters=[5, 4], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as a:
+        tab = a.autotune(c.shape, c.k, 2)
+        ra, _ = single(a, c, kw)
+    tab2 = json.loads(json.dumps(tab))
+    with cg.Context(0) as b:
+        b.load_tuning(tab2)
+        got = b.tuning()
+        key = lambda t: (tuple(t["shape"]), t["contour"], t["storage_dtype"])
+        assert sorted((key(t), t["smooth"], t["smooth_zchunk"], t["force_zchunk"]) for t in got) == \
+            sorted((key(t), t["smooth"], t["smooth_zchunk"], t["force_zchunk"]) for t in tab)
+        rb, _ = single(b, c, kw)
+        assert torch.equal(ra, rb)
+        bad = dict(tab2[0], force_zchunk=0)
+        with pytest.raises(cg.CgdirError):
+            b.load_tuning([bad])
+        assert len(b.tuning()) == len(tab)
+
+
 def test_autotune_on_first_use():
     c = phantom.make_case("phantom64", shape=(16, 40, 44))
     kw = dict(levels=2, iters=[5, 4], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
