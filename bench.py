@@ -40,6 +40,7 @@ WORKLOADS = {"headneck256": dict(WORKLOAD), "pelvis512": {"name": "pelvis512", "
 ORACLE_SAMPLE_ITERS = [8, 4, 2]
 FORCE_BYTES_PER_VOXEL = {True: 35, False: 33}   # contour terms on / off, FP32 images
 FORCE_BYTES_PER_VOXEL_16 = {True: 31, False: 29}   # the same with 16-bit images
+SMOOTH_BYTES_PER_VOXEL = 24                       # Gaussian of a 3-component field: read 12, write 12
 
 
 def parse():
@@ -218,6 +219,11 @@ def measured_peaks():
     return 6800.0, "fallback 6.8 TB/s"
 
 
+def sigma_default(kw):
+    """True when the registration smooths with sigma = 1 voxel (the profiled radius)."""
+    return kw.get("sigma_fluid", 1.0) == 1.0 and kw.get("sigma_diff", 1.0) == 1.0
+
+
 def force_traffic_record(case):
     """DRAM bytes per launch of the force kernel from the committed ncu
     summary (profiles/force_headneck256.md), if it was taken on the current
@@ -234,12 +240,32 @@ def force_traffic_record(case):
     return traffic if (sha == force_sources_sha1() and traffic) else None
 
 
-def force_sources_sha1():
-    """sha1 of the force kernels' sources (kernels_force.cu, then warp_corners.cuh)."""
+def smooth_traffic_record():
+    """DRAM bytes per launch of the z-march smoothing kernel from the committed
+    ncu summary (profiles/smooth_headneck256.md), if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "smooth_headneck256.md")
+    if not os.path.exists(path):
+        return None
+    sha, traffic = None, None
+    for line in open(path):
+        if line.startswith("- smoothing kernel sources sha1"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("- dram bytes per launch (full size):"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if (sha == sources_sha1(("kernels_smooth.cu", "tma.cuh")) and traffic) else None
+
+
+def sources_sha1(files):
     h = hashlib.sha1()
-    for f in ("kernels_force.cu", "warp_corners.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1301_0970_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
+
+
+def force_sources_sha1():
+    """sha1 of the force kernels' sources (kernels_force.cu, then warp_corners.cuh)."""
+    return sources_sha1(("kernels_force.cu", "warp_corners.cuh"))
 
 
 # --------------------------------------------------------------------------- #
@@ -326,7 +352,8 @@ def run_cgdir(args):
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs, CUDA events on the ctx stream
-    ctx.profile([cg.CGDIR_K_FORCE], levels=[L - 1])       # the roofline's launches only
+    # the roofline's launches only: the force step and the smoothing of u at the finest level
+    ctx.profile([cg.CGDIR_K_FORCE, cg.CGDIR_K_SMOOTH_U], levels=[L - 1])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     barrier()
@@ -379,20 +406,40 @@ def run_cgdir(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": 1e3 * t_max / args.steps}
 
-    # ---- roofline of the dominant kernel: force at the finest level
-    fine = [p for p in prof if p["kernel"] == "force" and p["level"] == L - 1]
-    roofline = None
-    if fine and fine[0]["launches"]:
-        avg_ms = fine[0]["total_ms"] / fine[0]["launches"]
-        bytes_per_launch = (FORCE_BYTES_PER_VOXEL if args.storage == "f32" else FORCE_BYTES_PER_VOXEL_16)[True] * N
-        peak, peak_src = measured_peaks()
+    # ---- roofline of the dominant kernel (largest share of device time in the
+    # launch list): the z-march Gaussian at the finest level, two launches per
+    # iteration (du and u; the u launch is the one timed here); the force step
+    # (its two passes) as a second entry
+    peak, peak_src = measured_peaks()
+    fine = {p["kernel"]: p for p in prof if p["level"] == L - 1 and p["launches"]}
+    fine_variant = next((t["smooth"] for t in tuning if tuple(t["shape"]) == tuple(case.shape)), None)
+    roofline, roofline_force = None, None
+    if "smooth_u" in fine and fine_variant == "march":
+        p = fine["smooth_u"]
+        avg_ms = p["total_ms"] / p["launches"]
+        bytes_per_launch = SMOOTH_BYTES_PER_VOXEL * N
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "force step = k_warp_pass + k_force_pass (finest level, contour terms on)",
+        roofline = {"bound": "hbm", "kernel": "k_smooth_tma (z-march Gaussian of u, finest level; the same kernel "
+                                              "also smooths du there)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": force_traffic_record(case) if (args.workload, args.storage) == ("headneck256", "f32")
+                    "traffic": smooth_traffic_record() if (args.workload, sigma_default(kw)) == ("headneck256", True)
                     else None,
                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-                    "launches": fine[0]["launches"], "peak_source": peak_src}
+                    "launches": p["launches"], "peak_source": peak_src}
+    if "force" in fine:
+        p = fine["force"]
+        avg_ms = p["total_ms"] / p["launches"]
+        bytes_per_launch = (FORCE_BYTES_PER_VOXEL if args.storage == "f32" else FORCE_BYTES_PER_VOXEL_16)[True] * N
+        achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        roofline_force = {"bound": "hbm", "kernel": "force step = k_warp_pass + k_force_pass2 (finest level, "
+                                                    "contour terms on)",
+                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                          "traffic": force_traffic_record(case) if (args.workload, args.storage) == ("headneck256", "f32")
+                          else None,
+                          "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                          "launches": p["launches"], "peak_source": peak_src}
+    if roofline is None:
+        roofline = roofline_force
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -410,6 +457,7 @@ def run_cgdir(args):
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "per": "registration"},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+                "roofline_force_step": roofline_force,
                 "cpu_baseline": cpu, "clocks": clk.summary(),
                 "kernel_breakdown_ms": {f"{p['kernel']}@L{p['level']}": round(p["total_ms"], 4)
                                         for p in breakdown},
