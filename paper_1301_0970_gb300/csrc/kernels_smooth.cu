@@ -216,6 +216,22 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
         t_g4[q] = 4 * g;
         t_dst[q] = row * TX + 4 * g;
     }
+    // halo columns outside the volume in x (border CTAs): the copies each
+    // plane needs, the first two per thread precomputed
+    const int fix_left = max(0, ML - x0), fix_right = max(0, x0 - ML + BXW - nx);
+    const int fix_cols = min(BXW, fix_left + fix_right), fix_n = xin ? 0 : NC * BY * fix_cols;
+    int fix_dst[2] = {-1, -1}, fix_src[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int f = tid + h * NT;
+        if (f < fix_n) {
+            const int row = f / fix_cols, k = f - row * fix_cols;
+            const int lx = k < fix_left ? k : BXW - fix_cols + k;
+            fix_dst[h] = row * BXW + lx;
+            fix_src[h] = row * BXW + clampi(x0 - ML + lx, 0, nx - 1) - (x0 - ML);
+        }
+    }
+    const int fix_more = 2 * NT + tid;
     float *outp[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) outp[c] = out + (size_t)(comp + c) * N + (size_t)ya * nx + x;
@@ -246,37 +262,37 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
             if (t >= P) break;
             tw = t;
             const bool ok = mbar_wait_bounded(&bar[sidx], par);
-            const float *S = stage + sidx * STAGE;
+            float *S = stage + sidx * STAGE;
             float *X = Xb + (t & 1) * G::XB;
+            if (!xin) {
+                // the box crosses an x border of the volume: copy the border
+                // column into the halo columns outside it (the clamped values
+                // the x pass must see; the copy holds zeros there)
+                if (fix_dst[0] >= 0) S[fix_dst[0]] = S[fix_src[0]];
+                if (fix_dst[1] >= 0) S[fix_dst[1]] = S[fix_src[1]];
+                for (int f = fix_more; f < fix_n; f += NT) {       // only for volumes narrower than a CTA
+                    const int row = f / fix_cols, k = f - row * fix_cols;
+                    const int lx = k < fix_left ? k : BXW - fix_cols + k;
+                    S[row * BXW + lx] = S[row * BXW + clampi(x0 - ML + lx, 0, nx - 1) - (x0 - ML)];
+                }
+                __syncthreads();
+            }
             // x pass: 4 adjacent outputs per task, paired FMAs
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
                 if (t_row[q] < 0) continue;
                 const float *src = S + t_row[q];
                 float2 o01 = make_float2(0.f, 0.f), o23 = make_float2(0.f, 0.f);
-                if (xin) {
-                    float v[4 * NV];
+                float v[4 * NV];
 #pragma unroll
-                    for (int h = 0; h < NV; ++h) {
-                        const float4 f = reinterpret_cast<const float4 *>(src + t_g4[q])[h];
-                        v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
-                    }
+                for (int h = 0; h < NV; ++h) {
+                    const float4 f = reinterpret_cast<const float4 *>(src + t_g4[q])[h];
+                    v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
+                }
 #pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        o01 = __ffma2_rn(w2[j], make_float2(v[j + ML - R], v[j + 1 + ML - R]), o01);
-                        o23 = __ffma2_rn(w2[j], make_float2(v[j + 2 + ML - R], v[j + 3 + ML - R]), o23);
-                    }
-                } else {
-                    const int gx = x0 + t_g4[q] - R;
-#pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        const float a0 = src[clampi(gx + j, 0, nx - 1) - x0 + ML];
-                        const float a1 = src[clampi(gx + j + 1, 0, nx - 1) - x0 + ML];
-                        const float a2 = src[clampi(gx + j + 2, 0, nx - 1) - x0 + ML];
-                        const float a3 = src[clampi(gx + j + 3, 0, nx - 1) - x0 + ML];
-                        o01 = __ffma2_rn(w2[j], make_float2(a0, a1), o01);
-                        o23 = __ffma2_rn(w2[j], make_float2(a2, a3), o23);
-                    }
+                for (int j = 0; j < K; ++j) {
+                    o01 = __ffma2_rn(w2[j], make_float2(v[j + ML - R], v[j + 1 + ML - R]), o01);
+                    o23 = __ffma2_rn(w2[j], make_float2(v[j + 2 + ML - R], v[j + 3 + ML - R]), o23);
                 }
                 reinterpret_cast<float4 *>(X + t_dst[q])[0] = make_float4(o01.x, o01.y, o23.x, o23.y);
             }
