@@ -216,22 +216,7 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
         t_g4[q] = 4 * g;
         t_dst[q] = row * TX + 4 * g;
     }
-    // halo columns outside the volume in x (border CTAs): the copies each
-    // plane needs, the first two per thread precomputed
-    const int fix_left = max(0, ML - x0), fix_right = max(0, x0 - ML + BXW - nx);
-    const int fix_cols = min(BXW, fix_left + fix_right), fix_n = xin ? 0 : NC * BY * fix_cols;
-    int fix_dst[2] = {-1, -1}, fix_src[2] = {0, 0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int f = tid + h * NT;
-        if (f < fix_n) {
-            const int row = f / fix_cols, k = f - row * fix_cols;
-            const int lx = k < fix_left ? k : BXW - fix_cols + k;
-            fix_dst[h] = row * BXW + lx;
-            fix_src[h] = row * BXW + clampi(x0 - ML + lx, 0, nx - 1) - (x0 - ML);
-        }
-    }
-    const int fix_more = 2 * NT + tid;
+    const int xlim = nx - x0 + ML;        // first local column beyond the volume's last x
     float *outp[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) outp[c] = out + (size_t)(comp + c) * N + (size_t)ya * nx + x;
@@ -262,21 +247,8 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
             if (t >= P) break;
             tw = t;
             const bool ok = mbar_wait_bounded(&bar[sidx], par);
-            float *S = stage + sidx * STAGE;
+            const float *S = stage + sidx * STAGE;
             float *X = Xb + (t & 1) * G::XB;
-            if (!xin) {
-                // the box crosses an x border of the volume: copy the border
-                // column into the halo columns outside it (the clamped values
-                // the x pass must see; the copy holds zeros there)
-                if (fix_dst[0] >= 0) S[fix_dst[0]] = S[fix_src[0]];
-                if (fix_dst[1] >= 0) S[fix_dst[1]] = S[fix_src[1]];
-                for (int f = fix_more; f < fix_n; f += NT) {       // only for volumes narrower than a CTA
-                    const int row = f / fix_cols, k = f - row * fix_cols;
-                    const int lx = k < fix_left ? k : BXW - fix_cols + k;
-                    S[row * BXW + lx] = S[row * BXW + clampi(x0 - ML + lx, 0, nx - 1) - (x0 - ML)];
-                }
-                __syncthreads();
-            }
             // x pass: 4 adjacent outputs per task, paired FMAs
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
@@ -288,6 +260,21 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
                 for (int h = 0; h < NV; ++h) {
                     const float4 f = reinterpret_cast<const float4 *>(src + t_g4[q])[h];
                     v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
+                }
+                if (!xin) {
+                    // the box crosses an x border of the volume (its copy holds
+                    // zeros there): the taps outside take the border value
+#pragma unroll
+                    for (int g = 0; g < ML; g += 4)            // left: x0 = 0, the first ML / 4 tasks of a row
+                        if (x0 == 0 && t_g4[q] == g) {
+#pragma unroll
+                            for (int k = 0; k < ML - g; ++k) v[k] = v[ML - g];
+                        }
+                    if (t_g4[q] + 4 * NV > xlim) {             // right: columns from xlim on lie beyond nx - 1
+                        const float b = src[xlim - 1];
+#pragma unroll
+                        for (int k = 0; k < 4 * NV; ++k) v[k] = t_g4[q] + k >= xlim ? b : v[k];
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
