@@ -434,15 +434,19 @@ int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap);
  * update (steps 2-4 of an iteration: TMA z-march with three z-chunk
  * lengths, 3-D shared-memory tile, split xy + z kernels with the update in
  * the z pass) and of the force stencil pass (three z-chunk lengths) on
- * ctx's stream, and keeps the fastest.  Later registrations of those shapes use the choices (results
- * are the same to rounding: only the launch geometry changes, except that
- * the two smoothing kernels may differ in the last bit).  Blocking. */
+ * ctx's stream and keeps the fastest, then times the fused schedule against
+ * it.  Later registrations of those shapes use the choices: cgdir_register
+ * the fused schedule where it won, batched and served registrations (which
+ * share the GPU, so throughput counts) the best per-step schedule.  Only
+ * the kernels change: every choice gives the same bits.  Blocking. */
 #define CGDIR_SMOOTH_MARCH 1
 #define CGDIR_SMOOTH_TILE  2
 #define CGDIR_SMOOTH_SPLIT 3
 #define CGDIR_SMOOTH_FUSED 4   /* fused schedule: 3-D tiles of G(du) with the update and of G(u')
                                   with the next warp; the force runs its stencil pass only.
-                                  smooth_ms / force_ms are then those kernels' times */
+                                  smooth_ms / force_ms are then those kernels' times (the
+                                  per-step alternative is kept but not reported; a loaded
+                                  table that says FUSED picks the per-step kernels by size) */
 typedef struct {
     int   nx, ny, nz;           /* level shape                                   */
     int   contour;              /* structure terms on at this level               */

@@ -66,7 +66,7 @@ static const TunedLevel *find_tuned(const cgdir_ctx *ctx, int nx, int ny, int nz
     return it == ctx->tuned.end() ? nullptr : &it->second;
 }
 
-SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
+SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt, bool allow_fused) {
     SmoothChoice ch;
     if (ctx->smooth_variant != SMOOTH_AUTO || ctx->smooth_zchunk > 0) {
         ch.variant = ctx->smooth_variant;
@@ -74,8 +74,8 @@ SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int con
         return ch;
     }
     if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt)) {
-        ch.variant = t->smooth_variant;
-        ch.zchunk = t->smooth_zchunk;
+        ch.variant = t->fused && allow_fused ? SMOOTH_FUSED : t->smooth_variant;
+        ch.zchunk = t->fused && allow_fused ? 0 : t->smooth_zchunk;
     }
     return ch;
 }
@@ -226,10 +226,9 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
                 return launch_fused_smooth_warp(out, sigma, u, a2, kerr(ctx), st);
             });
         if (rc == CGDIR_OK && f2 + fs < best.force_ms + best.smooth_ms) {
-            best.smooth_variant = SMOOTH_FUSED;
-            best.smooth_zchunk = 0;
-            best.smooth_ms = fs;
-            best.force_ms = f2;
+            best.fused = 1;
+            best.fused_smooth_ms = fs;
+            best.fused_force_ms = f2;
         }
     }
     cudaEventDestroy(e0);
@@ -290,9 +289,12 @@ int cgdir_tuning_read(const cgdir_ctx *ctx, cgdir_tuning *out, int cap) {
             cgdir_tuning &o = out[n];
             o.nx = kv.first[0]; o.ny = kv.first[1]; o.nz = kv.first[2];
             o.contour = kv.first[3]; o.storage_dtype = kv.first[4];
-            o.smooth_variant = kv.second.smooth_variant; o.smooth_zchunk = kv.second.smooth_zchunk;
-            o.force_zchunk = kv.second.force_zchunk;
-            o.smooth_ms = kv.second.smooth_ms; o.force_ms = kv.second.force_ms;
+            const TunedLevel &t = kv.second;
+            o.smooth_variant = t.fused ? CGDIR_SMOOTH_FUSED : t.smooth_variant;
+            o.smooth_zchunk = t.fused ? 0 : t.smooth_zchunk;
+            o.force_zchunk = t.force_zchunk;
+            o.smooth_ms = t.fused ? t.fused_smooth_ms : t.smooth_ms;
+            o.force_ms = t.fused ? t.fused_force_ms : t.force_ms;
             o.default_smooth_ms = kv.second.default_smooth_ms; o.default_force_ms = kv.second.default_force_ms;
         }
         ++n;
@@ -314,10 +316,15 @@ int cgdir_tuning_load(cgdir_ctx *ctx, const cgdir_tuning *in, int n) {
     for (int i = 0; i < n; ++i) {
         const cgdir_tuning &t = in[i];
         TunedLevel v;
-        v.smooth_variant = t.smooth_variant;
-        v.smooth_zchunk = t.smooth_zchunk;
+        if (t.smooth_variant == CGDIR_SMOOTH_FUSED) {     // the per-step alternative was not saved: by size
+            v.fused = 1;
+            v.fused_smooth_ms = t.smooth_ms; v.fused_force_ms = t.force_ms;
+        } else {
+            v.smooth_variant = t.smooth_variant;
+            v.smooth_zchunk = t.smooth_zchunk;
+            v.smooth_ms = t.smooth_ms; v.force_ms = t.force_ms;
+        }
         v.force_zchunk = t.force_zchunk;
-        v.smooth_ms = t.smooth_ms; v.force_ms = t.force_ms;
         v.default_smooth_ms = t.default_smooth_ms; v.default_force_ms = t.default_force_ms;
         ctx->tuned[TuneKey{t.nx, t.ny, t.nz, t.contour, t.storage_dtype}] = v;
     }

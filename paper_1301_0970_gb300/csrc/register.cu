@@ -59,6 +59,7 @@ struct RegPlan {
     uint8_t *rowdist = nullptr;
     void *stage = nullptr;
     void *fscr = nullptr;              // two-pass force scratch (null: one-pass kernels)
+    bool shared_gpu = false;           // batched or served: the per-step schedule (throughput)
     unsigned long long generation = 0;
     // the slot buffers this plan needs: name and bytes (see plan_prepare)
     enum { B_IMG, B_BITS, B_TEX, B_FIELDS, B_PARTIAL, B_STATE, B_ROWDIST, B_STAGE, B_FSCR, B_COUNT };
@@ -338,7 +339,7 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
         a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
         if (pl.fscr) force_scratch_assign(a, pl.fscr, pl.Nl[l]);
         const int zc = force_zchunk_for(ctx, lx, ly, lz, a.contour, sdt);
-        const SmoothChoice sch = smooth_choice(ctx, lx, ly, lz, a.contour, sdt);
+        const SmoothChoice sch = smooth_choice(ctx, lx, ly, lz, a.contour, sdt, !pl.shared_gpu);
         const int cap = P->iters[l];
         a.fin.done = done + l;
         a.fin.st = st;
@@ -412,6 +413,7 @@ std::string plan_key(cgdir_ctx *ctx, const RegPlan &pl) {
         P->margin_mm, P->intensity_offset, (int)ctx->plain_kernels + 2 * (int)ctx->fused_force + 4 * ctx->smooth_variant + 16 * (int)ctx->tune_gen,
         pl.maxcap, pl.generation, ctx->prof_mask, pl.sdt);
     std::string s(key, (size_t)len);
+    s += pl.shared_gpu ? "shared|" : "alone|";
     for (int l = 0; l < pl.L; ++l) s += std::to_string(P->iters[l]) + ",";
     for (int j = 0; j < pl.k; ++j) {
         char b[48];
@@ -576,7 +578,10 @@ int cgdir_register_batch(cgdir_ctx *ctx, int count, const cgdir_volume *statics,
     }
     DeviceGuard g(ctx->device);
     cudaStream_t s = ctx->stream;
-    for (int i = 0; i < count; ++i) TRY(plan_autotune(ctx, pls[i]));
+    for (int i = 0; i < count; ++i) {
+        pls[i].shared_gpu = true;     // the branches share the GPU: throughput over latency
+        TRY(plan_autotune(ctx, pls[i]));
+    }
     for (int i = 0; i < count; ++i) {
         Slot &sl = slot_at(ctx, (size_t)i);
         if (sl.busy) return fail(ctx, CGDIR_EBUSY, "register_batch: a slot is serving a request");
@@ -653,6 +658,7 @@ int cgdir_submit(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, c
     if (!dvf_out || !ticket) return fail(ctx, CGDIR_EINVAL, "submit: null argument");
     std::unique_ptr<RegPlan, RegPlanDeleter> pl(new RegPlan());
     TRY(plan_make(ctx, S, M, SM, MM, P, dvf_where, *pl));
+    pl->shared_gpu = true;            // served requests share the GPU: throughput over latency
     DeviceGuard g(ctx->device);
     TRY(plan_autotune(ctx, *pl));
     // a free slot (slot 0 is left to cgdir_register): first one that already

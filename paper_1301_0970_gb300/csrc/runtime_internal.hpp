@@ -50,11 +50,13 @@ struct WsSet {
 
 // Kernel choices for one pyramid level shape, picked by timing (autotune.cu).
 struct TunedLevel {
-    int smooth_variant = 0;    // SMOOTH_MARCH / SMOOTH_TILE
+    int smooth_variant = 0;    // best per-step smoothing: SMOOTH_MARCH / TILE / SPLIT (0 = by size)
     int smooth_zchunk = 0;     // z chunk of the z-march smoothing (0 = default)
     int force_zchunk = 0;      // z chunk of the force stencil pass (0 = default)
-    float smooth_ms = 0.f, force_ms = 0.f;   // best times measured
+    float smooth_ms = 0.f, force_ms = 0.f;   // best per-step times measured
     float default_smooth_ms = 0.f, default_force_ms = 0.f;
+    int fused = 0;             // the fused schedule beat the best per-step one (alone on the GPU)
+    float fused_smooth_ms = 0.f, fused_force_ms = 0.f;
 };
 using TuneKey = std::array<int, 5>;   // nx, ny, nz, structure terms on, image storage type
 
@@ -177,7 +179,9 @@ unsigned long long launches_now();
 void launches_sub(unsigned long long n);
 
 // Tuned (else default) kernel choices for a level shape.
-SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
+// allow_fused: false for registrations that share the GPU (batches, served
+// requests), which take the best per-step schedule.
+SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt, bool allow_fused);
 int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
 bool use_level_coop(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
 // Smallest force z chunk any tuning may choose (sizes the partial buffers).

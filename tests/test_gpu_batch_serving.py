@@ -219,6 +219,27 @@ def test_tuning_table_round_trip():
         assert len(b.tuning()) == len(tab)
 
 
+def test_shared_gpu_registrations_take_the_per_step_schedule():
+    """Where the fused schedule won the tuning, cgdir_register uses it and a
+    batch (whose branches share the GPU) the per-step kernels: more launches
+    per iteration, the same DVF bit for bit."""
+    c = phantom.make_case("headneck256", shape=(24, 64, 64))
+    kw = dict(levels=1, iters=[12], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED, contour_level_mask=1)
+    with cg.Context(0) as ctx:
+        tab = ctx.autotune(c.shape, c.k, 1, contour_level_mask=1)
+        single(ctx, c, kw)                       # capture the graphs first
+        ctx.register_batch([case_dict(c, kw)])
+        n0 = cg.launch_count()
+        a, _ = single(ctx, c, kw)
+        n1 = cg.launch_count()
+        (b, _), = ctx.register_batch([case_dict(c, kw)])
+        n2 = cg.launch_count()
+    assert torch.equal(a, b)
+    if tab[0]["smooth"] == "fused":
+        # per iteration after the first: 3 kernels fused, at least 5 per step
+        assert (n2 - n1) - (n1 - n0) >= 2 * (12 - 1)
+
+
 def test_autotune_on_first_use():
     c = phantom.make_case("phantom64", shape=(16, 40, 44))
     kw = dict(levels=2, iters=[5, 4], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
