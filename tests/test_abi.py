@@ -80,6 +80,8 @@ def test_null_context_is_rejected_without_touching_the_gpu():
     lib = cg.load()
     assert lib.cgdir_register(None, None, None, None, None, None, None, 0, None) == cg.CGDIR_EINVAL
     assert lib.cgdir_create(None, None) == cg.CGDIR_EINVAL
+    assert lib.cgdir_tuning_load(None, None, 0) == cg.CGDIR_EINVAL
+    assert lib.cgdir_smooth_compose(None, None, None, 0, 1.0, 1, 1, 1, None) == cg.CGDIR_EINVAL
 
 
 def test_sources_target_sm103a_only():
