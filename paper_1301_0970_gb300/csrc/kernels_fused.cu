@@ -5,7 +5,7 @@
 // by launch and memory latency rather than bandwidth.  Two kernels here
 // take four of those steps:
 //
-//   k_fused_smooth_compose  G_fluid(du) (steps 2) and the composite update
+//   k_fused_smooth_compose  G_fluid(du) (step 2) and the composite update
 //                           du + u(x + du) or u + du (step 3) -> u'
 //   k_fused_smooth_warp     G_diff(u') -> u (step 4), then the warp of the
 //                           moving image and the structure terms at the new
@@ -13,12 +13,13 @@
 //
 // so an iteration becomes the force stencil pass plus these two.  A CTA
 // owns an 8 x 8 x 8 output tile of all three components: the tile plus its
-// R-voxel halo (clamped indices, R = ceil(3 sigma)) is loaded into shared
-// memory, filtered along x, then y, then z, and each thread takes the z
-// pass of its output voxels for all three components, so the update (or
-// the warp) follows in registers with no further pass over memory.  Every
-// tap sum runs in the same order as the other smoothing kernels (x, y, z;
-// taps in ascending offset; explicit FMAs), the update has the update
+// R-voxel halo (R = ceil(3 sigma)) is brought into shared memory, filtered
+// along x (a row per task), then y (a column per task), then z (a z column
+// per task), and each thread then takes its output voxels' three smoothed
+// components from shared memory for the update (or the warp), with no
+// further pass over memory.  Every tap sum runs in the same order as the
+// other smoothing kernels (x, y, z; taps in ascending offset; every
+// multiply-add a separately rounded FMA), the update has the update
 // kernel's arithmetic and the warp is the force's own warp function, so
 // the fused schedule gives the same bits as the unfused one.
 #include "cgdir_internal.cuh"
