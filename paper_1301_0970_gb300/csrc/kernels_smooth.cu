@@ -278,8 +278,15 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
                 }
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
-                    o01 = __ffma2_rn(w2[j], make_float2(v[j + ML - R], v[j + 1 + ML - R]), o01);
-                    o23 = __ffma2_rn(w2[j], make_float2(v[j + 2 + ML - R], v[j + 3 + ML - R]), o23);
+                    if ((j + ML - R) % 2 == 0) {       // operand pairs register-aligned: paired FMAs
+                        o01 = __ffma2_rn(w2[j], make_float2(v[j + ML - R], v[j + 1 + ML - R]), o01);
+                        o23 = __ffma2_rn(w2[j], make_float2(v[j + 2 + ML - R], v[j + 3 + ML - R]), o23);
+                    } else {                           // odd offset: scalar FMAs (same rounding, no moves)
+                        o01.x = fmaf(w2[j].x, v[j + ML - R], o01.x);
+                        o01.y = fmaf(w2[j].x, v[j + 1 + ML - R], o01.y);
+                        o23.x = fmaf(w2[j].x, v[j + 2 + ML - R], o23.x);
+                        o23.y = fmaf(w2[j].x, v[j + 3 + ML - R], o23.y);
+                    }
                 }
                 reinterpret_cast<float4 *>(X + t_dst[q])[0] = make_float4(o01.x, o01.y, o23.x, o23.y);
             }
@@ -300,7 +307,14 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
                 for (int j = 0; j <= K; ++j) yin[j] = col[j * TX];
                 float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < K; ++j) a = __ffma2_rn(w2[j], make_float2(yin[j], yin[j + 1]), a);
+                for (int j = 0; j < K; ++j) {
+                    if (j % 2 == 0) {
+                        a = __ffma2_rn(w2[j], make_float2(yin[j], yin[j + 1]), a);
+                    } else {
+                        a.x = fmaf(w2[j].x, yin[j], a.x);
+                        a.y = fmaf(w2[j].x, yin[j + 1], a.y);
+                    }
+                }
                 ring[c][r] = a;
                 float2 o = make_float2(0.f, 0.f);
 #pragma unroll
