@@ -149,8 +149,14 @@ __device__ __forceinline__ bool tile_smooth(const CUtensorMap *tin, bool use_tma
             for (int q = 0; q < FQ; q += 2) {
                 float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < K; ++j)
-                    a = __ffma2_rn(w2[j], make_float2(v[ML - R + q + j], v[ML - R + q + 1 + j]), a);
+                for (int j = 0; j < K; ++j) {
+                    if ((ML - R + j) % 2 == 0) {       // operand pair register-aligned: paired FMA
+                        a = __ffma2_rn(w2[j], make_float2(v[ML - R + q + j], v[ML - R + q + 1 + j]), a);
+                    } else {                           // odd offset: scalar FMAs (same rounding, no moves)
+                        a.x = fmaf(w2[j].x, v[ML - R + q + j], a.x);
+                        a.y = fmaf(w2[j].x, v[ML - R + q + 1 + j], a.y);
+                    }
+                }
                 o[q] = a.x; o[q + 1] = a.y;
             }
         } else {
@@ -183,7 +189,14 @@ __device__ __forceinline__ bool tile_smooth(const CUtensorMap *tin, bool use_tma
         for (int q = 0; q < FQ; q += 2) {
             float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < K; ++j) a = __ffma2_rn(w2[j], make_float2(yin[q + j], yin[q + 1 + j]), a);
+            for (int j = 0; j < K; ++j) {
+                if (j % 2 == 0) {
+                    a = __ffma2_rn(w2[j], make_float2(yin[q + j], yin[q + 1 + j]), a);
+                } else {
+                    a.x = fmaf(w2[j].x, yin[q + j], a.x);
+                    a.y = fmaf(w2[j].x, yin[q + 1 + j], a.y);
+                }
+            }
             dst[q * FQ] = a.x;
             dst[(q + 1) * FQ] = a.y;
         }
@@ -201,7 +214,14 @@ __device__ __forceinline__ bool tile_smooth(const CUtensorMap *tin, bool use_tma
         for (int q = 0; q < FQ; q += 2) {
             float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int j = 0; j < K; ++j) a = __ffma2_rn(w2[j], make_float2(zin[q + j], zin[q + 1 + j]), a);
+            for (int j = 0; j < K; ++j) {
+                if (j % 2 == 0) {
+                    a = __ffma2_rn(w2[j], make_float2(zin[q + j], zin[q + 1 + j]), a);
+                } else {
+                    a.x = fmaf(w2[j].x, zin[q + j], a.x);
+                    a.y = fmaf(w2[j].x, zin[q + 1 + j], a.y);
+                }
+            }
             dst[q * FQ * FQ] = a.x;
             dst[(q + 1) * FQ * FQ] = a.y;
         }
