@@ -428,6 +428,14 @@ int cgdir_profile_levels(cgdir_ctx *ctx, unsigned level_mask);
    number of entries written (negative status on error). */
 int cgdir_profile_read(const cgdir_ctx *ctx, cgdir_kernel_time *out, int cap);
 
+/* Self-test of the device-side timeout path (not in the paper): one kernel
+   waits, with a limit of limit_us microseconds (1..2000000), on a barrier
+   that nothing completes; the wait runs out, the kernel records it in the
+   context's error word and returns, and the call reports it as a kernel
+   wait that ran out.  Returns CGDIR_ETIMEDOUT when the path works (the
+   context stays usable); EINVAL for a bad limit; ECUDA. */
+int cgdir_selftest_wait_timeout(cgdir_ctx *ctx, int limit_us);
+
 /* ---- autotuner (not in the paper: an execution choice) --------------------
  * For each level shape of a pyramid it times, on synthetic data of that
  * shape, the candidate configurations of the smoothing with the composite

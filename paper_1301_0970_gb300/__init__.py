@@ -95,6 +95,7 @@ _SIGNATURES = {
     "cgdir_set_autotune": (c_int, [c_void_p, c_int]),
     "cgdir_tuning_read": (c_int, [c_void_p, POINTER(cgdir_tuning), c_int]),
     "cgdir_tuning_load": (c_int, [c_void_p, POINTER(cgdir_tuning), c_int]),
+    "cgdir_selftest_wait_timeout": (c_int, [c_void_p, c_int]),
     "cgdir_register_batch": (c_int, [c_void_p, c_int, POINTER(cgdir_volume), POINTER(cgdir_volume),
                                      POINTER(cgdir_masks), POINTER(cgdir_masks), POINTER(cgdir_params),
                                      POINTER(c_void_p), c_int, POINTER(cgdir_level_stats)]),
@@ -379,6 +380,11 @@ class Context:
                  "force_zchunk": b.force_zchunk, "smooth_ms": b.smooth_ms, "force_ms": b.force_ms,
                  "default_smooth_ms": b.default_smooth_ms, "default_force_ms": b.default_force_ms}
                 for b in buf[:n]]
+
+    def selftest_wait_timeout(self, limit_us: int = 20000) -> int:
+        """Run a kernel whose bounded wait runs out; returns the status
+        (CGDIR_ETIMEDOUT when the timeout path works) without raising."""
+        return load().cgdir_selftest_wait_timeout(self._h, int(limit_us))
 
     def load_tuning(self, table):
         """Install a tuning table as tuning() returns it (e.g. saved as JSON by

@@ -384,3 +384,19 @@ def test_fused_schedule_matches_oracle():
     got = got.cpu().numpy().astype(np.float64)
     assert float(np.sqrt(((got - ref) ** 2).sum(axis=0).mean())) <= 0.05
     assert [s["iters_run"] for s in st] == [r["iters_run"] for r in rst]
+
+
+def test_device_wait_that_runs_out_reports_a_timeout_and_the_context_stays_usable():
+    """A kernel waits on a barrier that nothing completes (20 ms limit): the
+    call returns ETIMEDOUT, the error word is cleared, and the same context
+    then registers a case with the same result as a fresh one."""
+    c = phantom.make_case("phantom64", shape=(10, 20, 24))
+    kw = dict(levels=2, iters=[4, 3], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as fresh:
+        ref, _ = single(fresh, c, kw)
+    with cg.Context(0) as ctx:
+        assert ctx.selftest_wait_timeout(20000) == cg.CGDIR_ETIMEDOUT
+        assert ctx.selftest_wait_timeout(0) == cg.CGDIR_EINVAL
+        got, _ = single(ctx, c, kw)
+        assert torch.equal(got, ref)
+        assert ctx.selftest_wait_timeout(1000) == cg.CGDIR_ETIMEDOUT
