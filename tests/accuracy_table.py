@@ -1,9 +1,9 @@
 #!/usr/bin/env python3
 """Final-DVF error of the GPU registration against the FP64 oracle, per
 configuration and image storage type (FP32 / FP16 / BF16; the oracle always
-runs on the FP32 images).  Test infrastructure, run by hand on a GPU machine:
+runs on the FP32 images).  Test infrastructure, run by hand on a machine with a GB300:
 
-    python tests/accuracy_table.py [--full] > gpurun_out/accuracy.json
+    python tests/accuracy_table.py [--full] > accuracy.json
 
 (--full runs the 512 x 512 x 160 case for its whole 100/50/25 iterations:
 about 7 minutes of the oracle on 16 host cores.)
