@@ -319,10 +319,11 @@ int cgdir_compose(cgdir_ctx *ctx, const float *u, const float *du, int mode, flo
 /* Fluid smoothing and composite update (Algorithm A steps 2-3):
    out = G(du) + u(x + G(du)(x)) (mode CGDIR_COMPOSE) or u + G(du)
    (CGDIR_ADDITIVE), G the Gaussian of sigma voxels (0 <= sigma <= 2; 0 is
-   no smoothing).  The kernels are the ones a registration on this context
-   uses (the context's smoothing variant: under CGDIR_SMOOTH=fused, one 3-D
-   tile kernel).  Fields [3][nz][ny][nx] FP32 in device memory; out must not
-   alias u or du.  Errors: EINVAL, ENOMEM, ECUDA. */
+   no smoothing).  The kernels are the context's forced smoothing variant
+   (CGDIR_SMOOTH at creation; under CGDIR_SMOOTH=fused one 3-D tile kernel
+   for both steps), else chosen by size; every choice gives the same bits.
+   Fields [3][nz][ny][nx] FP32 in device memory; out must not alias u or
+   du.  Errors: EINVAL, ENOMEM, ECUDA. */
 int cgdir_smooth_compose(cgdir_ctx *ctx, const float *du, const float *u, int mode, float sigma,
                          int nx, int ny, int nz, float *out);
 
