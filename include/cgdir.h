@@ -399,7 +399,10 @@ unsigned long long cgdir_launch_count(void);
 #define CGDIR_K_SMOOTH_DU  1   /* Gaussian of du and, fused into it, the
                                   composite update (kernels 1 + 4, steps 2-3) */
 #define CGDIR_K_COMPOSE    2   /* composite update when it runs on its own    */
-#define CGDIR_K_SMOOTH_U   3   /* Gaussian of u (kernel 1, step 4)            */
+#define CGDIR_K_SMOOTH_U   3   /* Gaussian of u (kernel 1, step 4); on the fused
+                                  schedule with the next iteration's warp,
+                                  which the FORCE class then lacks after the
+                                  first iteration                             */
 #define CGDIR_K_FINALIZE   4   /* RMS-ID reduction and stop test (kernel 5)  */
 #define CGDIR_K_METRIC     5   /* warp-only metric pass after a level's cap  */
 #define CGDIR_K_SETUP      6   /* pyramid, masks, UROI, signs, prolongation  */
