@@ -10,13 +10,17 @@
 // holds until the process exits.  The caller still passes the inputs.
 //
 // Host code must not use the array's name as a device address (it is a host
-// stand-in for the symbol): the first call on a device looks up the real
-// address with cudaGetSymbolAddress, with that device current, and later
-// calls on that device reuse it.  Every call shares the one array, so calls
-// whose work overlaps on the GPU (two streams, two threads) race and give
-// undefined results; calls on one stream are ordered and safe.  The counter
-// is cleared at the start of every call.
+// stand-in for the symbol): the array's real address is looked up with
+// cudaGetSymbolAddress, with the device current, on the first call on that
+// device and again whenever the device's current CUDA context is not the one
+// the address was taken in (cudaDeviceReset, or another context made
+// current, can load the module at another address).  Every call shares the
+// one array, so calls whose work overlaps on the GPU (two streams, two
+// threads) race and give undefined results; calls on one stream are ordered
+// and safe.  The counter is cleared at the start of every call.
 #include "cgdir_internal.cuh"
+
+#include <cuda.h>
 
 #include <cmath>
 #include <mutex>
@@ -25,7 +29,7 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kMaxBlocks = 4096;                 // partials held in the array
-constexpr int kVoxelsPerThread = 64;             // keeps per-thread FP32 sums short
+constexpr int kVoxelsPerThread = 64;             // voxels per thread at the largest volume
 constexpr long long kMaxVoxels = (long long)kMaxBlocks * kNT * kVoxelsPerThread;   // 67,108,864
 // layout (doubles): [0, 4*kMaxBlocks) partials {ssd, count, -, -};
 // [4*kMaxBlocks] completion counter (as unsigned); [4*kMaxBlocks + 2 ..] result {ssd, count}
@@ -46,7 +50,7 @@ __global__ void __launch_bounds__(kNT) k_rms_noalloc(const float *__restrict__ I
                                                      const uint8_t *__restrict__ uroi, int nx, int ny, int nz,
                                                      double *scratch) {
     const size_t N = (size_t)nx * ny * nz;
-    float ssd = 0.f;
+    double ssd = 0.0;                            // FP64 per thread, like the block and grid sums
     int cnt = 0;
     for (size_t i = (size_t)blockIdx.x * kNT + threadIdx.x; i < N; i += (size_t)gridDim.x * kNT) {
         if (uroi && !uroi[i]) continue;
@@ -61,14 +65,14 @@ __global__ void __launch_bounds__(kNT) k_rms_noalloc(const float *__restrict__ I
                             ((q & 4) ? c.wz : 1.f - c.wz);
             acc = fmaf(w, __ldg(I0 + cgdir::vox(cx, cy, cz, nx, ny)), acc);
         }
-        const float r = __ldg(T0 + i) - acc;
-        ssd = fmaf(r, r, ssd);
+        const double r = (double)(__ldg(T0 + i) - acc);
+        ssd = fma(r, r, ssd);
         cnt += 1;
     }
     // fixed-order block sum in FP64
     __shared__ double ws[kNT / 32], wc[kNT / 32];
     __shared__ int last;
-    double s = warp_sum_d((double)ssd), k = warp_sum_d((double)cnt);
+    double s = warp_sum_d(ssd), k = warp_sum_d((double)cnt);
     if ((threadIdx.x & 31) == 0) { ws[threadIdx.x >> 5] = s; wc[threadIdx.x >> 5] = k; }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -103,10 +107,41 @@ __global__ void __launch_bounds__(kNT) k_rms_noalloc(const float *__restrict__ I
     }
 }
 
-// Device address of g_rms_scratch per device, looked up once with that device current.
+// Current context's unique id through the driver entry points (resolved once).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+bool current_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr, *q = nullptr;
+        cudaDriverEntryPointQueryResult r1, r2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &r1) == cudaSuccess &&
+            r1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &q, 12000, cudaEnableDefault, &r2) == cudaSuccess &&
+            r2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+            get_id = reinterpret_cast<CtxGetIdFn>(q);
+        } else {
+            cudaGetLastError();
+        }
+    });
+    CUcontext c = nullptr;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || c == nullptr) return false;
+    return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_rms_scratch per device, with the id of the context it
+// was looked up in; looked up again when the current context differs.
 constexpr int kMaxDevices = 64;
+struct ScratchAddr {
+    double *ptr = nullptr;
+    unsigned long long ctx_id = 0;
+};
 std::mutex g_mu;
-double *g_addr[kMaxDevices] = {};
+ScratchAddr g_addr[kMaxDevices];
 
 int scratch_for_current_device(double **out) {
     int dev = 0;
@@ -115,16 +150,22 @@ int scratch_for_current_device(double **out) {
         return CGDIR_ECUDA;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    ScratchAddr &a = g_addr[dev];
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);   // false before the runtime binds a context
+    if (!a.ptr || !have_id || id != a.ctx_id) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_rms_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_rms_scratch);   // binds the device's context
         if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
+            a.ptr = nullptr;
             return CGDIR_ECUDA;
         }
-        g_addr[dev] = static_cast<double *>(p);
+        if (!current_context_id(&id)) return CGDIR_ECUDA;
+        a.ptr = static_cast<double *>(p);
+        a.ctx_id = id;
     }
-    *out = g_addr[dev];
+    *out = a.ptr;
     return CGDIR_OK;
 }
 
