@@ -138,13 +138,19 @@ typedef struct {
     const float  *init_dvf;           /* NULL, or a full-resolution DVF that
                                          replaces the coarse levels (Sec. 4)    */
     int           init_dvf_where;     /* CGDIR_HOST or CGDIR_DEVICE             */
-    int           storage_dtype;      /* type of the pyramid's images: CGDIR_F32,
+    int           storage_dtype;      /* type of the images at the finest level
+                                         (the input resolution): CGDIR_F32,
                                          CGDIR_F16, CGDIR_BF16 (inputs converted
                                          at ingest, round to nearest even), or
                                          CGDIR_STORAGE_AUTO = the input type (F32
-                                         if static and moving differ).  All force,
-                                         DVF and smoothing arithmetic is FP32
-                                         whatever the storage.                  */
+                                         if static and moving differ).  The
+                                         coarser levels (1/7 of the pyramid's
+                                         voxels) are restricted from it and kept
+                                         in FP32: the box mean lowers the noise
+                                         sqrt(8)-fold per level, so a 16-bit
+                                         rounding there would weigh 2.8x, 8x, ...
+                                         more.  All force, DVF and smoothing
+                                         arithmetic is FP32 whatever the storage. */
 } cgdir_params;
 
 typedef struct {
@@ -379,11 +385,16 @@ int cgdir_rms_id(cgdir_ctx *ctx, const float *I0, const float *T0, const float *
    process exits.  Limit: nx*ny*nz <= 67,108,864 voxels; larger volumes are
    rejected with CGDIR_EINVAL.  Device pointers as in cgdir_rms_id (uroi may be
    NULL = whole volume); stream = cudaStream_t (NULL = legacy default stream).
-   Blocking: *rms_host (and *count_host if not NULL) are written on return.
-   The first call on a device looks up the array's device address (with that
-   device current); make that first call before any stream capture.  All calls
-   share the one array: calls whose work overlaps on the GPU (two streams or
-   threads at once) race and give undefined results.  Errors: EINVAL, ECUDA. */
+   Sums are FP64 from each thread's first term on (fixed order within a
+   block and across blocks).
+   Blocking: *rms_host (and *count_host if not NULL) are written on return,
+   after the call has synchronized `stream`.  So no call may be made while a
+   stream of that device is capturing a CUDA graph.  The first call on a
+   device (and the first after that device's current context changes, e.g.
+   after cudaDeviceReset) does the set-up: it looks up the array's device
+   address with the device current.  All calls share the one array: calls
+   whose work overlaps on the GPU (two streams or threads at once) race and
+   give undefined results.  Errors: EINVAL, ECUDA. */
 int cgdir_rms_id_noalloc(const float *I0, const float *T0, const float *u, const uint8_t *uroi,
                          int nx, int ny, int nz, void *stream, double *rms_host,
                          long long *count_host);
@@ -472,7 +483,8 @@ typedef struct {
 
 /* Tune every level of a `levels`-level pyramid whose finest level is
    nx x ny x nz, with k structures, structure terms at the levels of
-   contour_level_mask, image storage storage_dtype (CGDIR_F32/F16/BF16) and
+   contour_level_mask, image storage storage_dtype (CGDIR_F32/F16/BF16; as in
+   cgdir_params, the coarser levels are tuned for their FP32 images) and
    Gaussian sigma (voxels).  Errors: EINVAL, ENOMEM, ECUDA. */
 int cgdir_autotune(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int levels, unsigned contour_level_mask,
                    int storage_dtype, float sigma);

@@ -270,8 +270,8 @@ int cgdir_autotune(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int levels, un
         for (int a = 0; a < 3; ++a) d[a] = (d[a] + 1) / 2;
     }
     for (int l = 0; l < levels; ++l)
-        TRY(tune_level(ctx, dims[l][0], dims[l][1], dims[l][2], k, (contour_level_mask >> l) & 1u, storage_dtype,
-                       sigma));
+        TRY(tune_level(ctx, dims[l][0], dims[l][1], dims[l][2], k, (contour_level_mask >> l) & 1u,
+                       level_storage(storage_dtype, l, levels), sigma));
     return CGDIR_OK;
 }
 

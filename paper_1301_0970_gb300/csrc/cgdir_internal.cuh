@@ -127,6 +127,15 @@ struct LevelCoopArgs {
 int level_coop_grid(int nx, int ny, int nz, bool contour, int img_dtype);
 cudaError_t launch_level_coop(const LevelCoopArgs &p, int grid, cudaStream_t s);
 
+// Image type of pyramid level l (0 = coarsest) of L when the registration
+// stores its images as `storage`: the finest level (the input resolution,
+// 7/8 of the pyramid's voxels) in that type, the coarser levels in float32.
+// The box mean lowers the image noise by sqrt(8) per level, so a 16-bit
+// rounding of a restricted image weighs 2.8x, 8x, ... more against it than
+// at the finest level; the coarse levels' DVF, prolongated, then carries
+// that error to the end.
+inline int level_storage(int storage, int l, int L) { return l == L - 1 ? storage : CGDIR_F32; }
+
 // Bytes of the two-pass force scratch for n voxels and k structures.
 inline size_t force_scratch_bytes(size_t n, int k) {
     return n * 4 + ((n * 2 + 255) / 256) * 256 + (size_t)k * n * 4 + 512;
@@ -214,6 +223,9 @@ bool fused_schedule_ok(const ForceArgs &a);
 cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint8_t *bits,
                               cudaStream_t s);
 cudaError_t launch_restrict_image(const void *in, int dtype, int nx, int ny, int nz, void *out,
+                                  cudaStream_t s);
+// The same from an in_dtype level into an out_dtype level.
+cudaError_t launch_restrict_image(const void *in, int in_dtype, int nx, int ny, int nz, void *out, int out_dtype,
                                   cudaStream_t s);
 cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint8_t *out,
                                  cudaStream_t s);

@@ -34,10 +34,10 @@ __global__ void k_pack(MaskPtrs m, int k, size_t n, uint8_t *__restrict__ bits) 
 }
 
 // 2x2x2 box mean, source indices clamped (odd sizes replicate the border),
-// accumulated in float32 and stored in the image type.
-template <typename IT>
+// accumulated in float32 and stored in the output level's image type.
+template <typename IT, typename OT>
 __global__ void k_restrict_image(const IT *__restrict__ in, int nx, int ny, int nz,
-                                 IT *__restrict__ out) {
+                                 OT *__restrict__ out) {
     const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
     const size_t Nc = (size_t)cx * cy * cz;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < Nc;
@@ -50,7 +50,7 @@ __global__ void k_restrict_image(const IT *__restrict__ in, int nx, int ny, int 
                       z = min(2 * Z + ((q >> 2) & 1), nz - 1);
             s += ld_img<IT>(in + vox(x, y, z, nx, ny));
         }
-        out[i] = from_f<IT>(s * 0.125f);
+        out[i] = from_f<OT>(s * 0.125f);
     }
 }
 
@@ -260,18 +260,34 @@ cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_restrict_image(const void *in, int dtype, int nx, int ny, int nz, void *out,
+template <typename IT>
+static void restrict_image_to(const void *in, int nx, int ny, int nz, void *out, int out_dtype, size_t Nc,
+                              cudaStream_t s) {
+    const IT *src = static_cast<const IT *>(in);
+    if (out_dtype == CGDIR_F16)
+        k_restrict_image<IT, __half><<<flat_grid(Nc), 256, 0, s>>>(src, nx, ny, nz, (__half *)out);
+    else if (out_dtype == CGDIR_BF16)
+        k_restrict_image<IT, __nv_bfloat16><<<flat_grid(Nc), 256, 0, s>>>(src, nx, ny, nz, (__nv_bfloat16 *)out);
+    else
+        k_restrict_image<IT, float><<<flat_grid(Nc), 256, 0, s>>>(src, nx, ny, nz, (float *)out);
+}
+
+cudaError_t launch_restrict_image(const void *in, int in_dtype, int nx, int ny, int nz, void *out, int out_dtype,
                                   cudaStream_t s) {
     const size_t Nc = (size_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
-    if (dtype == CGDIR_F16)
-        k_restrict_image<__half><<<flat_grid(Nc), 256, 0, s>>>((const __half *)in, nx, ny, nz, (__half *)out);
-    else if (dtype == CGDIR_BF16)
-        k_restrict_image<__nv_bfloat16><<<flat_grid(Nc), 256, 0, s>>>((const __nv_bfloat16 *)in, nx, ny, nz,
-                                                                      (__nv_bfloat16 *)out);
+    if (in_dtype == CGDIR_F16)
+        restrict_image_to<__half>(in, nx, ny, nz, out, out_dtype, Nc, s);
+    else if (in_dtype == CGDIR_BF16)
+        restrict_image_to<__nv_bfloat16>(in, nx, ny, nz, out, out_dtype, Nc, s);
     else
-        k_restrict_image<float><<<flat_grid(Nc), 256, 0, s>>>((const float *)in, nx, ny, nz, (float *)out);
+        restrict_image_to<float>(in, nx, ny, nz, out, out_dtype, Nc, s);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_image(const void *in, int dtype, int nx, int ny, int nz, void *out,
+                                  cudaStream_t s) {
+    return launch_restrict_image(in, dtype, nx, ny, nz, out, dtype, s);
 }
 
 cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint8_t *out,

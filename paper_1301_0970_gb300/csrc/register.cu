@@ -44,7 +44,10 @@ struct RegPlan {
     int8_t sign[kMaxMasks] = {};
     int nx = 0, ny = 0, nz = 0, k = 0, L = 0, maxcap = 0, hcap = 0, first = 0, sdt = CGDIR_F32;
     int dims[CGDIR_MAX_LEVELS][3] = {};
-    size_t Nl[CGDIR_MAX_LEVELS] = {}, off[CGDIR_MAX_LEVELS + 1] = {}, Nf = 0, Ntot = 0, esz = 4, tsz = 8;
+    size_t Nl[CGDIR_MAX_LEVELS] = {}, off[CGDIR_MAX_LEVELS + 1] = {}, Nf = 0, Ntot = 0;
+    int ldt[CGDIR_MAX_LEVELS] = {};                   // image type per level (level_storage)
+    size_t ioff[CGDIR_MAX_LEVELS + 1] = {};           // byte offsets of the levels' images
+    size_t toff[CGDIR_MAX_LEVELS + 1] = {};           // byte offsets of the levels' texels
     ForceArgs base{};
     // device buffers of the slot
     char *T[CGDIR_MAX_LEVELS] = {}, *I[CGDIR_MAX_LEVELS] = {};
@@ -156,8 +159,6 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
     pl.nx = nx; pl.ny = ny; pl.nz = nz; pl.k = k; pl.L = L; pl.maxcap = maxcap; pl.hcap = maxcap + 1;
     pl.first = P->init_dvf ? L - 1 : 0;
     pl.sdt = P->storage_dtype >= 0 ? P->storage_dtype : (S->dtype == M->dtype ? S->dtype : CGDIR_F32);
-    pl.esz = img_elem_size(pl.sdt);
-    pl.tsz = tex_elem_size(pl.sdt);
     pl.dims[L - 1][0] = nx; pl.dims[L - 1][1] = ny; pl.dims[L - 1][2] = nz;
     for (int l = L - 2; l >= 0; --l)
         for (int a = 0; a < 3; ++a) pl.dims[l][a] = (pl.dims[l + 1][a] + 1) / 2;
@@ -165,6 +166,9 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
     for (int l = 0; l < L; ++l) {
         pl.Nl[l] = (size_t)pl.dims[l][0] * pl.dims[l][1] * pl.dims[l][2];
         pl.off[l + 1] = pl.off[l] + round_up(pl.Nl[l], 64);
+        pl.ldt[l] = level_storage(pl.sdt, l, L);
+        pl.ioff[l + 1] = pl.ioff[l] + round_up(pl.Nl[l], 64) * img_elem_size(pl.ldt[l]);
+        pl.toff[l + 1] = pl.toff[l] + round_up(pl.Nl[l], 64) * tex_elem_size(pl.ldt[l]);
     }
     pl.Nf = pl.Nl[L - 1];
     pl.Ntot = pl.off[L];
@@ -178,9 +182,9 @@ int plan_make(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, cons
                                    metric_partial_count(d[0], d[1], d[2])));
     }
     const size_t Ntot = pl.Ntot, Nf = pl.Nf;
-    pl.need[RegPlan::B_IMG] = 2 * Ntot * pl.esz;
+    pl.need[RegPlan::B_IMG] = 2 * pl.ioff[L];
     pl.need[RegPlan::B_BITS] = 3 * Ntot;
-    pl.need[RegPlan::B_TEX] = Ntot * pl.tsz;
+    pl.need[RegPlan::B_TEX] = pl.toff[L];
     pl.need[RegPlan::B_FIELDS] = 4 * 3 * Nf * sizeof(float);
     pl.need[RegPlan::B_PARTIAL] = std::max<size_t>(np * kPartialStride * sizeof(double), 256);
     pl.need[RegPlan::B_STATE] = pl.state_bytes;
@@ -199,8 +203,8 @@ int plan_autotune(cgdir_ctx *ctx, const RegPlan &pl) {
     if (!ctx->autotune_on) return CGDIR_OK;
     for (int l = pl.first; l < pl.L; ++l) {
         const int contour = ((pl.P.contour_level_mask >> l) & 1u) && pl.k > 0;
-        if (ctx->tuned.count(TuneKey{pl.dims[l][0], pl.dims[l][1], pl.dims[l][2], contour, pl.sdt})) continue;
-        TRY(tune_level(ctx, pl.dims[l][0], pl.dims[l][1], pl.dims[l][2], pl.k, contour, pl.sdt,
+        if (ctx->tuned.count(TuneKey{pl.dims[l][0], pl.dims[l][1], pl.dims[l][2], contour, pl.ldt[l]})) continue;
+        TRY(tune_level(ctx, pl.dims[l][0], pl.dims[l][1], pl.dims[l][2], pl.k, contour, pl.ldt[l],
                        std::max(pl.P.sigma_fluid, pl.P.sigma_diff)));
     }
     return CGDIR_OK;
@@ -219,8 +223,8 @@ int plan_prepare(cgdir_ctx *ctx, Slot &sl, RegPlan &pl, cudaStream_t s) {
          *p_rowdist = p[RegPlan::B_ROWDIST], *p_stage = p[RegPlan::B_STAGE];
     pl.generation = ws.generation;
     for (int l = 0; l < L; ++l) {
-        pl.T[l] = (char *)p_img + pl.off[l] * pl.esz;
-        pl.I[l] = (char *)p_img + (Ntot + pl.off[l]) * pl.esz;
+        pl.T[l] = (char *)p_img + pl.ioff[l];
+        pl.I[l] = (char *)p_img + pl.ioff[L] + pl.ioff[l];
         pl.SB[l] = (uint8_t *)p_bits + pl.off[l];
         pl.MB[l] = (uint8_t *)p_bits + Ntot + pl.off[l];
         pl.UR[l] = (uint8_t *)p_bits + 2 * Ntot + pl.off[l];
@@ -288,20 +292,20 @@ int plan_prepare(cgdir_ctx *ctx, Slot &sl, RegPlan &pl, cudaStream_t s) {
 // The device part of a registration (capturable: touches the slot's buffers only).
 int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *prof) {
     const cgdir_params *P = &pl.P;
-    const int L = pl.L, k = pl.k, sdt = pl.sdt;
+    const int L = pl.L, k = pl.k;
     const unsigned m = ctx->prof_mask;
     for (int l = L - 2; l >= 0; --l) {
         const int *d = pl.dims[l + 1];
         ProfScope ps(prof, m, s, CGDIR_K_SETUP, l);
-        CK(launch_restrict_image(pl.T[l + 1], sdt, d[0], d[1], d[2], pl.T[l], s));
-        CK(launch_restrict_image(pl.I[l + 1], sdt, d[0], d[1], d[2], pl.I[l], s));
+        CK(launch_restrict_image(pl.T[l + 1], pl.ldt[l + 1], d[0], d[1], d[2], pl.T[l], pl.ldt[l], s));
+        CK(launch_restrict_image(pl.I[l + 1], pl.ldt[l + 1], d[0], d[1], d[2], pl.I[l], pl.ldt[l], s));
         CK(launch_restrict_bits(pl.SB[l + 1], d[0], d[1], d[2], pl.SB[l], s));
         CK(launch_restrict_bits(pl.MB[l + 1], d[0], d[1], d[2], pl.MB[l], s));
     }
     for (int l = 0; l < L; ++l) {
         if (((P->contour_level_mask >> l) & 1u) && k > 0 && !ctx->plain_kernels) {
             ProfScope ps(prof, m, s, CGDIR_K_SETUP, l);
-            CK(launch_make_texels(pl.I[l], sdt, pl.MB[l], pl.Nl[l], pl.tex + pl.off[l] * pl.tsz, s));
+            CK(launch_make_texels(pl.I[l], pl.ldt[l], pl.MB[l], pl.Nl[l], pl.tex + pl.toff[l], s));
         }
         const double f = (double)(1 << (L - 1 - l));
         const double sp[3] = {P->spacing_mm[0] * f, P->spacing_mm[1] * f, P->spacing_mm[2] * f};
@@ -316,6 +320,7 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
     float *ucur = pl.ua, *uoth = pl.ub;
     for (int l = pl.first; l < L; ++l) {
         const int lx = pl.dims[l][0], ly = pl.dims[l][1], lz = pl.dims[l][2];
+        const int sdt = pl.ldt[l];
         if (l == pl.first) {
             if (!P->init_dvf) CK(cudaMemsetAsync(ucur, 0, 3 * pl.Nl[l] * sizeof(float), s));
         } else {
@@ -333,7 +338,7 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
         ForceArgs a = pl.base;
         a.I0 = pl.I[l]; a.T0 = pl.T[l]; a.img_dtype = sdt;
         a.mbits = pl.MB[l]; a.sbits = pl.SB[l]; a.uroi = pl.UR[l];
-        a.mtex = ctx->plain_kernels ? nullptr : (const void *)(pl.tex + pl.off[l] * pl.tsz);
+        a.mtex = ctx->plain_kernels ? nullptr : (const void *)(pl.tex + pl.toff[l]);
         a.u = ucur; a.du = pl.du; a.warped = nullptr; a.partial = pl.partial; a.stop_flag = flags + l;
         a.nx = lx; a.ny = ly; a.nz = lz;
         a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
