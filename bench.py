@@ -2,10 +2,14 @@
 """Throughput of contour-guided demons registration (CG-DIR) on GB300.
 
 One step = one whole registration (Algorithm A over the pyramid: restriction,
-UROI, every level's iterations, prolongation) of the head-and-neck-shaped
-synthetic case: 256 x 256 x 96 float32 CT, 5 structure masks, 3 levels with
-100 / 50 / 25 iterations, FIXED stopping.  Metric: voxel-iterations/s =
-sum over levels of (voxels x iterations) per step / step time.
+UROI, every level's iterations, prolongation) of the pelvic CT-to-CBCT-like
+synthetic case: 512 x 512 x 160 float32 CT, 6 structure masks, 3 levels with
+100 / 50 / 25 iterations, FIXED stopping (the largest single-GPU workload).
+Metric: voxel-iterations/s = sum over levels of (voxels x iterations) per
+step / step time.  The same JSON line carries the 256 x 256 x 96
+head-and-neck case as a secondary key and, under "batched", the uneven-size
+mix of 32 registrations run as one batch with FP16 image storage against
+plain FP32 registrations one at a time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgdir|reference]
 
@@ -30,14 +34,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "voxel-iters/s and p50/p99 latency per registration, batched vs plain FP32"
 UNIT = "voxel-iter/s"
-WORKLOAD = {"name": "headneck256", "levels": 3, "iters": [100, 50, 25]}
-# other single-registration workloads (--workload): the pelvic CT-to-CBCT-like
-# case, 512 x 512 x 160, 6 structures (built on the GPU: host generation of
-# 42 M voxels takes minutes)
-WORKLOADS = {"headneck256": dict(WORKLOAD), "pelvis512": {"name": "pelvis512", "levels": 3, "iters": [100, 50, 25]}}
-# bounded sample of the same workload for the CPU oracle: same case, same
-# pyramid, iterations cut to 8 / 4 / 2 (about 16.5 M voxel-iterations)
-ORACLE_SAMPLE_ITERS = [8, 4, 2]
+# single-registration workloads (--workload): the pelvic CT-to-CBCT-like case
+# (default) and the head-and-neck case; both are built on the GPU (host
+# generation of 42 M voxels takes minutes) and copied to the host for the
+# end-to-end leg and the oracle
+WORKLOADS = {"pelvis512": {"name": "pelvis512", "levels": 3, "iters": [100, 50, 25]},
+             "headneck256": {"name": "headneck256", "levels": 3, "iters": [100, 50, 25]}}
+WORKLOAD = dict(WORKLOADS["pelvis512"])
+# bounded sample of the workload for the CPU oracle: the central SAMPLE_SLICES
+# axial slices of the same case, the same pyramid and iterations (the oracle
+# takes about a minute for the whole 512 x 512 x 160 registration)
+SAMPLE_SLICES = 16
 FORCE_BYTES_PER_VOXEL = {True: 35, False: 33}   # contour terms on / off, FP32 images
 FORCE_BYTES_PER_VOXEL_16 = {True: 31, False: 29}   # the same with 16-bit images
 SMOOTH_BYTES_PER_VOXEL = 24                       # Gaussian of a 3-component field: read 12, write 12
@@ -58,14 +65,18 @@ def parse():
     ap.add_argument("--shape", default=None,
                     help="with --only: nz,ny,nx of the inputs (the workload's case resampled)")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
-                    help="single: the head-and-neck registration (default); batch: 32 cases of "
+                    help="single: one registration per step (default); batch: 32 cases of "
                          "uneven sizes in one graph launch, FP16 images, against plain FP32 one "
                          "at a time; serve: Poisson arrivals of the same mix at 1-64 requests/s "
                          "under a 160 GB device budget, p50/p99 latency against plain FP32 one at "
                          "a time")
     ap.add_argument("--batch-n", type=int, default=32, help="cases in the batch / serving mix")
-    ap.add_argument("--workload", default="headneck256", choices=sorted(WORKLOADS),
-                    help="single-registration workload (default: the 256x256x96 head-and-neck case)")
+    ap.add_argument("--workload", default="pelvis512", choices=sorted(WORKLOADS),
+                    help="single-registration workload (default: the 512x512x160 pelvic case)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="single: skip the head-and-neck secondary key and the batched comparison")
+    ap.add_argument("--batch-passes", type=int, default=2,
+                    help="single: timed passes of the batched comparison (after one warm-up pass)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="image storage type of the registration (arithmetic stays FP32)")
     ap.add_argument("--rates", default="1,2,4,8,16,32,64", help="serve: arrival rates (requests/s)")
@@ -107,16 +118,38 @@ def whole_job_value(world: int, vox_iters_per_step: int, steps: int, max_total_m
     return world * vox_iters_per_step * steps / (max_total_ms / 1e3)
 
 
-def workload_config(case, n_gpus, storage="f32"):
+def workload_config(case, n_gpus, storage="f32", wl=None):
+    wl = wl or WORKLOAD
     nz, ny, nx = case.shape
     img = {"f32": "float32", "f16": "float16", "bf16": "bfloat16"}[storage]
-    return {"workload": f"{WORKLOAD['name']}: {nx}x{ny}x{nz} {img} CT, {case.k} uint8 structure "
-                        f"masks, {WORKLOAD['levels']}-level pyramid "
-                        f"{'/'.join(map(str, WORKLOAD['iters']))} iterations, FIXED stop",
-            "shape_zyx": [nz, ny, nx], "masks": case.k, "levels": WORKLOAD["levels"],
-            "iters": WORKLOAD["iters"], "lambda": case.lam[0], "sigma": 1.0,
+    return {"workload": f"{wl['name']}: {nx}x{ny}x{nz} {img} CT, {case.k} uint8 structure "
+                        f"masks, {wl['levels']}-level pyramid "
+                        f"{'/'.join(map(str, wl['iters']))} iterations, FIXED stop",
+            "shape_zyx": [nz, ny, nx], "masks": case.k, "levels": wl["levels"],
+            "iters": wl["iters"], "lambda": case.lam[0], "sigma": 1.0,
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"replicas x{n_gpus}"}
+
+
+class HostCase:
+    """Host copies of a case built on the device (float32 images, uint8 masks
+    [k, nz, ny, nx]), plus its structure parameters."""
+
+    def __init__(self, dc):
+        self.static, self.moving = dc.static.cpu().numpy(), dc.moving.cpu().numpy()
+        self.static_masks, self.moving_masks = dc.static_masks.cpu().numpy(), dc.moving_masks.cpu().numpy()
+        self.shape, self.k, self.lam, self.signs = tuple(dc.shape), dc.k, dc.lam, dc.signs
+
+
+def build_case(torch, name, index, dev):
+    """One case of a single-registration workload, built on the device:
+    (device case with images and masks, host copies)."""
+    import phantom
+    dc = phantom.make_case_device(name, index=index, device=dev)
+    dc.u_gt = dc.body = None
+    host = HostCase(dc)
+    torch.cuda.empty_cache()
+    return dc, host
 
 
 def oracle_cores():
@@ -124,25 +157,36 @@ def oracle_cores():
     return oracle.num_threads()
 
 
-def time_oracle_sample(case):
-    """One registration of the bounded sample by the FP64 CPU oracle."""
+def oracle_sample(host):
+    """The oracle's bounded sample of a case: its central SAMPLE_SLICES axial
+    slices, the same structures and signs."""
+    nz = host.shape[0]
+    z0 = max(0, (nz - SAMPLE_SLICES) // 2)
+    z1 = min(nz, z0 + SAMPLE_SLICES)
+    return (host.static[z0:z1], host.moving[z0:z1], host.static_masks[:, z0:z1], host.moving_masks[:, z0:z1])
+
+
+def time_oracle_sample(host):
+    """One registration of the bounded sample by the FP64 CPU oracle:
+    (voxel-iterations, seconds)."""
     import oracle
     import phantom
+    S, M, SM, MM = oracle_sample(host)
     t0 = time.perf_counter()
-    oracle.register(case.static, case.moving, case.static_masks, case.moving_masks,
-                    levels=WORKLOAD["levels"], iters=ORACLE_SAMPLE_ITERS, lam=case.lam,
-                    sign=case.signs, stop_mode=oracle.STOP_FIXED)
+    oracle.register(S, M, SM, MM, levels=WORKLOAD["levels"], iters=WORKLOAD["iters"], lam=host.lam,
+                    sign=host.signs, stop_mode=oracle.STOP_FIXED)
     dt = time.perf_counter() - t0
-    vi = phantom.voxel_iters(case.shape, WORKLOAD["levels"], ORACLE_SAMPLE_ITERS)
-    return vi, dt
+    return phantom.voxel_iters(S.shape, WORKLOAD["levels"], WORKLOAD["iters"]), dt
 
 
-def sample_desc(case):
+def sample_desc(host):
     import phantom
-    vi = phantom.voxel_iters(case.shape, WORKLOAD["levels"], ORACLE_SAMPLE_ITERS)
-    return (f"same case and pyramid, iterations {'/'.join(map(str, ORACLE_SAMPLE_ITERS))} "
-            f"instead of {'/'.join(map(str, WORKLOAD['iters']))} ({vi / 1e6:.1f} M voxel-iters "
-            f"per run, set-up included)")
+    S = oracle_sample(host)[0]
+    nz, ny, nx = S.shape
+    vi = phantom.voxel_iters(S.shape, WORKLOAD["levels"], WORKLOAD["iters"])
+    return (f"the central {nz} axial slices of the same case ({nx}x{ny}x{nz}), same structures, pyramid "
+            f"and iterations {'/'.join(map(str, WORKLOAD['iters']))} ({vi / 1e6:.1f} M voxel-iters per run, "
+            f"set-up included)")
 
 
 # --------------------------------------------------------------------------- #
@@ -224,36 +268,24 @@ def sigma_default(kw):
     return kw.get("sigma_fluid", 1.0) == 1.0 and kw.get("sigma_diff", 1.0) == 1.0
 
 
-def force_traffic_record(case):
-    """DRAM bytes per launch of the force kernel from the committed ncu
-    summary (profiles/force_headneck256.md), if it was taken on the current
-    kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "force_headneck256.md")
+def traffic_record(kernel, workload, sources):
+    """DRAM bytes per launch of a kernel from its committed ncu summary
+    (profiles/<kernel>_<workload>.md), if it was taken on the current kernel
+    sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     sha, traffic = None, None
     for line in open(path):
-        if line.startswith("- force kernel sources sha1"):
+        if line.startswith("- kernel sources sha1"):
             sha = line.split(":", 1)[1].strip()
         if line.startswith("- dram bytes per launch (full size):"):
             traffic = float(line.split(":", 1)[1].strip())
-    return traffic if (sha == force_sources_sha1() and traffic) else None
+    return traffic if (sha == sources_sha1(sources) and traffic) else None
 
 
-def smooth_traffic_record():
-    """DRAM bytes per launch of the z-march smoothing kernel from the committed
-    ncu summary (profiles/smooth_headneck256.md), if it was taken on the
-    current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "smooth_headneck256.md")
-    if not os.path.exists(path):
-        return None
-    sha, traffic = None, None
-    for line in open(path):
-        if line.startswith("- smoothing kernel sources sha1"):
-            sha = line.split(":", 1)[1].strip()
-        if line.startswith("- dram bytes per launch (full size):"):
-            traffic = float(line.split(":", 1)[1].strip())
-    return traffic if (sha == sources_sha1(("kernels_smooth.cu", "tma.cuh")) and traffic) else None
+FORCE_SOURCES = ("kernels_force.cu", "warp_corners.cuh")
+SMOOTH_SOURCES = ("kernels_smooth.cu", "tma.cuh")
 
 
 def sources_sha1(files):
@@ -263,21 +295,21 @@ def sources_sha1(files):
     return h.hexdigest()
 
 
-def force_sources_sha1():
-    """sha1 of the force kernels' sources (kernels_force.cu, then warp_corners.cuh)."""
-    return sources_sha1(("kernels_force.cu", "warp_corners.cuh"))
-
-
 # --------------------------------------------------------------------------- #
 def run_reference(args):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload
+    per step (rank 0 only; the GPU, where present, only builds the inputs)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import phantom
-    case = phantom.make_case(WORKLOAD["name"])
+    import torch
+    WORKLOAD.update(WORKLOADS[getattr(args, "workload", "pelvis512")])
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    dc, host = build_case(torch, WORKLOAD["name"], 0, dev)
+    del dc
     times, vi = [], 0
     for i in range(args.warmup + args.steps):
-        vi, dt = time_oracle_sample(case)
+        vi, dt = time_oracle_sample(host)
         if i >= args.warmup:
             times.append(dt)
     value = vi * len(times) / sum(times)
@@ -286,12 +318,70 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(case, 1),
+            "config": workload_config(host, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample_desc(case)},
+                             "sample": sample_desc(host)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_registrations(torch, cg, ctx, dc, kw, steps, warmup, flush, stream, barrier=lambda: None,
+                       profile_levels=None):
+    """Register the device-resident case `steps` times after `warmup` untimed
+    runs, L2 flushed before each; CUDA events on the context stream around
+    each registration.  Returns (per-step ms, kernels launched, clock summary,
+    per-kernel profile of the timed steps)."""
+    S, M = dc["S"], dc["M"]
+    for _ in range(warmup):
+        ctx.register(S, M, dc["SM"], dc["MM"], dvf_out=dc["dvf"], **kw)
+    torch.cuda.synchronize()
+    if profile_levels is not None:
+        ctx.profile([cg.CGDIR_K_FORCE, cg.CGDIR_K_SMOOTH_U], levels=profile_levels)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = cg.launch_count()
+    with ClockSampler(gpu_uuid(torch, stream.device)) as clk:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ctx.register(S, M, dc["SM"], dc["MM"], dvf_out=dc["dvf"], **kw)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = cg.launch_count() - launches0
+    barrier()
+    prof = None
+    if profile_levels is not None:
+        prof = ctx.profile_read()
+        ctx.profile([])
+    return [a.elapsed_time(b) for a, b in ev], launches, clk.summary(), prof
+
+
+def device_case(torch, dc, host, img_t, dev):
+    """Device inputs of one registration in the storage type, and its DVF buffer."""
+    return {"S": dc.static.to(img_t), "M": dc.moving.to(img_t),
+            "SM": list(dc.static_masks.unbind(0)), "MM": list(dc.moving_masks.unbind(0)),
+            "dvf": torch.empty((3,) + host.shape, dtype=torch.float32, device=dev)}
+
+
+def secondary_headneck(torch, cg, dev, flush, stream, steps, warmup):
+    """The 256 x 256 x 96 head-and-neck case (FP32), autotuned, timed like
+    the headline workload: a secondary key of the line."""
+    import numpy as np
+    import phantom
+    wl = WORKLOADS["headneck256"]
+    dc, host = build_case(torch, wl["name"], 0, dev)
+    d = device_case(torch, dc, host, torch.float32, dev)
+    kw = dict(levels=wl["levels"], iters=wl["iters"], lam=host.lam, sign=host.signs,
+              stop_mode=cg.CGDIR_STOP_FIXED, storage_dtype=cg.CGDIR_F32)
+    with cg.Context(dev.index) as ctx:
+        ctx.autotune(host.shape, host.k, wl["levels"], storage_dtype=cg.CGDIR_F32)
+        ms, _, _, _ = time_registrations(torch, cg, ctx, d, kw, steps, warmup, flush, stream)
+    vi = phantom.voxel_iters(host.shape, wl["levels"], wl["iters"])
+    return {"value": vi * len(ms) / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "steps": steps, "config": workload_config(host, 1, "f32", wl)}
 
 
 def run_cgdir(args):
@@ -308,27 +398,15 @@ def run_cgdir(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     WORKLOAD.update(WORKLOADS[args.workload])
-    if args.workload == "headneck256":
-        case = phantom.make_case(WORKLOAD["name"], index=replica_case_index(rank))
-    else:                                     # built on the GPU, host copies for the oracle
-        dc = phantom.make_case_device(WORKLOAD["name"], index=replica_case_index(rank), device=dev)
-        dc.static, dc.moving = dc.static.cpu().numpy(), dc.moving.cpu().numpy()
-        dc.static_masks, dc.moving_masks = dc.static_masks.cpu().numpy(), dc.moving_masks.cpu().numpy()
-        dc.u_gt = dc.body = None
-        case = dc
-        torch.cuda.empty_cache()
+    dc, host = build_case(torch, WORKLOAD["name"], replica_case_index(rank), dev)
     L, iters = WORKLOAD["levels"], WORKLOAD["iters"]
-    vox_iters = phantom.voxel_iters(case.shape, L, iters)
-    N = int(np.prod(case.shape))
+    vox_iters = phantom.voxel_iters(host.shape, L, iters)
+    N = int(np.prod(host.shape))
     img_t = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.storage]
     img_code = {"f32": cg.CGDIR_F32, "f16": cg.CGDIR_F16, "bf16": cg.CGDIR_BF16}[args.storage]
-
-    S = torch.from_numpy(case.static).to(dev).to(img_t)
-    M = torch.from_numpy(case.moving).to(dev).to(img_t)
-    SM = [torch.from_numpy(m).to(dev) for m in case.static_masks]
-    MM = [torch.from_numpy(m).to(dev) for m in case.moving_masks]
-    dvf = torch.empty((3,) + case.shape, dtype=torch.float32, device=dev)
-    kw = dict(levels=L, iters=iters, lam=case.lam, sign=case.signs, stop_mode=cg.CGDIR_STOP_FIXED,
+    d = device_case(torch, dc, host, img_t, dev)
+    del dc
+    kw = dict(levels=L, iters=iters, lam=host.lam, sign=host.signs, stop_mode=cg.CGDIR_STOP_FIXED,
               storage_dtype=img_code)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
@@ -343,53 +421,35 @@ def run_cgdir(args):
             ctx.load_tuning(json.load(f))
         tuning = ctx.tuning()
     else:
-        tuning = ctx.autotune(case.shape, case.k, L, storage_dtype=img_code)
+        tuning = ctx.autotune(host.shape, host.k, L, storage_dtype=img_code)
     if args.tuning_out:
         with open(args.tuning_out, "w") as f:
             json.dump(tuning, f)
-    for _ in range(args.warmup):
-        ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
-    torch.cuda.synchronize()
 
-    # ---- timed region: device-resident inputs, CUDA events on the ctx stream
-    # the roofline's launches only: the force step and the smoothing of u at the finest level
-    ctx.profile([cg.CGDIR_K_FORCE, cg.CGDIR_K_SMOOTH_U], levels=[L - 1])
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    launches0 = cg.launch_count()
-    with ClockSampler(gpu_uuid(torch, dev)) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-    launches = cg.launch_count() - launches0
-    barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    # ---- timed region: device-resident inputs, CUDA events on the ctx stream;
+    # the roofline's launches are timed too: the force step and the smoothing
+    # of u at the finest level
+    step_ms, launches, clocks, prof = time_registrations(torch, cg, ctx, d, kw, args.steps, args.warmup, flush,
+                                                         stream, barrier, profile_levels=[L - 1])
     total_ms = sum(step_ms)
-    prof = ctx.profile_read()
-    ctx.profile([])
     max_total_ms = reduce_max(total_ms, dev)
     value = whole_job_value(world, vox_iters, args.steps, max_total_ms)
 
     # ---- one profiled step with every kernel class timed (breakdown only)
     ctx.profile(list(range(8)))
     flush.zero_()
-    ctx.register(S, M, SM, MM, dvf_out=dvf, **kw)
+    ctx.register(d["S"], d["M"], d["SM"], d["MM"], dvf_out=d["dvf"], **kw)
     breakdown = ctx.profile_read()
     ctx.profile([])
 
     # ---- end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        Sh = torch.from_numpy(case.static).to(img_t).pin_memory()
-        Mh = torch.from_numpy(case.moving).to(img_t).pin_memory()
-        SMh = [torch.from_numpy(m).pin_memory() for m in case.static_masks]
-        MMh = [torch.from_numpy(m).pin_memory() for m in case.moving_masks]
-        dvf_h = torch.empty((3,) + case.shape, dtype=torch.float32).pin_memory()
+        Sh = torch.from_numpy(host.static).to(img_t).pin_memory()
+        Mh = torch.from_numpy(host.moving).to(img_t).pin_memory()
+        SMh = [torch.from_numpy(m).pin_memory() for m in host.static_masks]
+        MMh = [torch.from_numpy(m).pin_memory() for m in host.moving_masks]
+        dvf_h = torch.empty((3,) + host.shape, dtype=torch.float32).pin_memory()
         ctx.register(Sh, Mh, SMh, MMh, dvf_out=dvf_h, **kw)      # warm the host path
         barrier()
         et = []
@@ -400,11 +460,12 @@ def run_cgdir(args):
             _, st = ctx.register(Sh, Mh, SMh, MMh, dvf_out=dvf_h, **kw)
             et.append(time.perf_counter() - t0)
         t_max = reduce_max(sum(et), dev)
-        h2d = 2 * N * S.element_size() + 2 * case.k * N
+        h2d = 2 * N * d["S"].element_size() + 2 * host.k * N
         d2h = 3 * N * 4 + L * (max(iters) + 1) * 8 + 4 * 8 * 4
         e2e = {"value": whole_job_value(world, vox_iters, args.steps, 1e3 * t_max), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": 1e3 * t_max / args.steps}
+        del Sh, Mh, SMh, MMh, dvf_h
 
     # ---- roofline of the dominant kernel (largest share of device time in the
     # launch list): the z-march Gaussian at the finest level, two launches per
@@ -412,7 +473,7 @@ def run_cgdir(args):
     # (its two passes) as a second entry
     peak, peak_src = measured_peaks()
     fine = {p["kernel"]: p for p in prof if p["level"] == L - 1 and p["launches"]}
-    fine_variant = next((t["smooth"] for t in tuning if tuple(t["shape"]) == tuple(case.shape)), None)
+    fine_variant = next((t["smooth"] for t in tuning if tuple(t["shape"]) == tuple(host.shape)), None)
     roofline, roofline_force = None, None
     if "smooth_u" in fine and fine_variant == "march":
         p = fine["smooth_u"]
@@ -422,7 +483,7 @@ def run_cgdir(args):
         roofline = {"bound": "hbm", "kernel": "k_smooth_tma (z-march Gaussian of u, finest level; the same kernel "
                                               "also smooths du there)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": smooth_traffic_record() if (args.workload, sigma_default(kw)) == ("headneck256", True)
+                    "traffic": traffic_record("smooth", args.workload, SMOOTH_SOURCES) if sigma_default(kw)
                     else None,
                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                     "launches": p["launches"], "peak_source": peak_src}
@@ -434,18 +495,28 @@ def run_cgdir(args):
         roofline_force = {"bound": "hbm", "kernel": "force step = k_warp_pass + k_force_pass2 (finest level, "
                                                     "contour terms on)",
                           "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                          "traffic": force_traffic_record(case) if (args.workload, args.storage) == ("headneck256", "f32")
-                          else None,
+                          "traffic": traffic_record("force", args.workload, FORCE_SOURCES)
+                          if args.storage == "f32" else None,
                           "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                           "launches": p["launches"], "peak_source": peak_src}
     if roofline is None:
         roofline = roofline_force
+    ctx.close()
+    del d
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        vi, dt = time_oracle_sample(case)
+        vi, dt = time_oracle_sample(host)
         cpu = {"value": vi / dt, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
-               "sample": sample_desc(case), "seconds": dt}
+               "sample": sample_desc(host), "seconds": dt}
+
+    secondary, batched = None, None
+    if world == 1 and not args.no_secondary:
+        secondary = secondary_headneck(torch, cg, dev, flush, stream, args.steps, args.warmup)
+        del flush
+        torch.cuda.empty_cache()
+        batched = batched_comparison(torch, cg, dev, args.batch_n, args.batch_passes, 1)
 
     if rank == 0:
         lat = sorted(step_ms)
@@ -453,12 +524,13 @@ def run_cgdir(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.storage == "f32" else f"{args.storage} images, f32 arithmetic",
-                "data": "synthetic", "config": workload_config(case, world, args.storage),
+                "data": "synthetic", "config": workload_config(host, world, args.storage),
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "per": "registration"},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
                 "roofline_force_step": roofline_force,
-                "cpu_baseline": cpu, "clocks": clk.summary(),
+                "cpu_baseline": cpu, "clocks": clocks,
+                "headneck256": secondary, "batched": batched,
                 "kernel_breakdown_ms": {f"{p['kernel']}@L{p['level']}": round(p["total_ms"], 4)
                                         for p in breakdown},
                 "tuning": [{"shape_zyx": list(t["shape"]), "smooth": t["smooth"],
@@ -467,7 +539,6 @@ def run_cgdir(args):
                             "untuned_smooth_ms": round(t["default_smooth_ms"], 4),
                             "untuned_force_ms": round(t["default_force_ms"], 4)} for t in tuning]}
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -529,65 +600,86 @@ def one_at_a_time(torch, cg, ctx, cases, stream):
     return [a.elapsed_time(b) for a, b in out]
 
 
-def run_batch(args):
+def batched_comparison(torch, cg, dev, n, passes, warmup):
+    """The uneven-size mix of n cases: plain FP32 registrations one at a time
+    against all n in one batched graph launch (FP16 images, and FP32 for
+    comparison), on the same GPU and context.  voxel-iter/s of each, the
+    multiple over plain FP32, and per-registration latency: for plain runs
+    each registration's own CUDA-event time, for a batch the pass time (every
+    case completes with the batch)."""
     import numpy as np
-    import torch
-
-    import paper_1301_0970_gb300 as cg
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    cases = build_mix(torch, dev, args.batch_n)
+    t_build = time.perf_counter()
+    cases = build_mix(torch, dev, n)
+    t_build = time.perf_counter() - t_build
     total_vi = sum(c["vi"] for c in cases)
     stream = torch.cuda.current_stream(dev)
     res = {}
-    with cg.Context(0) as ctx:
+    with cg.Context(dev.index) as ctx:
         ctx.set_autotune(True)        # each new level shape is tuned at its first registration
         # plain FP32, one at a time (warm-up passes capture every shape's graph)
-        for _ in range(max(args.warmup, 2)):
+        for _ in range(max(warmup, 1)):
             one_at_a_time(torch, cg, ctx, cases, stream)
         per, tot = [], []
-        for _ in range(args.steps):
-            t = one_at_a_time(torch, cg, ctx, cases, stream)
-            per += t
-            tot.append(sum(t))
-        res["plain"] = {"value": total_vi * len(tot) / (sum(tot) / 1e3), "ms_per_pass": float(np.mean(tot)),
-                        "p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))}
+        with ClockSampler(gpu_uuid(torch, dev)) as clk:
+            for _ in range(passes):
+                t = one_at_a_time(torch, cg, ctx, cases, stream)
+                per += t
+                tot.append(sum(t))
+        res["plain_f32_one_at_a_time"] = {
+            "value": total_vi * len(tot) / (sum(tot) / 1e3), "unit": UNIT, "ms_per_pass": float(np.mean(tot)),
+            "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                           "per": "registration", "samples": len(per)},
+            "clocks": clk.summary()}
         # batched: every case in one graph launch
-        for half in (False, True):
+        for half in (True, False):
             outs = [torch.empty((3,) + c["shape"], dtype=torch.float32, device=dev) for c in cases]
             reqs = [mix_request(cg, c, half, o) for c, o in zip(cases, outs)]
-            for _ in range(args.warmup):
+            for _ in range(max(warmup, 1)):
                 ctx.register_batch(reqs)
             torch.cuda.synchronize()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
+                  for _ in range(passes)]
             l0 = cg.launch_count()
             with ClockSampler(gpu_uuid(torch, dev)) as clk:
-                for i in range(args.steps):
+                for i in range(passes):
                     ev[i][0].record(stream)
                     ctx.register_batch(reqs)
                     ev[i][1].record(stream)
                 torch.cuda.synchronize()
             launches = cg.launch_count() - l0
             ms = [a.elapsed_time(b) for a, b in ev]
-            res["f16" if half else "f32"] = {"value": total_vi * len(ms) / (sum(ms) / 1e3),
-                                             "ms_per_pass": float(np.mean(ms)), "launches": launches,
-                                             "clocks": clk.summary()}
+            res["batch_f16" if half else "batch_f32"] = {
+                "value": total_vi * len(ms) / (sum(ms) / 1e3), "unit": UNIT, "ms_per_pass": float(np.mean(ms)),
+                "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                               "per": "registration (every case of a batch completes with the batch)"},
+                "gpu_launches_per_pass": int(launches // max(passes, 1)), "clocks": clk.summary()}
             del outs, reqs
-    b16 = res["f16"]
+    plain = res["plain_f32_one_at_a_time"]["value"]
+    res["multiple_batch_f16_over_plain_f32"] = res["batch_f16"]["value"] / plain
+    res["multiple_batch_f32_over_plain_f32"] = res["batch_f32"]["value"] / plain
+    res["config"] = mix_config(cases)
+    res["passes"] = passes
+    res["build_s"] = round(t_build, 1)
+    del cases
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batch(args):
+    import torch
+
+    import paper_1301_0970_gb300 as cg
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    res = batched_comparison(torch, cg, dev, args.batch_n, args.steps, args.warmup)
+    b16 = res["batch_f16"]
     line = {"metric": METRIC, "value": b16["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": b16["ms_per_pass"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16 images, f32 arithmetic",
-            "data": "synthetic", "config": mix_config(cases),
-            "latency_ms": {"p50": b16["ms_per_pass"], "p99": b16["ms_per_pass"],
-                           "per": "registration (every case of a batch completes with the batch)"},
-            "gpu_launches": int(b16["launches"]), "clocks": b16["clocks"],
-            "batched_f32": {"value": res["f32"]["value"], "ms_per_pass": res["f32"]["ms_per_pass"]},
-            "plain_f32_one_at_a_time": {"value": res["plain"]["value"], "ms_per_pass": res["plain"]["ms_per_pass"],
-                                        "latency_ms": {"p50": res["plain"]["p50"], "p99": res["plain"]["p99"],
-                                                       "per": "registration"}},
-            "speedup_vs_plain_f32": b16["value"] / res["plain"]["value"]}
+            "data": "synthetic", "config": res["config"], "latency_ms": b16["latency_ms"],
+            "gpu_launches": int(b16["gpu_launches_per_pass"] * args.steps), "clocks": b16["clocks"],
+            "batched": res}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -709,13 +801,17 @@ def run_only_kernel(args):
     import phantom
 
     dev = torch.device("cuda", 0)
+    WORKLOAD.update(WORKLOADS[args.workload])
     shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
-    case = phantom.make_case(WORKLOAD["name"], shape=shape)
-    bits = lambda m: torch.from_numpy(
-        np.bitwise_or.reduce([(x.astype(np.uint8) << j) for j, x in enumerate(m)], axis=0)).to(dev)
-    I0, T0 = torch.from_numpy(case.moving).to(dev), torch.from_numpy(case.static).to(dev)
-    mb, sb = bits(case.moving_masks), bits(case.static_masks)
-    u = torch.from_numpy(0.5 * case.u_gt).to(dev)
+    case = phantom.make_case_device(WORKLOAD["name"], shape=shape, device=dev)
+    pk = torch.zeros(case.shape, dtype=torch.uint8, device=dev)
+    mb, sb = pk.clone(), pk.clone()
+    for j in range(case.k):
+        mb |= (case.moving_masks[j] != 0).to(torch.uint8) << j
+        sb |= (case.static_masks[j] != 0).to(torch.uint8) << j
+    I0, T0 = case.moving, case.static
+    u = (0.5 * case.u_gt).contiguous()
+    del pk
     du = torch.empty_like(u)
     dus = (0.1 * u).contiguous()
     n = int(np.prod(case.shape))
