@@ -180,7 +180,11 @@ cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, i
 // fused iteration schedule (3-D tiles of all three components with the
 // composite update fused into the du pass and the next warp into the u
 // pass; a standalone smoothing takes the tile kernel), or chosen by size.
-enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2, SMOOTH_SPLIT = 3, SMOOTH_FUSED = 4 };
+// SMOOTH_MARCH takes the wide-tile z-march (64 x 16 tiles, nx % 8 == 0, R <= 4)
+// where it applies, else the 32 x 16 one; SMOOTH_MARCH_NARROW always the
+// 32 x 16 one (same bits; a context setting for comparisons, never tuned).
+enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2, SMOOTH_SPLIT = 3, SMOOTH_FUSED = 4,
+       SMOOTH_MARCH_NARROW = 5 };
 int smooth_auto_variant(int nx, int ny, int nz);
 // Kernel choice for one smoothing launch: variant and (z-march) z chunk, 0 = default.
 struct SmoothChoice {

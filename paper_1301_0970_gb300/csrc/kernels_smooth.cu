@@ -367,6 +367,196 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
     }
 }
 
+// ---- wide-tile z-march (one component per CTA, nx % 8 == 0, R <= 4) -----
+// The same passes and the same order of operations as k_smooth_tma (so the
+// same bits), on a 64 x 16 output tile with less work per output:
+//  * per input plane one TMA box (x from x0 - 4, 72 wide; y from y0 - R)
+//    lands in a ring of stages; the ring and the x-pass buffers are indexed
+//    from the kernel's own shared array, so every access is a shared-memory
+//    load or store;
+//  * x pass: a task is 8 adjacent outputs of one box row (four 16-byte
+//    loads, 56 FMAs, half of them paired); the clamp at the volume's x
+//    borders is a select on the loaded values (the box is zero-filled
+//    there), the clamp in y a remapped row, in z a clamped plane;
+//  * y pass: a thread takes a column pair and two rows: 8-byte loads of the
+//    pair, paired FMAs only;
+//  * z pass: the last 2R+1 y-pass results of those four outputs stay in
+//    registers (slots fixed at compile time by unrolling the plane loop
+//    2R+1 times), paired FMAs; 8-byte stores.
+// One barrier per plane (the x-pass buffer is double-buffered).
+// Box rows are 76 floats wide (x0 - 4 .. x0 + 71; the last 4 columns are
+// not used) and so are the x-pass buffer's rows: 19 16-byte units, so the
+// x-pass tasks below (task q: box row q % BY, column group q / BY) hit
+// distinct bank groups in every quarter-warp, for their 16-byte loads and
+// stores alike (unit 19 row + 2 group = 3 q mod 8 when BY = 6 mod 8).
+constexpr int WX = 64, WY = 16, WML = 4, WBX = 76;
+
+template <int R>
+struct WideGeom {
+    static constexpr int BY = WY + 2 * R;                       // box rows
+    static constexpr int ST = 8;                                // pipeline stages
+    static constexpr int STAGE = (BY * WBX + 31) / 32 * 32;     // floats per stage (128-byte multiple)
+    static constexpr int XB = BY * WBX;                         // floats per x-pass buffer
+    static constexpr int NTASK = BY * (WX / 8);                 // x-pass tasks per plane
+    static constexpr size_t bytes() {
+        return sizeof(float) * ((size_t)ST * STAGE + 2 * XB) + ST * sizeof(uint64_t) + 128;
+    }
+};
+
+template <int R>
+__global__ void __launch_bounds__(NT, 2) k_smooth_wide(const __grid_constant__ CUtensorMap tin,
+                                                       float *__restrict__ out, Taps taps, int nx, int ny,
+                                                       int nz, int zchunk, const int *stop_flag, int *err) {
+    if (stop_flag && *stop_flag) return;
+    using G = WideGeom<R>;
+    constexpr int K = 2 * R + 1, BY = G::BY, ST = G::ST, STAGE = G::STAGE, XB = G::XB;
+    static_assert(R >= 1 && R <= 4, "8-output x tasks read 16 loaded values");
+    extern __shared__ __align__(128) float wsm[];
+    // 128-byte aligned base for the TMA stages, still a shared-memory pointer
+    const int pad = (int)(((128u - (smem_u32(wsm) & 127u)) & 127u) >> 2);
+    float *stage0 = wsm + pad;                                   // [ST][STAGE]
+    float *xbuf = stage0 + ST * STAGE;                           // [2][BY][WX]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(xbuf + 2 * XB);
+
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int x0 = blockIdx.x * WX, y0 = blockIdx.y * WY;
+    const int nchunks = (nz + zchunk - 1) / zchunk;
+    const int chunk = (int)blockIdx.z % nchunks, comp = (int)blockIdx.z / nchunks;
+    const int zb = chunk * zchunk, ze = min(zb + zchunk, nz);
+    const int P = (ze - zb) + 2 * R;
+    const uint32_t tx_bytes = (uint32_t)(BY * WBX * sizeof(float));
+
+    float2 w2[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w2[j] = make_float2(taps.w[j], taps.w[j]);
+
+    // x-pass task of this thread (fixed for every plane): box row and column group
+    const bool xtask = tid < G::NTASK;
+    const int xrow = tid % BY, xg = tid / BY;
+    const int srow = clampi(y0 - R + xrow, 0, ny - 1) - (y0 - R);    // clamped source row in the box
+    const int xsrc = srow * WBX + 8 * xg;                            // first loaded float
+    const int xdst = xrow * WBX + 8 * xg;
+    const bool pleft = x0 == 0 && xg == 0;                            // taps left of x = 0
+    const bool pright = x0 + 8 * xg + 8 == nx;                        // taps right of x = nx - 1
+    const bool xedge = x0 == 0 || x0 + WX >= nx;                      // the same for the whole CTA
+    // y / z pass: column pair (x, x + 1) and rows (y, y + 1) of this thread
+    const int yc = 2 * (tid & 31), yr = 2 * (tid >> 5);
+    const int gx = x0 + yc, gy = y0 + yr;
+    const bool act0 = gx < nx && gy < ny, act1 = gx < nx && gy + 1 < ny;
+    const size_t nxy = (size_t)nx * ny;
+    float *optr = out + (size_t)comp * nxy * nz + (size_t)zb * nxy + (size_t)gy * nx + gx;
+
+    auto issue = [&](int q) {
+        const int sidx = q % ST;
+        const int z = clampi(zb - R + q, 0, nz - 1);
+        mbar_expect_tx(&bar[sidx], tx_bytes);
+        tma_load_4d(stage0 + sidx * STAGE, &tin, x0 - WML, y0 - R, z, comp, &bar[sidx]);
+    };
+    if (tid == 0) {
+        for (int q = 0; q < ST; ++q) mbar_init(&bar[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int q = 0; q < ST && q < P; ++q) issue(q);
+
+    float2 ring[2][K];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int j = 0; j < K; ++j) ring[h][j] = make_float2(0.f, 0.f);
+
+    int tw = -1;                        // plane whose wait ran out (-1: none)
+    int sidx = 0, xo = 0;               // stage of plane t, x-pass buffer offset
+    uint32_t par = 0;                   // phase parity of that stage
+    for (int t0 = 0; t0 < P && tw < 0; t0 += K) {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const int t = t0 + r;
+            if (t >= P) break;
+            bool ok = true;
+            if (xtask) {
+                ok = mbar_wait_bounded(&bar[sidx], par);
+                const float *src = stage0 + sidx * STAGE + xsrc;
+                float v[16];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const float4 f = *reinterpret_cast<const float4 *>(src + 4 * h);
+                    v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
+                }
+                if (xedge) {                   // CTAs at an x border of the volume only
+#pragma unroll
+                    for (int k = WML - R; k < WML; ++k) v[k] = pleft ? v[WML] : v[k];
+#pragma unroll
+                    for (int k = 8 + WML; k < 8 + WML + R; ++k) v[k] = pright ? v[7 + WML] : v[k];
+                }
+                float2 o[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) o[m] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    constexpr int B = WML - R;
+                    if ((B + j) % 2 == 0) {            // operand pairs register-aligned
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            o[m] = __ffma2_rn(w2[j], make_float2(v[B + j + 2 * m], v[B + j + 2 * m + 1]), o[m]);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            o[m].x = fmaf(w2[j].x, v[B + j + 2 * m], o[m].x);
+                            o[m].y = fmaf(w2[j].x, v[B + j + 2 * m + 1], o[m].y);
+                        }
+                    }
+                }
+                float *dst = xbuf + xo + xdst;
+                *reinterpret_cast<float4 *>(dst) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+            }
+            if (__syncthreads_or(!ok)) { tw = t; break; }
+            if (tid == 0 && t + ST < P) {      // the stage just consumed takes plane t + ST
+                fence_proxy_async();
+                issue(t + ST);
+            }
+            if (++sidx == ST) { sidx = 0; par ^= 1u; }
+            // y pass into this plane's ring slot, z pass for plane t - 2R
+            const float *col = xbuf + xo + yr * WBX + yc;
+            float2 yin[K + 1];
+#pragma unroll
+            for (int j = 0; j <= K; ++j) yin[j] = *reinterpret_cast<const float2 *>(col + j * WBX);
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                a0 = __ffma2_rn(w2[j], yin[j], a0);
+                a1 = __ffma2_rn(w2[j], yin[j + 1], a1);
+            }
+            ring[0][r] = a0;
+            ring[1][r] = a1;
+            xo ^= XB;
+            if (t >= 2 * R) {
+                float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    o0 = __ffma2_rn(w2[j], ring[0][(r + 1 + j) % K], o0);
+                    o1 = __ffma2_rn(w2[j], ring[1][(r + 1 + j) % K], o1);
+                }
+                if (act0) *reinterpret_cast<float2 *>(optr) = o0;
+                if (act1) *reinterpret_cast<float2 *>(optr + nx) = o1;
+                optr += nxy;
+            }
+        }
+    }
+    if (tw >= 0) {
+        // a wait ran out: record it, drain the loads still in flight (planes
+        // tw .. tw + ST - 1 were issued; bounded waits), leave
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int q = tw; q < min(tw + ST, P); ++q)
+                mbar_wait_bounded(&bar[q % ST], (uint32_t)((q / ST) & 1));
+        }
+        __syncthreads();
+    }
+}
+
 // Composite update u_new = du + u(x + du) (trilinear, clamped) or u + du,
 // one voxel per thread along x-y tiles marching a few planes in z.
 __global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict__ u, const float *__restrict__ du,
@@ -723,6 +913,46 @@ static cudaError_t smooth_tma_r(const float *in, const float *ucomp, int mode, f
     return cudaGetLastError();
 }
 
+// z chunk of the wide-tile z-march: about four waves of 3 resident CTAs per SM.
+static int wide_default_zchunk(int nx, int ny, int nz, int ncomp) {
+    return pick_zchunk(nz, (long)((nx + WX - 1) / WX) * ((ny + WY - 1) / WY) * ncomp, 3, 4);
+}
+
+// The wide-tile z-march for one component per CTA (nx % 8 == 0, R <= 4).
+template <int R>
+static cudaError_t smooth_wide_r(const float *in, float *out, int ncomp, const Taps &t, int nx, int ny, int nz,
+                                 const int *stop_flag, int *err, cudaStream_t s, bool *launched, int zc_override) {
+    using G = WideGeom<R>;
+    CUtensorMap m;
+    const uint64_t dims[4] = {(uint64_t)nx, (uint64_t)ny, (uint64_t)nz, (uint64_t)ncomp};
+    const uint32_t box[4] = {(uint32_t)WBX, (uint32_t)G::BY, 1u, 1u};
+    *launched = false;
+    if (!encode_tensor_map(&m, in, 4, dims, box, 4)) return cudaSuccess;
+    const int zc = zc_override > 0 ? std::min(zc_override, nz) : wide_default_zchunk(nx, ny, nz, ncomp);
+    const int nchunks = (nz + zc - 1) / zc;
+    dim3 grid((nx + WX - 1) / WX, (ny + WY - 1) / WY, nchunks * ncomp), block(TX, TY);
+    const size_t smem = G::bytes();
+    cudaError_t e = ensure_smem((const void *)k_smooth_wide<R>, smem);
+    if (e != cudaSuccess) return e;
+    k_smooth_wide<R><<<grid, block, smem, s>>>(m, out, t, nx, ny, nz, zc, stop_flag, err);
+    *launched = true;
+    note_launch();
+    return cudaGetLastError();
+}
+
+static cudaError_t smooth_wide(const float *in, float *out, int ncomp, const Taps &t, int nx, int ny, int nz,
+                               const int *stop_flag, int *err, cudaStream_t s, bool *launched, int zc = 0) {
+    *launched = false;
+    if (nx % 8 != 0) return cudaSuccess;
+    switch (t.r) {
+        case 1: return smooth_wide_r<1>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 2: return smooth_wide_r<2>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 3: return smooth_wide_r<3>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 4: return smooth_wide_r<4>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        default: return cudaSuccess;
+    }
+}
+
 template <int NC, bool COMPOSE>
 static cudaError_t smooth_tma(const float *in, const float *ucomp, int mode, float *out, int ncomp,
                               const Taps &t, int nx, int ny, int nz, const int *stop_flag, int *err,
@@ -824,6 +1054,7 @@ static cudaError_t smooth_split(const float *in, const float *u, int mode, bool 
 }
 
 int smooth_default_zchunk(int nx, int ny, int nz, int ncomp) {
+    if (nx % 8 == 0) return wide_default_zchunk(nx, ny, nz, ncomp);
     return smooth_zchunk(nx, ny, nz, SY, ncomp, 4);
 }
 
@@ -846,6 +1077,10 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
         if (variant == SMOOTH_SPLIT && scratch != nullptr && scratch != in && scratch != out)
             return smooth_split(in, nullptr, 0, false, ncomp, t, nx, ny, nz, out, scratch, ch.zchunk, stop_flag, s);
         bool launched = false;
+        if (variant != SMOOTH_MARCH_NARROW) {      // the wide-tile z-march where it applies
+            cudaError_t e = smooth_wide(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched, ch.zchunk);
+            if (e != cudaSuccess || launched) return e;
+        }
         cudaError_t e =
             smooth_tma<1, false>(in, nullptr, 0, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched, ch.zchunk);
         if (e != cudaSuccess || launched) return e;

@@ -330,6 +330,7 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     c->smooth_variant = !sv ? SMOOTH_AUTO
                             : std::strcmp(sv, "tile") == 0 ? SMOOTH_TILE
                             : std::strcmp(sv, "march") == 0 ? SMOOTH_MARCH
+                            : std::strcmp(sv, "march32") == 0 ? SMOOTH_MARCH_NARROW
                             : std::strcmp(sv, "split") == 0 ? SMOOTH_SPLIT
                             : std::strcmp(sv, "fused") == 0 ? SMOOTH_FUSED : SMOOTH_AUTO;
     const char *gr = std::getenv("CGDIR_GRAPHS");
