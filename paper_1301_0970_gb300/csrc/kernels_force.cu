@@ -470,12 +470,26 @@ __device__ __forceinline__ void force_voxel(const ForceArgs &a, const ContourTab
     dux = __fmul_rn(v, nxv); duy = __fmul_rn(v, nyv); duz = __fmul_rn(v, nzv);
 }
 
-// Loads of one plane of pass 2 for one thread's column.
+// Loads of one plane of pass 2 for one thread's column.  T0 stays raw (its
+// bits) until the voxel's arithmetic: a conversion of a 16-bit value at the
+// load would wait for the load in the prefetch.
 template <bool CONTOUR, typename IT>
 struct PlaneLoads {
-    float wp, wxm, wxp, wym, wyp, t;
+    float wp, wxm, wxp, wym, wyp;
+    unsigned t;
     unsigned sp, sxm, sxp, sym, syp, sb, ur;
 };
+
+// T0 of a voxel from its raw bits (plane loads), and of a voxel pair.
+template <typename IT>
+__device__ __forceinline__ float t_of(unsigned raw) { return from_raw16<IT>(raw); }
+template <>
+__device__ __forceinline__ float t_of<float>(unsigned raw) { return __uint_as_float(raw); }
+template <typename IT>
+__device__ __forceinline__ unsigned t_raw(const void *T0, int i) {
+    return sizeof(IT) == 2 ? (unsigned)__ldg(static_cast<const unsigned short *>(T0) + i)
+                           : __float_as_uint(__ldg(static_cast<const float *>(T0) + i));
+}
 
 // Issue every load of plane z (centre index ic) at once: one memory
 // latency per plane, hidden behind the previous plane's arithmetic.
@@ -486,7 +500,7 @@ __device__ __forceinline__ void plane_load(const ForceArgs &a, int ic, int ip, i
     L.wp = __ldg(W + ip);
     L.wxm = __ldg(W + ic + oxm); L.wxp = __ldg(W + ic + oxp);
     L.wym = __ldg(W + ic + oym); L.wyp = __ldg(W + ic + oyp);
-    L.t = ld_img<IT>(static_cast<const IT *>(a.T0) + ic);
+    L.t = t_raw<IT>(a.T0, ic);
     L.ur = a.uroi ? __ldg(a.uroi + ic) : 1u;
     if (CONTOUR) {
         const uint16_t *__restrict__ S = a.wstate;
@@ -497,7 +511,7 @@ __device__ __forceinline__ void plane_load(const ForceArgs &a, int ic, int ip, i
     }
 }
 
-template <bool CONTOUR, typename IT>
+template <bool CONTOUR, typename IT, bool MAXDU>
 __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
     if (a.stop_flag && *a.stop_flag) return;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
             const unsigned Sp = CONTOUR ? cur.sp : 0u;
             if (a.warped) a.warped[ic] = Wc;
             float dux, duy, duz, r0;
-            force_voxel<CONTOUR>(a, tab, N, Wc, cur.wxm, cur.wxp, cur.wym, cur.wyp, Wm, Wp, cur.t, Sc, cur.sxm,
+            force_voxel<CONTOUR>(a, tab, N, Wc, cur.wxm, cur.wxp, cur.wym, cur.wyp, Wm, Wp, t_of<IT>(cur.t), Sc, cur.sxm,
                                  cur.sxp, cur.sym, cur.syp, Sm, Sp, CONTOUR ? cur.sb : 0u, ic, ic + oxm, ic + oxp,
                                  ic + oym, ic + oyp, im, ip, dux, duy, duz, r0);
             du[ic] = dux;
@@ -544,7 +558,7 @@ __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
                 ssd = fmaf(r0, r0, ssd);
                 cnt += 1;
             }
-            mx = fmaxf(mx, dux * dux + duy * duy + duz * duz);
+            if (MAXDU) mx = fmaxf(mx, dux * dux + duy * duy + duz * duz);
             Wm = Wc; Wc = Wp; im = ic;
             if (CONTOUR) { Sm = Sc; Sc = Sp; }
             ++z;
@@ -595,11 +609,24 @@ struct ImgPair<__nv_bfloat16> {
 struct PlaneLoads2 {
     float2 wp, wym, wyp;       // I0~ pairs at z+1, y-1, y+1
     float wxm, wxp;            // I0~ at x-1 and x+2 (clamped)
-    float t0, t1;              // T0 pair
+    float t0, t1;              // T0 pair (float images)
+    unsigned t16;              // T0 pair, raw (16-bit images; converted at use)
     unsigned sp, sym, syp;     // corner-bit word pairs (low half: x)
     unsigned sxm, sxp;         // corner-bit words at x-1 and x+2
     unsigned sb, ur;           // static bits / UROI byte pairs
 };
+
+// The T0 pair of a plane load as floats.
+template <typename IT>
+__device__ __forceinline__ void t_pair(const PlaneLoads2 &L, float &t0, float &t1) {
+    t0 = from_raw16<IT>(L.t16 & 0xffffu);
+    t1 = from_raw16<IT>(L.t16 >> 16);
+}
+template <>
+__device__ __forceinline__ void t_pair<float>(const PlaneLoads2 &L, float &t0, float &t1) {
+    t0 = L.t0;
+    t1 = L.t1;
+}
 
 template <bool CONTOUR, typename IT>
 __device__ __forceinline__ void plane_load2(const ForceArgs &a, int ic, int ip, int oxm, int oxp, int oym, int oyp,
@@ -610,7 +637,13 @@ __device__ __forceinline__ void plane_load2(const ForceArgs &a, int ic, int ip, 
     L.wyp = __ldg(reinterpret_cast<const float2 *>(W + ic + oyp));
     L.wxm = __ldg(W + ic + oxm);
     L.wxp = __ldg(W + ic + oxp);
-    ImgPair<IT>::ld(static_cast<const IT *>(a.T0) + ic, L.t0, L.t1);
+    if (sizeof(IT) == 2) {
+        L.t16 = __ldg(reinterpret_cast<const unsigned *>(static_cast<const IT *>(a.T0) + ic));
+        L.t0 = L.t1 = 0.f;
+    } else {
+        ImgPair<float>::ld(static_cast<const float *>(a.T0) + ic, L.t0, L.t1);
+        L.t16 = 0u;
+    }
     L.ur = a.uroi ? (unsigned)__ldg(reinterpret_cast<const unsigned short *>(a.uroi + ic)) : 0x0101u;
     if (CONTOUR) {
         const uint16_t *__restrict__ S = a.wstate;
@@ -625,7 +658,7 @@ __device__ __forceinline__ void plane_load2(const ForceArgs &a, int ic, int ip, 
     }
 }
 
-template <bool CONTOUR, typename IT>
+template <bool CONTOUR, typename IT, bool MAXDU>
 __global__ void __launch_bounds__(NT, 2) k_force_pass2(ForceArgs a, int zchunk) {
     if (a.stop_flag && *a.stop_flag) return;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -662,12 +695,13 @@ __global__ void __launch_bounds__(NT, 2) k_force_pass2(ForceArgs a, int zchunk) 
                 plane_load2<CONTOUR, IT>(a, ic + nxy, z + 1 < nz - 1 ? ic + 2 * nxy : ic + nxy, oxm, oxp, oym, oyp,
                                          nxt);
             if (a.warped) { a.warped[ic] = Wc.x; a.warped[ic + 1] = Wc.y; }
-            float d0x, d0y, d0z, r00, d1x, d1y, d1z, r01;
-            force_voxel<CONTOUR>(a, tab, N, Wc.x, cur.wxm, Wc.y, cur.wym.x, cur.wyp.x, Wm.x, cur.wp.x, cur.t0,
+            float d0x, d0y, d0z, r00, d1x, d1y, d1z, r01, tv0, tv1;
+            t_pair<IT>(cur, tv0, tv1);
+            force_voxel<CONTOUR>(a, tab, N, Wc.x, cur.wxm, Wc.y, cur.wym.x, cur.wyp.x, Wm.x, cur.wp.x, tv0,
                                  Sc & 0xffffu, cur.sxm, Sc >> 16, cur.sym & 0xffffu, cur.syp & 0xffffu,
                                  Sm & 0xffffu, cur.sp & 0xffffu, cur.sb & 0xffu, ic, ic + oxm, ic + 1, ic + oym,
                                  ic + oyp, im, ip, d0x, d0y, d0z, r00);
-            force_voxel<CONTOUR>(a, tab, N, Wc.y, Wc.x, cur.wxp, cur.wym.y, cur.wyp.y, Wm.y, cur.wp.y, cur.t1,
+            force_voxel<CONTOUR>(a, tab, N, Wc.y, Wc.x, cur.wxp, cur.wym.y, cur.wyp.y, Wm.y, cur.wp.y, tv1,
                                  Sc >> 16, Sc & 0xffffu, cur.sxp, cur.sym >> 16, cur.syp >> 16, Sm >> 16,
                                  cur.sp >> 16, (cur.sb >> 8) & 0xffu, ic + 1, ic, ic + oxp, ic + 1 + oym,
                                  ic + 1 + oyp, im + 1, ip + 1, d1x, d1y, d1z, r01);
@@ -676,7 +710,7 @@ __global__ void __launch_bounds__(NT, 2) k_force_pass2(ForceArgs a, int zchunk) 
             *reinterpret_cast<float2 *>(du + N + N + ic) = make_float2(d0z, d1z);
             if (cur.ur & 0xffu) { ssd = fmaf(r00, r00, ssd); cnt += 1; }
             if (cur.ur >> 8) { ssd = fmaf(r01, r01, ssd); cnt += 1; }
-            mx = fmaxf(mx, fmaxf(d0x * d0x + d0y * d0y + d0z * d0z, d1x * d1x + d1y * d1y + d1z * d1z));
+            if (MAXDU) mx = fmaxf(mx, fmaxf(d0x * d0x + d0y * d0y + d0z * d0z, d1x * d1x + d1y * d1y + d1z * d1z));
             Wm = Wc; Wc = cur.wp; im = ic;
             Sm = Sc; Sc = cur.sp;
             ++z;
@@ -1270,15 +1304,22 @@ static cudaError_t launch_force_t(const ForceArgs &a, int zchunk, dim3 grid, dim
         const bool paired = a.nx % 2 == 0 && !a.single_voxel;
         dim3 g2 = paired ? dim3((a.nx / 2 + TX - 1) / TX, grid.y, grid.z) : grid;
         const bool warp = !a.skip_warp;
+        // max |du| is reported by the primitive only (a registration's fused
+        // reduction keeps the RMS-ID sums alone)
+        const bool maxdu = a.partial != nullptr && (a.fin.done == nullptr || a.fin.stats_out != nullptr);
+#define CGDIR_PASS2(C, M)                                                        \
+    do {                                                                         \
+        if (paired) k_force_pass2<C, IT, M><<<g2, block, 0, s>>>(a, zchunk);     \
+        else k_force_pass<C, IT, M><<<grid, block, 0, s>>>(a, zchunk);           \
+    } while (0)
         if (contour) {
             if (warp) k_warp_pass<true, IT><<<g, block, 0, s>>>(a, zc);
-            if (paired) k_force_pass2<true, IT><<<g2, block, 0, s>>>(a, zchunk);
-            else k_force_pass<true, IT><<<grid, block, 0, s>>>(a, zchunk);
+            if (maxdu) CGDIR_PASS2(true, true); else CGDIR_PASS2(true, false);
         } else {
             if (warp) k_warp_pass<false, IT><<<g, block, 0, s>>>(a, zc);
-            if (paired) k_force_pass2<false, IT><<<g2, block, 0, s>>>(a, zchunk);
-            else k_force_pass<false, IT><<<grid, block, 0, s>>>(a, zchunk);
+            if (maxdu) CGDIR_PASS2(false, true); else CGDIR_PASS2(false, false);
         }
+#undef CGDIR_PASS2
         note_launch(warp ? 2 : 1);
         return cudaGetLastError();
     }

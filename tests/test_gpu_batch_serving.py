@@ -295,13 +295,14 @@ def test_cooperative_level_kernel_matches_per_iteration_kernels(stop):
         assert float((a - b).abs().max()) <= 1e-4
 
 
-@pytest.mark.parametrize("variant", ["split", "tile", "fused"])
+@pytest.mark.parametrize("variant", ["split", "tile", "fused", "march32"])
 def test_smoothing_variants_give_the_same_registration(variant):
     """Every smoothing variant (incl. the split kernels with the composite
-    update in the z pass, and the fused schedule: 3-D tiles of G(du) with
-    the update, 3-D tiles of G(u') with the next warp, the force's stencil
-    pass alone) gives the same DVF as the z-march, bit for bit."""
-    c = phantom.make_case("headneck256", shape=(24, 72, 76))
+    update in the z pass, the fused schedule: 3-D tiles of G(du) with the
+    update, 3-D tiles of G(u') with the next warp, the force's stencil pass
+    alone, and the 32 x 16 z-march) gives the same DVF as the wide-tile
+    z-march, bit for bit."""
+    c = phantom.make_case("headneck256", shape=(24, 72, 80))     # nx % 8 == 0: the wide-tile z-march
     kw = dict(levels=2, iters=[6, 5], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED, contour_level_mask=3)
     a_ctx = _ctx_with_env({"CGDIR_SMOOTH": "march"})
     b_ctx = _ctx_with_env({"CGDIR_SMOOTH": variant})
