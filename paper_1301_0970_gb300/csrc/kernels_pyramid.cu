@@ -18,9 +18,29 @@ unsigned flat_grid(size_t n, size_t cap = 152 * 16) {
     return (unsigned)(g ? g : 1);
 }
 
+// Row launches: a CTA covers RB consecutive x of one (y, z) row, so no
+// index is recovered by division (the grid-stride loops above divide a
+// 64-bit index per voxel).  Volumes with ny or nz above the grid limit keep
+// the grid-stride kernels.
+constexpr int RB = 128;
+bool rows_ok(int ny, int nz) { return ny <= 65535 && nz <= 65535; }
+dim3 row_grid(int nx, int ny, int nz) { return dim3((unsigned)((nx + RB - 1) / RB), (unsigned)ny, (unsigned)nz); }
+
 struct MaskPtrs {
     const uint8_t *p[kMaxMasks];
 };
+
+// Four voxels per thread: one 32-bit load per mask, a byte-wise nonzero test.
+__global__ void k_pack4(MaskPtrs m, int k, size_t n4, uint32_t *__restrict__ bits) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t b = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxMasks; ++j)
+            if (j < k) b |= __vcmpne4(__ldg(reinterpret_cast<const uint32_t *>(m.p[j]) + i), 0u) & (0x01010101u << j);
+        bits[i] = b;
+    }
+}
 
 __global__ void k_pack(MaskPtrs m, int k, size_t n, uint8_t *__restrict__ bits) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -54,6 +74,22 @@ __global__ void k_restrict_image(const IT *__restrict__ in, int nx, int ny, int 
     }
 }
 
+// The same box mean per coarse row (X = thread, Y, Z = grid).
+template <typename IT, typename OT>
+__global__ void k_restrict_image_rows(const IT *__restrict__ in, int nx, int ny, int nz, OT *__restrict__ out) {
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2;
+    const int X = blockIdx.x * RB + threadIdx.x, Y = blockIdx.y, Z = blockIdx.z;
+    if (X >= cx) return;
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int x = min(2 * X + (q & 1), nx - 1), y = min(2 * Y + ((q >> 1) & 1), ny - 1),
+                  z = min(2 * Z + ((q >> 2) & 1), nz - 1);
+        s += ld_img<IT>(in + vox(x, y, z, nx, ny));
+    }
+    out[vox(X, Y, Z, cx, cy)] = from_f<OT>(s * 0.125f);
+}
+
 // Per bit: inside if at least 4 of the 8 source voxels are inside.
 __global__ void k_restrict_bits(const uint8_t *__restrict__ in, int nx, int ny, int nz,
                                 uint8_t *__restrict__ out) {
@@ -79,6 +115,49 @@ __global__ void k_restrict_bits(const uint8_t *__restrict__ in, int nx, int ny, 
 }
 
 // u_f(x) = 2 u_c((x + 0.5)/2 - 0.5), trilinear with clamped coordinates.
+__global__ void k_restrict_bits_rows(const uint8_t *__restrict__ in, int nx, int ny, int nz,
+                                     uint8_t *__restrict__ out) {
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2;
+    const int X = blockIdx.x * RB + threadIdx.x, Y = blockIdx.y, Z = blockIdx.z;
+    if (X >= cx) return;
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int x = min(2 * X + (q & 1), nx - 1), y = min(2 * Y + ((q >> 1) & 1), ny - 1),
+                  z = min(2 * Z + ((q >> 2) & 1), nz - 1);
+        const unsigned b = __ldg(in + vox(x, y, z, nx, ny));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cnt[j] += (b >> j) & 1u;
+    }
+    unsigned o = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o |= (cnt[j] >= 4 ? 1u : 0u) << j;
+    out[vox(X, Y, Z, cx, cy)] = (uint8_t)o;
+}
+
+// Prolongation per fine row (x = thread, y, z = grid), the arithmetic of k_prolong.
+__global__ void k_prolong_rows(const float *__restrict__ uc, int cx, int cy, int cz, int nx, int ny, int nz,
+                               float *__restrict__ uf) {
+    const int x = blockIdx.x * RB + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= nx) return;
+    const size_t N = (size_t)nx * ny * nz, Nc = (size_t)cx * cy * cz;
+    const size_t i = vox(x, y, z, nx, ny);
+    const Corners c = corners((x + 0.5f) * 0.5f - 0.5f, (y + 0.5f) * 0.5f - 0.5f, (z + 0.5f) * 0.5f - 0.5f,
+                              cx, cy, cz);
+    float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int qx = (q & 1) ? c.x1 : c.x0, qy = (q & 2) ? c.y1 : c.y0, qz = (q & 4) ? c.z1 : c.z0;
+        const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
+                        ((q & 4) ? c.wz : 1.f - c.wz);
+        const size_t ci = vox(qx, qy, qz, cx, cy);
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) acc[comp] = fmaf(w, __ldg(uc + comp * Nc + ci), acc[comp]);
+    }
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) uf[comp * N + i] = 2.f * acc[comp];
+}
+
 __global__ void k_prolong(const float *__restrict__ uc, int cx, int cy, int cz, int nx, int ny,
                           int nz, float *__restrict__ uf) {
     const size_t N = (size_t)nx * ny * nz, Nc = (size_t)cx * cy * cz;
@@ -169,6 +248,62 @@ __global__ void k_uroi_dilate(const uint32_t *__restrict__ zbits, int rz, int nx
     }
 }
 
+// Row versions of the three UROI passes.  Pass 1 stages the row's mask bits
+// (with an rx halo) in shared memory; pass 2 takes, per y offset, the z
+// offsets whose extent admits the row distance r from a table built on the
+// host (bit dz + rz of zsets[dy + ry][r] set iff r <= ext[dz][dy]), the same
+// decisions as the loop over dz.
+struct UroiZsets {
+    uint32_t zs[2 * kMaxUroiRadius + 1][kMaxUroiRadius + 1];
+};
+
+__global__ void k_uroi_rows_r(const uint8_t *__restrict__ sbits, unsigned mask, int rx, int nx, int ny, int nz,
+                              uint8_t *__restrict__ rowdist) {
+    __shared__ uint8_t row[RB + 2 * kMaxUroiRadius];
+    const int x0 = blockIdx.x * RB, y = blockIdx.y, z = blockIdx.z;
+    const size_t rb = vox(0, y, z, nx, ny);
+    for (int p = threadIdx.x; p < RB + 2 * rx; p += RB) {
+        const int xx = x0 - rx + p;
+        row[p] = (xx >= 0 && xx < nx && (__ldg(sbits + rb + xx) & mask)) ? 1 : 0;
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= nx) return;
+    int d = 255;
+    for (int dx = -rx; dx <= rx; ++dx)
+        if (row[threadIdx.x + rx + dx]) d = min(d, abs(dx));
+    rowdist[rb + x] = (uint8_t)d;
+}
+
+__global__ void k_uroi_planes_r(const uint8_t *__restrict__ rowdist, const __grid_constant__ UroiZsets t, int ry,
+                                int nx, int ny, int nz, uint32_t *__restrict__ zbits) {
+    const int x = blockIdx.x * RB + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= nx) return;
+    const size_t i = vox(x, y, z, nx, ny);
+    uint32_t b = 0;
+    for (int dy = -ry; dy <= ry; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= ny) continue;
+        const int r = __ldg(rowdist + i + (ptrdiff_t)dy * nx);
+        if (r != 255) b |= t.zs[dy + ry][r];
+    }
+    zbits[i] = b;
+}
+
+__global__ void k_uroi_dilate_r(const uint32_t *__restrict__ zbits, int rz, int nx, int ny, int nz,
+                                uint8_t *__restrict__ out) {
+    const int x = blockIdx.x * RB + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= nx) return;
+    const size_t nxy = (size_t)nx * ny, i = vox(x, y, z, nx, ny);
+    uint32_t hit = 0;
+    for (int dz = -rz; dz <= rz; ++dz) {
+        const int zz = z + dz;
+        if (zz < 0 || zz >= nz) continue;
+        hit |= (__ldg(zbits + i + (ptrdiff_t)dz * (ptrdiff_t)nxy) >> (dz + rz)) & 1u;
+    }
+    out[i] = (uint8_t)hit;
+}
+
 __global__ void k_fill_u8(uint8_t *p, size_t n, uint8_t v) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
@@ -255,8 +390,16 @@ __global__ void k_convert(const IN *__restrict__ in, size_t n, OUT *__restrict__
 cudaError_t launch_pack_masks(const uint8_t *const *masks, int k, size_t n, uint8_t *bits,
                               cudaStream_t s) {
     MaskPtrs m{};
-    for (int j = 0; j < k && j < kMaxMasks; ++j) m.p[j] = masks[j];
-    k_pack<<<flat_grid(n), 256, 0, s>>>(m, k, n, bits); note_launch();
+    bool aligned = n % 4 == 0 && reinterpret_cast<uintptr_t>(bits) % 4 == 0;
+    for (int j = 0; j < k && j < kMaxMasks; ++j) {
+        m.p[j] = masks[j];
+        aligned = aligned && reinterpret_cast<uintptr_t>(masks[j]) % 4 == 0;
+    }
+    if (aligned)
+        k_pack4<<<flat_grid(n / 4), 256, 0, s>>>(m, k, n / 4, reinterpret_cast<uint32_t *>(bits));
+    else
+        k_pack<<<flat_grid(n), 256, 0, s>>>(m, k, n, bits);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -264,6 +407,17 @@ template <typename IT>
 static void restrict_image_to(const void *in, int nx, int ny, int nz, void *out, int out_dtype, size_t Nc,
                               cudaStream_t s) {
     const IT *src = static_cast<const IT *>(in);
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
+    if (rows_ok(cy, cz)) {
+        const dim3 g = row_grid(cx, cy, cz);
+        if (out_dtype == CGDIR_F16)
+            k_restrict_image_rows<IT, __half><<<g, RB, 0, s>>>(src, nx, ny, nz, (__half *)out);
+        else if (out_dtype == CGDIR_BF16)
+            k_restrict_image_rows<IT, __nv_bfloat16><<<g, RB, 0, s>>>(src, nx, ny, nz, (__nv_bfloat16 *)out);
+        else
+            k_restrict_image_rows<IT, float><<<g, RB, 0, s>>>(src, nx, ny, nz, (float *)out);
+        return;
+    }
     if (out_dtype == CGDIR_F16)
         k_restrict_image<IT, __half><<<flat_grid(Nc), 256, 0, s>>>(src, nx, ny, nz, (__half *)out);
     else if (out_dtype == CGDIR_BF16)
@@ -293,13 +447,22 @@ cudaError_t launch_restrict_image(const void *in, int dtype, int nx, int ny, int
 cudaError_t launch_restrict_bits(const uint8_t *in, int nx, int ny, int nz, uint8_t *out,
                                  cudaStream_t s) {
     const size_t Nc = (size_t)((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
-    k_restrict_bits<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out); note_launch();
+    const int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
+    if (rows_ok(cy, cz))
+        k_restrict_bits_rows<<<row_grid(cx, cy, cz), RB, 0, s>>>(in, nx, ny, nz, out);
+    else
+        k_restrict_bits<<<flat_grid(Nc), 256, 0, s>>>(in, nx, ny, nz, out);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(const float *uc, int cx, int cy, int cz, int nx, int ny, int nz,
                            float *uf, cudaStream_t s) {
-    k_prolong<<<flat_grid((size_t)nx * ny * nz), 256, 0, s>>>(uc, cx, cy, cz, nx, ny, nz, uf); note_launch();
+    if (rows_ok(ny, nz))
+        k_prolong_rows<<<row_grid(nx, ny, nz), RB, 0, s>>>(uc, cx, cy, cz, nx, ny, nz, uf);
+    else
+        k_prolong<<<flat_grid((size_t)nx * ny * nz), 256, 0, s>>>(uc, cx, cy, cz, nx, ny, nz, uf);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -333,6 +496,21 @@ cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, con
     const unsigned mask = (k >= 8) ? 0xffu : ((1u << k) - 1u);
     uint8_t *rowdist = scratch;
     uint32_t *zbits = reinterpret_cast<uint32_t *>(scratch + (N + 3) / 4 * 4);
+    if (rows_ok(ny, nz)) {
+        UroiZsets zt{};
+        for (int dy = -t.ry; dy <= t.ry; ++dy)
+            for (int r = 0; r <= t.rx; ++r) {
+                uint32_t b = 0;
+                for (int dz = -t.rz; dz <= t.rz; ++dz)
+                    if (r <= t.ext[dz + t.rz][dy + t.ry]) b |= 1u << (dz + t.rz);
+                zt.zs[dy + t.ry][r] = b;
+            }
+        const dim3 g = row_grid(nx, ny, nz);
+        k_uroi_rows_r<<<g, RB, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist); note_launch();
+        k_uroi_planes_r<<<g, RB, 0, s>>>(rowdist, zt, t.ry, nx, ny, nz, zbits); note_launch();
+        k_uroi_dilate_r<<<g, RB, 0, s>>>(zbits, t.rz, nx, ny, nz, out); note_launch();
+        return cudaGetLastError();
+    }
     k_uroi_rows<<<flat_grid(N), 256, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist); note_launch();
     k_uroi_planes<<<flat_grid(N), 256, 0, s>>>(rowdist, t, nx, ny, nz, zbits); note_launch();
     k_uroi_dilate<<<flat_grid(N), 256, 0, s>>>(zbits, t.rz, nx, ny, nz, out); note_launch();
