@@ -484,7 +484,8 @@ def run_cgdir(args):
         avg_ms = p["total_ms"] / p["launches"]
         bytes_per_launch = SMOOTH_BYTES_PER_VOXEL * N
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_smooth_tma (z-march Gaussian of u, finest level; the same kernel "
+        kname = "k_smooth_wide" if host.shape[2] % 8 == 0 else "k_smooth_tma"
+        roofline = {"bound": "hbm", "kernel": f"{kname} (z-march Gaussian of u, finest level; the same kernel "
                                               "also smooths du there)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic_record("smooth", args.workload, SMOOTH_SOURCES) if sigma_default(kw)
