@@ -198,10 +198,7 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
                           float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr,
                           SmoothChoice ch = SmoothChoice(), float *scratch = nullptr);
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
-                           float *out, const int *stop_flag, cudaStream_t s, int *err = nullptr);
-// The composite update (step 3); err: device word for bounded-wait timeouts,
-// nullptr selects the kernel that gathers u from global memory only (with
-// err, the kernel that stages u in shared memory where TMA applies).
+                           float *out, const int *stop_flag, cudaStream_t s);
 // Algorithm A steps 2 + 3: out = G(du) + u(x + G(du)) (or u + G(du)).  By
 // default G(du) goes to tmp (3N floats) and a composite-update kernel
 // follows; one_pass fuses both into one TMA kernel over all three

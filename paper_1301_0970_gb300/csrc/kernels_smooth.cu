@@ -616,132 +616,6 @@ __global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict
     }
 }
 
-// ---- composite update with u staged in shared memory -----------------------
-// The same update as k_compose_tiles (same arithmetic, same bits) for a
-// 32 x 8 column marching z.  Stage q of a ring of CW holds, by one TMA copy
-// each, u's three components at volume plane zb - 2 + q over a box of
-// 40 x 12 (x from x0 - 4, y from y0 - 2) and du's three components at the
-// same plane over the column itself; so the box holds u within 2 voxels of
-// the column in y and z (4 / 3 in x), and no global load waits inside the
-// march.  A voxel whose eight corners lie in the planes z - 2 .. z + 2 reads
-// them from shared memory (the smoothed update is a fraction of a voxel
-// almost everywhere); the others gather them from global memory.  Both give
-// the same values.  One barrier per plane.
-constexpr int CWX = 40, CWY = 12, CWH = 2;          // u box and its halo in y and z
-constexpr int CW = 6;                               // ring of planes (4 CTAs/SM)
-constexpr int CUP = 3 * CWY * CWX;                  // floats of u per stage
-constexpr int CDP = 3 * TY * TX;                    // floats of du per stage
-constexpr int CWP = CUP + CDP;                      // floats per stage (128-byte multiple)
-static_assert(CWP % 32 == 0 && CUP % 32 == 0, "stages and their du part stay 128-byte aligned");
-constexpr size_t compose_window_bytes() { return sizeof(float) * CW * CWP + CW * sizeof(uint64_t) + 128; }
-
-__global__ void __launch_bounds__(NT, 4) k_compose_window(const __grid_constant__ CUtensorMap umap,
-                                                          const __grid_constant__ CUtensorMap dumap,
-                                                          const float *__restrict__ u, int nx, int ny, int nz,
-                                                          int zc, float *__restrict__ out, const int *stop_flag,
-                                                          int *err) {
-    if (stop_flag && *stop_flag) return;
-    extern __shared__ __align__(128) float csm[];
-    const int pad = (int)(((128u - (smem_u32(csm) & 127u)) & 127u) >> 2);
-    float *win = csm + pad;                                  // [CW][u: 3][CWY][CWX | du: 3][TY][TX]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(win + CW * CWP);
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    const int zb = blockIdx.z * zc, ze = min(zb + zc, nz);
-    const int nxy = nx * ny, N = nxy * nz;
-    const bool act = x < nx && y < ny;
-    const float fxmax = (float)(nx - 1), fymax = (float)(ny - 1), fzmax = (float)(nz - 1);
-    const int P = (ze - zb) + 2 * CWH;                       // stages of this chunk
-    auto issue = [&](int q) {
-        const int sidx = q % CW;
-        const int zq = clampi(zb - CWH + q, 0, nz - 1);
-        mbar_expect_tx(&bar[sidx], (uint32_t)(CWP * sizeof(float)));
-        tma_load_4d(win + sidx * CWP, &umap, x0 - 4, y0 - CWH, zq, 0, &bar[sidx]);
-        tma_load_4d(win + sidx * CWP + CUP, &dumap, x0, y0, zq, 0, &bar[sidx]);
-    };
-    if (tid == 0) {
-        for (int q = 0; q < CW; ++q) mbar_init(&bar[q], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0)
-        for (int q = 0; q < CW && q < P; ++q) issue(q);
-    const int col = y * nx + x;
-    const int dofs = threadIdx.y * TX + threadIdx.x;            // this voxel in a stage's du part
-    int tw = -1;                                               // stage whose wait ran out
-    for (int z = zb; z < ze; ++z) {
-        // planes z - 2 .. z + 2 are stages r .. r + 4; du of plane z is in stage r + 2
-        const int r = z - zb;
-        bool ok = true;
-        for (int q = (r == 0 ? 0 : r + 2 * CWH); q <= r + 2 * CWH && ok; ++q) {
-            ok = mbar_wait_bounded(&bar[q % CW], (uint32_t)((q / CW) & 1));
-            if (!ok) tw = q;
-        }
-        if (__syncthreads_or(!ok)) break;
-        if (act) {
-            const int i = z * nxy + col;
-            const float *dp = win + ((r + CWH) % CW) * CWP + CUP + dofs;
-            const float dx = dp[0], dy = dp[TY * TX], dz = dp[2 * TY * TX];
-            const float px = fminf(fmaxf((float)x + dx, 0.f), fxmax);
-            const float py = fminf(fmaxf((float)y + dy, 0.f), fymax);
-            const float pz = fminf(fmaxf((float)z + dz, 0.f), fzmax);
-            const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
-            const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-            const float wx = px - fx, wy = py - fy, wz = pz - fz;
-            const int ddx = ix < nx - 1 ? 1 : 0, ddy = iy < ny - 1 ? 1 : 0, ddz = iz < nz - 1 ? 1 : 0;
-            const int lx = ix - (x0 - 4), ly = iy - (y0 - CWH), lz = iz - (z - CWH);
-            float cx[8], cy[8], cz[8];
-            if (lx >= 0 && lx + ddx < CWX && ly >= 0 && ly + ddy < CWY && lz >= 0 && lz + ddz <= 2 * CWH) {
-                const float *p0 = win + ((r + lz) % CW) * CWP + ly * CWX + lx;
-                const float *p1 = win + ((r + lz + ddz) % CW) * CWP + ly * CWX + lx;
-                const int o[4] = {0, ddx, ddy * CWX, ddy * CWX + ddx};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float *d = c == 0 ? cx : (c == 1 ? cy : cz);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        d[q] = p0[c * CWY * CWX + o[q]];
-                        d[q + 4] = p1[c * CWY * CWX + o[q]];
-                    }
-                }
-            } else {
-                const int b0 = iz * nxy + iy * nx + ix;
-                const int o[8] = {0, ddx, ddy * nx, ddy * nx + ddx, ddz * nxy, ddz * nxy + ddx, ddz * nxy + ddy * nx,
-                                  ddz * nxy + ddy * nx + ddx};
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    cx[q] = __ldg(u + b0 + o[q]);
-                    cy[q] = __ldg(u + N + b0 + o[q]);
-                    cz[q] = __ldg(u + 2 * N + b0 + o[q]);
-                }
-            }
-            auto tri = [&](const float *c) {
-                const float e00 = fmaf(wx, c[1] - c[0], c[0]), e10 = fmaf(wx, c[3] - c[2], c[2]);
-                const float e01 = fmaf(wx, c[5] - c[4], c[4]), e11 = fmaf(wx, c[7] - c[6], c[6]);
-                const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
-                return fmaf(wz, f1 - f0, f0);
-            };
-            out[i] = dx + tri(cx);
-            out[N + i] = dy + tri(cy);
-            out[2 * N + i] = dz + tri(cz);
-        }
-        __syncthreads();                          // stage r (volume plane z - 2) is free
-        if (tid == 0 && r + CW < P) {
-            fence_proxy_async();
-            issue(r + CW);
-        }
-    }
-    if (tw >= 0) {
-        // a wait ran out: record it, drain the copies still in flight (bounded), leave
-        if (tid == 0) {
-            atomicExch(err, 1);
-            for (int q = 0; q < min(P, tw + CW); ++q) mbar_wait_bounded(&bar[q % CW], (uint32_t)((q / CW) & 1));
-        }
-        __syncthreads();
-    }
-}
-
 // ---- 3-D tile version (small volumes) ------------------------------------
 // A CTA loads a 16 x 16 x 8 output tile of one component with its R-voxel
 // halo into shared memory (clamped indices) and runs the x, y and z passes
@@ -1234,27 +1108,12 @@ cudaError_t launch_smooth_compose(const float *du, const float *u, int mode, flo
     if (ch.variant == SMOOTH_SPLIT) ch.variant = SMOOTH_MARCH;
     cudaError_t e = launch_smooth(du, 3, sigma, nx, ny, nz, tmp, stop_flag, s, err, ch);
     if (e != cudaSuccess) return e;
-    return launch_compose(u, tmp, mode, nx, ny, nz, out, stop_flag, s, err);
+    return launch_compose(u, tmp, mode, nx, ny, nz, out, stop_flag, s);
 }
 
 cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, int ny, int nz,
-                           float *out, const int *stop_flag, cudaStream_t s, int *err) {
+                           float *out, const int *stop_flag, cudaStream_t s) {
     const long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
-    if (mode == CGDIR_COMPOSE && err != nullptr && (size_t)nx * ny * nz * 3 < ((size_t)1 << 31)) {
-        CUtensorMap m, md;
-        const uint64_t dims[4] = {(uint64_t)nx, (uint64_t)ny, (uint64_t)nz, 3};
-        const uint32_t box[4] = {(uint32_t)CWX, (uint32_t)CWY, 1u, 3u}, dbox[4] = {TX, TY, 1u, 3u};
-        if (encode_tensor_map(&m, u, 4, dims, box, 4) && encode_tensor_map(&md, du, 4, dims, dbox, 4)) {
-            const int zc = pick_zchunk(nz, tiles, 4, 4);
-            dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + zc - 1) / zc), block(TX, TY);
-            const size_t smem = compose_window_bytes();
-            cudaError_t e = ensure_smem((const void *)k_compose_window, smem);
-            if (e != cudaSuccess) return e;
-            k_compose_window<<<grid, block, smem, s>>>(m, md, u, nx, ny, nz, zc, out, stop_flag, err);
-            note_launch();
-            return cudaGetLastError();
-        }
-    }
     const int zc = pick_zchunk(nz, tiles, 8, 4);
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + zc - 1) / zc), block(TX, TY);
     k_compose_tiles<<<grid, block, 0, s>>>(u, du, mode, nx, ny, nz, zc, out, stop_flag);

@@ -478,12 +478,12 @@ int cgdir_compose(cgdir_ctx *ctx, const float *u, const float *du, int mode, flo
     DeviceGuard g(ctx->device);
     const size_t N = (size_t)nx * ny * nz;
     if (gauss_radius(sigma) == 0) {
-        CK(launch_compose(u, du, mode, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx)));
+        CK(launch_compose(u, du, mode, nx, ny, nz, out, nullptr, ctx->stream));
         return CGDIR_OK;
     }
     void *tmp = nullptr;
     TRY(ws_get(ctx, "field_tmp", 3 * N * sizeof(float), &tmp));
-    CK(launch_compose(u, du, mode, nx, ny, nz, (float *)tmp, nullptr, ctx->stream, kerr(ctx)));
+    CK(launch_compose(u, du, mode, nx, ny, nz, (float *)tmp, nullptr, ctx->stream));
     CK(launch_smooth((float *)tmp, 3, sigma, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
     return CGDIR_OK;
 }
@@ -496,7 +496,7 @@ int cgdir_smooth_compose(cgdir_ctx *ctx, const float *du, const float *u, int mo
         return fail(ctx, CGDIR_EINVAL, "smooth_compose: bad arguments");
     DeviceGuard g(ctx->device);
     if (gauss_radius(sigma) == 0) {
-        CK(launch_compose(u, du, mode, nx, ny, nz, out, nullptr, ctx->stream, kerr(ctx)));
+        CK(launch_compose(u, du, mode, nx, ny, nz, out, nullptr, ctx->stream));
         return CGDIR_OK;
     }
     void *tmp = nullptr;
@@ -533,7 +533,7 @@ int cgdir_iterate(cgdir_ctx *ctx, const float *I0, const float *T0, const uint8_
     TRY(force_impl(ctx, a, stats_host));
     if (du_out) {   // the smoothed du is wanted: steps 2 and 3 separately
         CK(launch_smooth(du, 3, sigma_fluid, nx, ny, nz, du_out, nullptr, ctx->stream, kerr(ctx), prim_smooth(ctx)));
-        CK(launch_compose(u_in, du_out, compose_mode, nx, ny, nz, un, nullptr, ctx->stream, kerr(ctx)));
+        CK(launch_compose(u_in, du_out, compose_mode, nx, ny, nz, un, nullptr, ctx->stream));
     } else {
         CK(launch_smooth_compose(du, u_in, compose_mode, sigma_fluid, nx, ny, nz, un, (float *)t3, nullptr,
                                  ctx->stream, kerr(ctx), ctx->fused_force, prim_smooth(ctx)));
