@@ -383,7 +383,11 @@ __global__ void __launch_bounds__(NT) k_smooth_tma(const __grid_constant__ CUten
 //  * z pass: the last 2R+1 y-pass results of those four outputs stay in
 //    registers (slots fixed at compile time by unrolling the plane loop
 //    2R+1 times), paired FMAs; 8-byte stores.
-// One barrier per plane (the x-pass buffer is double-buffered).
+// One barrier per PB planes (PB x-pass buffers, double-buffered); the
+// launcher takes PB = 1 (two to four planes per barrier measured slower:
+// 262-332 against 218 us at 512 x 512 x 160).  The plane count of a step is
+// the runtime min(PB, planes left) even for PB = 1: written with a
+// compile-time 1 instead (same bits), the kernel took 265 us.
 // Box rows are 76 floats wide (x0 - 4 .. x0 + 71; the last 4 columns are
 // not used) and so are the x-pass buffer's rows: 19 16-byte units, so the
 // x-pass tasks below (task q: box row q % BY, column group q / BY) hit
@@ -398,12 +402,12 @@ struct WideGeom {
     static constexpr int STAGE = (BY * WBX + 31) / 32 * 32;     // floats per stage (128-byte multiple)
     static constexpr int XB = BY * WBX;                         // floats per x-pass buffer
     static constexpr int NTASK = BY * (WX / 8);                 // x-pass tasks per plane
-    static constexpr size_t bytes() {
-        return sizeof(float) * ((size_t)ST * STAGE + 2 * XB) + ST * sizeof(uint64_t) + 128;
+    static constexpr size_t bytes(int pb) {
+        return sizeof(float) * ((size_t)ST * STAGE + 2 * (size_t)pb * XB) + ST * sizeof(uint64_t) + 128;
     }
 };
 
-template <int R>
+template <int R, int PB>
 __global__ void __launch_bounds__(NT, 2) k_smooth_wide(const __grid_constant__ CUtensorMap tin,
                                                        float *__restrict__ out, Taps taps, int nx, int ny,
                                                        int nz, int zchunk, const int *stop_flag, int *err) {
@@ -411,12 +415,13 @@ __global__ void __launch_bounds__(NT, 2) k_smooth_wide(const __grid_constant__ C
     using G = WideGeom<R>;
     constexpr int K = 2 * R + 1, BY = G::BY, ST = G::ST, STAGE = G::STAGE, XB = G::XB;
     static_assert(R >= 1 && R <= 4, "8-output x tasks read 16 loaded values");
+    static_assert(PB >= 1 && PB <= 4, "planes per barrier");
     extern __shared__ __align__(128) float wsm[];
     // 128-byte aligned base for the TMA stages, still a shared-memory pointer
     const int pad = (int)(((128u - (smem_u32(wsm) & 127u)) & 127u) >> 2);
     float *stage0 = wsm + pad;                                   // [ST][STAGE]
-    float *xbuf = stage0 + ST * STAGE;                           // [2][BY][WX]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(xbuf + 2 * XB);
+    float *xbuf = stage0 + ST * STAGE;                           // [2][PB][BY][WBX]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(xbuf + 2 * PB * XB);
 
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int x0 = blockIdx.x * WX, y0 = blockIdx.y * WY;
@@ -466,91 +471,111 @@ __global__ void __launch_bounds__(NT, 2) k_smooth_wide(const __grid_constant__ C
 #pragma unroll
         for (int j = 0; j < K; ++j) ring[h][j] = make_float2(0.f, 0.f);
 
+    // x pass of the plane in stage sidx into x-pass buffer dst
+    auto xpass = [&](int sidx, float *dst) {
+        const float *src = stage0 + sidx * STAGE + xsrc;
+        float v[16];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float4 f = *reinterpret_cast<const float4 *>(src + 4 * h);
+            v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
+        }
+        if (xedge) {                   // CTAs at an x border of the volume only
+#pragma unroll
+            for (int k = WML - R; k < WML; ++k) v[k] = pleft ? v[WML] : v[k];
+#pragma unroll
+            for (int k = 8 + WML; k < 8 + WML + R; ++k) v[k] = pright ? v[7 + WML] : v[k];
+        }
+        float2 o[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) o[m] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            constexpr int B = WML - R;
+            if ((B + j) % 2 == 0) {            // operand pairs register-aligned
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    o[m] = __ffma2_rn(w2[j], make_float2(v[B + j + 2 * m], v[B + j + 2 * m + 1]), o[m]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    o[m].x = fmaf(w2[j].x, v[B + j + 2 * m], o[m].x);
+                    o[m].y = fmaf(w2[j].x, v[B + j + 2 * m + 1], o[m].y);
+                }
+            }
+        }
+        float *d = dst + xdst;
+        *reinterpret_cast<float4 *>(d) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+        *reinterpret_cast<float4 *>(d + 4) = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+    };
+
     int tw = -1;                        // plane whose wait ran out (-1: none)
     int sidx = 0, xo = 0;               // stage of plane t, x-pass buffer offset
     uint32_t par = 0;                   // phase parity of that stage
-    for (int t0 = 0; t0 < P && tw < 0; t0 += K) {
+    for (int t0 = 0; t0 < P && tw < 0; t0 += PB * K) {
 #pragma unroll
-        for (int r = 0; r < K; ++r) {
-            const int t = t0 + r;
+        for (int rr = 0; rr < PB * K; rr += PB) {
+            const int t = t0 + rr;
             if (t >= P) break;
+            const int np = min(PB, P - t);                // planes this step (the same for every thread)
             bool ok = true;
             if (xtask) {
-                ok = mbar_wait_bounded(&bar[sidx], par);
-                const float *src = stage0 + sidx * STAGE + xsrc;
-                float v[16];
+                int si = sidx;
+                uint32_t pa = par;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const float4 f = *reinterpret_cast<const float4 *>(src + 4 * h);
-                    v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
+                for (int e = 0; e < PB; ++e) {
+                    if (e >= np) break;
+                    ok = ok && mbar_wait_bounded(&bar[si], pa);
+                    xpass(si, xbuf + xo + e * XB);
+                    if (++si == ST) { si = 0; pa ^= 1u; }
                 }
-                if (xedge) {                   // CTAs at an x border of the volume only
-#pragma unroll
-                    for (int k = WML - R; k < WML; ++k) v[k] = pleft ? v[WML] : v[k];
-#pragma unroll
-                    for (int k = 8 + WML; k < 8 + WML + R; ++k) v[k] = pright ? v[7 + WML] : v[k];
-                }
-                float2 o[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) o[m] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    constexpr int B = WML - R;
-                    if ((B + j) % 2 == 0) {            // operand pairs register-aligned
-#pragma unroll
-                        for (int m = 0; m < 4; ++m)
-                            o[m] = __ffma2_rn(w2[j], make_float2(v[B + j + 2 * m], v[B + j + 2 * m + 1]), o[m]);
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-                            o[m].x = fmaf(w2[j].x, v[B + j + 2 * m], o[m].x);
-                            o[m].y = fmaf(w2[j].x, v[B + j + 2 * m + 1], o[m].y);
-                        }
-                    }
-                }
-                float *dst = xbuf + xo + xdst;
-                *reinterpret_cast<float4 *>(dst) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-                *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
             }
             if (__syncthreads_or(!ok)) { tw = t; break; }
-            if (tid == 0 && t + ST < P) {      // the stage just consumed takes plane t + ST
+            if (tid == 0) {                    // the stages just consumed take planes t + e + ST
                 fence_proxy_async();
-                issue(t + ST);
+                for (int e = 0; e < np; ++e)
+                    if (t + e + ST < P) issue(t + e + ST);
             }
-            if (++sidx == ST) { sidx = 0; par ^= 1u; }
-            // y pass into this plane's ring slot, z pass for plane t - 2R
-            const float *col = xbuf + xo + yr * WBX + yc;
-            float2 yin[K + 1];
+            for (int e = 0; e < np; ++e)
+                if (++sidx == ST) { sidx = 0; par ^= 1u; }
+            // y pass into the planes' ring slots, z pass for planes t + e - 2R
 #pragma unroll
-            for (int j = 0; j <= K; ++j) yin[j] = *reinterpret_cast<const float2 *>(col + j * WBX);
-            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+            for (int e = 0; e < PB; ++e) {
+                if (e >= np) break;
+                const int te = t + e, re = (rr + e) % K;
+                const float *col = xbuf + xo + e * XB + yr * WBX + yc;
+                float2 yin[K + 1];
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                a0 = __ffma2_rn(w2[j], yin[j], a0);
-                a1 = __ffma2_rn(w2[j], yin[j + 1], a1);
-            }
-            ring[0][r] = a0;
-            ring[1][r] = a1;
-            xo ^= XB;
-            if (t >= 2 * R) {
-                float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
+                for (int j = 0; j <= K; ++j) yin[j] = *reinterpret_cast<const float2 *>(col + j * WBX);
+                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
-                    o0 = __ffma2_rn(w2[j], ring[0][(r + 1 + j) % K], o0);
-                    o1 = __ffma2_rn(w2[j], ring[1][(r + 1 + j) % K], o1);
+                    a0 = __ffma2_rn(w2[j], yin[j], a0);
+                    a1 = __ffma2_rn(w2[j], yin[j + 1], a1);
                 }
-                if (act0) *reinterpret_cast<float2 *>(optr) = o0;
-                if (act1) *reinterpret_cast<float2 *>(optr + nx) = o1;
-                optr += nxy;
+                ring[0][re] = a0;
+                ring[1][re] = a1;
+                if (te >= 2 * R) {
+                    float2 o0 = make_float2(0.f, 0.f), o1 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        o0 = __ffma2_rn(w2[j], ring[0][(re + 1 + j) % K], o0);
+                        o1 = __ffma2_rn(w2[j], ring[1][(re + 1 + j) % K], o1);
+                    }
+                    if (act0) *reinterpret_cast<float2 *>(optr) = o0;
+                    if (act1) *reinterpret_cast<float2 *>(optr + nx) = o1;
+                    optr += nxy;
+                }
             }
+            xo ^= PB * XB;
         }
     }
     if (tw >= 0) {
         // a wait ran out: record it, drain the loads still in flight (planes
-        // tw .. tw + ST - 1 were issued; bounded waits), leave
+        // tw .. tw + ST + PB - 2 were issued at most; bounded waits), leave
         if (tid == 0) {
             atomicExch(err, 1);
-            for (int q = tw; q < min(tw + ST, P); ++q)
+            for (int q = tw; q < min(tw + ST + PB - 1, P); ++q)
                 mbar_wait_bounded(&bar[q % ST], (uint32_t)((q / ST) & 1));
         }
         __syncthreads();
@@ -931,10 +956,11 @@ static cudaError_t smooth_wide_r(const float *in, float *out, int ncomp, const T
     const int zc = zc_override > 0 ? std::min(zc_override, nz) : wide_default_zchunk(nx, ny, nz, ncomp);
     const int nchunks = (nz + zc - 1) / zc;
     dim3 grid((nx + WX - 1) / WX, (ny + WY - 1) / WY, nchunks * ncomp), block(TX, TY);
-    const size_t smem = G::bytes();
-    cudaError_t e = ensure_smem((const void *)k_smooth_wide<R>, smem);
+    constexpr int PB = 1;       // planes per barrier: 2 to 4 measured slower (more x-pass buffers)
+    const size_t smem = G::bytes(PB);
+    cudaError_t e = ensure_smem((const void *)k_smooth_wide<R, PB>, smem);
     if (e != cudaSuccess) return e;
-    k_smooth_wide<R><<<grid, block, smem, s>>>(m, out, t, nx, ny, nz, zc, stop_flag, err);
+    k_smooth_wide<R, PB><<<grid, block, smem, s>>>(m, out, t, nx, ny, nz, zc, stop_flag, err);
     *launched = true;
     note_launch();
     return cudaGetLastError();
