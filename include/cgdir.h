@@ -183,10 +183,17 @@ void cgdir_default_params(cgdir_params *p);
                                  TMA force and fused smoothing kernels
      CGDIR_GRAPHS=0              launch eagerly instead of replaying graphs
      CGDIR_SMOOTH=march|tile|split|fused, CGDIR_SMOOTH_ZCHUNK=n   smoothing variant
-     CGDIR_FORCE_ZCHUNK=n, CGDIR_FORCE_SINGLE=1   force pass 2 z chunk / one
-                                 voxel per thread
+     CGDIR_FORCE_ZCHUNK=n, CGDIR_FORCE_WIDTH=1|2   force pass 2 z chunk / voxels
+                                 per thread (default: 4 where nx % 4 == 0, else 2
+                                 for even nx, else 1)
      CGDIR_COOP_MAX=n            levels below the finest with at most n voxels
-                                 run as one cooperative launch */
+                                 run as one cooperative launch
+     CGDIR_SERVE_SCHEDULE=shared|alone|auto   schedule of submitted requests
+                                 (default auto: the latency schedule of
+                                 cgdir_register when no other request is
+                                 running at submission, else the throughput one)
+     CGDIR_SHARED_WIDE_CAP=n     z-march smoothing CTAs per SM in batched and
+                                 shared served registrations (default 2; 0: no cap) */
 int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg);
 
 /* Release every device buffer, cached graph and (if owned) stream of ctx.
@@ -259,8 +266,11 @@ int cgdir_register_batch(cgdir_ctx *ctx, int count, const cgdir_volume *statics,
  * release).  Inputs must stay valid until the request completes; dvf_out
  * is written by the time cgdir_wait / cgdir_poll return CGDIR_OK (a
  * pageable host dvf_out is copied by that call, pinned or device memory by
- * the request's stream).  A result is the same, bit for bit, whether the
- * request ran alone or among others.  The context's stream is not used. */
+ * the request's stream).  A request submitted while no other is running
+ * takes the kernel schedule of cgdir_register (latency); one submitted
+ * while others run takes the throughput schedule of cgdir_register_batch.
+ * A result is the same, bit for bit, whether the request ran alone or among
+ * others, on either schedule.  The context's stream is not used. */
 int cgdir_set_max_inflight(cgdir_ctx *ctx, int n);            /* 1..256 */
 int cgdir_submit(cgdir_ctx *ctx, const cgdir_volume *static_img, const cgdir_volume *moving_img,
                  const cgdir_masks *static_masks, const cgdir_masks *moving_masks,

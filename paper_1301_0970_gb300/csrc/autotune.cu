@@ -3,11 +3,12 @@
 // data of that shape, the candidate launch configurations of the two
 // kernels whose best configuration depends on the shape:
 //   smoothing (with the composite update, i.e. steps 2-4 of an iteration):
-//              the TMA z-march with its default z chunk, half and double
-//              that chunk (plus the separate update kernel), the 3-D
+//              the TMA z-march with its default z chunk, half, double and
+//              four times that chunk (plus the separate update kernel), the 3-D
 //              shared-memory tile kernel (idem), and the split xy + z
 //              kernels with the update fused into the z pass;
-//   force:     the stencil pass with the default z chunk, half and double;
+//   force:     the stencil pass with the default z chunk, half, a quarter
+//              and double;
 // then the fused schedule (force stencil pass alone, 3-D tiles of G(du)
 // with the update, 3-D tiles of G(u') with the next iteration's warp)
 // against the best of those two, summed.
@@ -28,8 +29,11 @@ __device__ __forceinline__ unsigned hash3(unsigned x, unsigned y, unsigned z, un
     return h;
 }
 
-// Synthetic level: CT-like values with structure, blocky masks (so both the
-// uniform and the mixed structure paths run), displacements up to 1.5 voxels.
+// Synthetic level shaped like a registration's: CT-like values with
+// structure and noise, k compact structures (ellipsoids around the centre,
+// the moving ones 2 voxels off the static ones, so a thin shell of voxels
+// takes the mixed structure path as near real organ borders) and a smooth
+// displacement field of up to 1.5 voxels.
 template <typename IT>
 __global__ void k_tune_fill(IT *I0, IT *T0, uint8_t *mbits, uint8_t *sbits, uint8_t *uroi, float *u, int nx,
                             int ny, int nz, int k) {
@@ -41,16 +45,21 @@ __global__ void k_tune_fill(IT *I0, IT *T0, uint8_t *mbits, uint8_t *sbits, uint
         const float n1 = (float)(hash3(x, y, z, 2) & 1023u) * (50.f / 1023.f);
         I0[i] = from_f<IT>(base + n0);
         T0[i] = from_f<IT>(base + n1);
+        const float fx = (x + 0.5f) / nx, fy = (y + 0.5f) / ny, fz = (z + 0.5f) / nz, sx = 2.f / nx;
         unsigned mb = 0, sb = 0;
         for (int j = 0; j < k; ++j) {
-            if (((x / 24 + y / 24 + z / 12 + j) % 3) == 0) mb |= 1u << j;
-            if ((((x + 2) / 24 + y / 24 + z / 12 + j) % 3) == 0) sb |= 1u << j;
+            const float a = 6.2831853f * j / (k > 0 ? k : 1);
+            const float cx = 0.5f + 0.22f * __cosf(a), cy = 0.5f + 0.22f * __sinf(a);
+            const float dy = (fy - cy) / 0.1f, dz = (fz - 0.5f) / 0.2f;
+            const float ds = (fx - cx) / 0.1f, dm = (fx + sx - cx) / 0.1f;
+            if (dm * dm + dy * dy + dz * dz <= 1.f) mb |= 1u << j;
+            if (ds * ds + dy * dy + dz * dz <= 1.f) sb |= 1u << j;
         }
         mbits[i] = (uint8_t)mb;
         sbits[i] = (uint8_t)sb;
         uroi[i] = 1;
         for (int c = 0; c < 3; ++c)
-            u[c * N + i] = ((float)(hash3(x / 4, y / 4, z / 4, 10 + c) & 255u) - 127.5f) * (1.5f / 127.5f);
+            u[c * N + i] = 1.5f * __sinf(6.2831853f * (fx + 0.3f * c)) * __cosf(4.712389f * fy) * __cosf(3.1415927f * (fz - 0.5f));
     }
 }
 
@@ -59,7 +68,7 @@ __global__ void k_tune_fill(IT *I0, IT *T0, uint8_t *mbits, uint8_t *sbits, uint
 namespace cgdir {
 namespace rt {
 
-int force_zchunk_min(int nx, int ny, int nz) { return std::max(1, force_default_zchunk(nx, ny, nz) / 2); }
+int force_zchunk_min(int nx, int ny, int nz) { return std::max(1, force_default_zchunk(nx, ny, nz) / 4); }
 
 static const TunedLevel *find_tuned(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
     auto it = ctx->tuned.find(TuneKey{nx, ny, nz, contour ? 1 : 0, sdt});
@@ -68,6 +77,10 @@ static const TunedLevel *find_tuned(const cgdir_ctx *ctx, int nx, int ny, int nz
 
 SmoothChoice smooth_choice(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt, bool allow_fused) {
     SmoothChoice ch;
+    // registrations that share the GPU (batched, served) cap the wide z-march
+    // at two CTAs per SM: three fill an SM's shared memory and registers and
+    // starve the other registrations' kernels
+    if (!allow_fused) ch.ctas_per_sm = ctx->shared_wide_cap;
     if (ctx->smooth_variant != SMOOTH_AUTO || ctx->smooth_zchunk > 0) {
         ch.variant = ctx->smooth_variant;
         ch.zchunk = ctx->smooth_zchunk;
@@ -85,10 +98,13 @@ bool use_level_coop(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, i
     return (long)nx * ny * nz <= ctx->coop_max_voxels;
 }
 
+// Never below force_zchunk_min: the registration's partial-sum buffer is
+// sized for that chunk (a loaded table may hold any chunk).
 int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
-    if (ctx->force_zchunk > 0) return std::max(force_zchunk_min(nx, ny, nz), std::min(ctx->force_zchunk, nz));
+    const int lo = force_zchunk_min(nx, ny, nz);
+    if (ctx->force_zchunk > 0) return std::max(lo, std::min(ctx->force_zchunk, nz));
     if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt))
-        if (t->force_zchunk > 0) return t->force_zchunk;
+        if (t->force_zchunk > 0) return std::max(lo, std::min(t->force_zchunk, nz));
     return force_default_zchunk(nx, ny, nz);
 }
 
@@ -168,10 +184,12 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     int rc = CGDIR_OK;
     {
         const int d = force_default_zchunk(nx, ny, nz);
-        const int cand[3] = {d, std::max(1, d / 2), std::min(nz, 2 * d)};
+        const int cand[4] = {d, std::max(1, d / 2), std::max(1, d / 4), std::min(nz, 2 * d)};
         float bt = 1e30f;
-        for (int ci = 0; ci < 3 && rc == CGDIR_OK; ++ci) {
-            if (ci > 0 && cand[ci] == cand[0]) continue;
+        for (int ci = 0; ci < 4 && rc == CGDIR_OK; ++ci) {
+            bool seen = false;
+            for (int cj = 0; cj < ci; ++cj) seen = seen || cand[cj] == cand[ci];
+            if (seen) continue;
             float ms = 0.f;
             rc = time_ms(ctx, e0, e1, reps, &ms, [&](cudaStream_t st) { return launch_force(a, cand[ci], nullptr, st, kerr(ctx)); });
             if (ci == 0) best.default_force_ms = ms;
@@ -181,25 +199,36 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     if (rc == CGDIR_OK) {
         float bt = 1e30f;
         const int d = smooth_default_zchunk(nx, ny, nz, 3);
-        SmoothChoice cand[6];
+        SmoothChoice cand[7];
         int nc = 0;
         if (nx % 4 == 0) {
-            cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = d;
-            if (std::max(1, d / 2) != d) { cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = std::max(1, d / 2); }
-            if (std::min(nz, 2 * d) != d) { cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = std::min(nz, 2 * d); }
+            // z chunks: the default, half, double and four times (longer
+            // chunks reload fewer halo planes; shorter ones fill more SMs)
+            const int zs[4] = {d, std::max(1, d / 2), std::min(nz, 2 * d), std::min(nz, 4 * d)};
+            for (int q = 0; q < 4; ++q) {
+                bool seen = false;
+                for (int r = 0; r < nc; ++r) seen = seen || cand[r].zchunk == zs[q];
+                if (!seen) { cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = zs[q]; }
+            }
         }
         cand[nc].variant = SMOOTH_TILE; cand[nc++].zchunk = 0;
         cand[nc].variant = SMOOTH_SPLIT; cand[nc++].zchunk = 0;
         const SmoothChoice dflt{smooth_auto_variant(nx, ny, nz), 0};
         for (int ci = 0; ci < nc && rc == CGDIR_OK; ++ci) {
             float ms = 0.f;
-            // one iteration's smoothing: G(du) with the composite update, then G(u')
+            // one iteration: the force step (so du and the caches are as in a
+            // registration: timed alone on a level that fits in L2, the
+            // smoothing favours other z chunks), G(du) with the composite
+            // update, then G(u'); the force step's own time is taken off
             rc = time_ms(ctx, e0, e1, reps, &ms, [&](cudaStream_t st) {
-                cudaError_t e = launch_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, sscr, nullptr, st,
-                                                      kerr(ctx), false, cand[ci]);
+                cudaError_t e = launch_force(a, best.force_zchunk, nullptr, st, kerr(ctx));
+                if (e != cudaSuccess) return e;
+                e = launch_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, sscr, nullptr, st, kerr(ctx),
+                                          false, cand[ci]);
                 if (e != cudaSuccess) return e;
                 return launch_smooth(out, 3, sigma, nx, ny, nz, du, nullptr, st, kerr(ctx), cand[ci], sscr);
             });
+            ms = std::max(ms - best.force_ms, 0.f);
             const bool is_default = cand[ci].variant == dflt.variant &&
                                     (cand[ci].variant == SMOOTH_TILE || cand[ci].zchunk == d);
             if (is_default) best.default_smooth_ms = ms;
@@ -219,12 +248,15 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
         float f2 = 0.f, fs = 0.f;
         rc = time_ms(ctx, e0, e1, reps, &f2,
                      [&](cudaStream_t st) { return launch_force(a2, best.force_zchunk, nullptr, st, kerr(ctx)); });
-        if (rc == CGDIR_OK)
+        if (rc == CGDIR_OK)    // timed after the stencil pass, as in an iteration
             rc = time_ms(ctx, e0, e1, reps, &fs, [&](cudaStream_t st) {
-                cudaError_t e = launch_fused_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, nullptr, kerr(ctx), st);
+                cudaError_t e = launch_force(a2, best.force_zchunk, nullptr, st, kerr(ctx));
+                if (e != cudaSuccess) return e;
+                e = launch_fused_smooth_compose(du, u, CGDIR_COMPOSE, sigma, nx, ny, nz, out, nullptr, kerr(ctx), st);
                 if (e != cudaSuccess) return e;
                 return launch_fused_smooth_warp(out, sigma, u, a2, kerr(ctx), st);
             });
+        fs = std::max(fs - f2, 0.f);
         if (rc == CGDIR_OK && f2 + fs < best.force_ms + best.smooth_ms) {
             best.fused = 1;
             best.fused_smooth_ms = fs;

@@ -103,7 +103,8 @@ struct ForceArgs {
     float *wfield;
     uint16_t *wstate;
     float *pfield;
-    int single_voxel;             // 1: pass 2 takes one voxel per thread even for even nx
+    int pass2_width;              // voxels per thread in pass 2: 1 or 2 (at most), 0 = the
+                                  // widest the shape and the fields' alignment allow
     int skip_warp;                // 1: pass 1's outputs are already current for u (the fused
                                   // smoothing + warp kernel wrote them): launch pass 2 only
 };
@@ -190,6 +191,7 @@ int smooth_auto_variant(int nx, int ny, int nz);
 struct SmoothChoice {
     int variant = SMOOTH_AUTO;
     int zchunk = 0;
+    int ctas_per_sm = 0;          // at most this many wide z-march CTAs per SM (0: no cap)
 };
 int smooth_default_zchunk(int nx, int ny, int nz, int ncomp);
 // err: device word set to 1 if a bounded wait inside the kernel ran out;

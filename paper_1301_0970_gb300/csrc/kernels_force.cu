@@ -410,31 +410,38 @@ __device__ __forceinline__ float p_at_l2(const ForceArgs &a, int j, int N, int i
     return ((andb >> j) & 1u) ? w + a.offset : 0.f;
 }
 
-// Eq. 7 at one voxel from its 7-point stencil of I0~ (w0 centre; x-, x+,
-// y-, y+, z-, z+ neighbours) and corner-bit words, the static image T and
-// bits sb; i* are the stencil points' indices (for the stored P_j).  Every
-// multiply-add is written out (no compiler contraction), so the result does
-// not depend on where this function is inlined.
+// As force_voxel below, with the stencil's corner-bit AND (A) and OR (O)
+// over its seven points already formed by the caller.
 template <bool CONTOUR, bool L2ONLY = false>
-__device__ __forceinline__ void force_voxel(const ForceArgs &a, const ContourTables &tab, int N, float w0, float Wxm,
-                                            float Wxp, float Wym, float Wyp, float Wm, float Wp, float T, unsigned Sc,
-                                            unsigned Sxm, unsigned Sxp, unsigned Sym, unsigned Syp, unsigned Sm,
-                                            unsigned Sp, unsigned sb, int ic, int ixm, int ixp, int iym, int iyp,
-                                            int im, int ip, float &dux, float &duy, float &duz, float &r0) {
+__device__ __forceinline__ void force_voxel_ao(const ForceArgs &a, const ContourTables &tab, int N, float w0,
+                                               float Wxm, float Wxp, float Wym, float Wyp, float Wm, float Wp,
+                                               float T, unsigned A, unsigned O, unsigned Sc, unsigned Sxm,
+                                               unsigned Sxp, unsigned Sym, unsigned Syp, unsigned Sm, unsigned Sp,
+                                               unsigned sb, int ic, int ixm, int ixp, int iym, int iyp, int im,
+                                               int ip, float &dux, float &duy, float &duz, float &r0) {
     const float off = a.offset;
     const float gxv = 0.5f * (Wxp - Wxm), gyv = 0.5f * (Wyp - Wym), gzv = 0.5f * (Wp - Wm);
     r0 = T - w0;
     const float g2 = fmaf(gzv, gzv, fmaf(gyv, gyv, __fmul_rn(gxv, gxv)));
     dux = 0.f; duy = 0.f; duz = 0.f;
-    if (g2 == 0.f) return;
-    const float inv = g2 > 1e-30f ? rsqrtf(g2) : 1.f / sqrtf(g2);
+    // a vanishing gradient gives no force; below |g|^2 = 1e-30 (far below
+    // the rounding of any image value) the gradient counts as vanishing, so
+    // the reciprocal root never meets a subnormal argument
+    if (!(g2 > 1e-30f)) return;
+    const float inv = rsqrtf(g2);
     const float gn = __fmul_rn(g2, inv);
     const float nxv = __fmul_rn(gxv, inv), nyv = __fmul_rn(gyv, inv), nzv = __fmul_rn(gzv, inv);
     float num = __fmul_rn(gn, r0), den = __fmul_rn(gn, gn);
-    if (CONTOUR) {
+    if (CONTOUR && (O | sb) == 0u) {
+        // no structure at any corner of the stencil nor at the static voxel:
+        // every table entry below is entry 0 (all sums zero) but lam[all],
+        // and the multiply-adds of zero sums change nothing, so this is the
+        // same arithmetic without the lookups
+        const float c1 = 1.f + tab.lam[(1u << a.k) - 1u];
+        num = __fmul_rn(gn, __fmul_rn(r0, c1));
+        den = __fmul_rn(__fmul_rn(gn, gn), c1);
+    } else if (CONTOUR) {
         const float Toff = T + off;
-        const unsigned A = (Sc & Sxm & Sxp & Sym & Syp & Sm & Sp) >> 8;
-        const unsigned O = (Sc | Sxm | Sxp | Sym | Syp | Sm | Sp) & 0xffu;
         const unsigned kmask = (1u << a.k) - 1u;
         unsigned mixed = O & ~A & kmask;
         {
@@ -468,6 +475,23 @@ __device__ __forceinline__ void force_voxel(const ForceArgs &a, const ContourTab
     }
     const float v = __fdividef(num, fmaf(r0, r0, den));
     dux = __fmul_rn(v, nxv); duy = __fmul_rn(v, nyv); duz = __fmul_rn(v, nzv);
+}
+
+// Eq. 7 at one voxel from its 7-point stencil of I0~ (w0 centre; x-, x+,
+// y-, y+, z-, z+ neighbours) and corner-bit words, the static image T and
+// bits sb; i* are the stencil points' indices (for the stored P_j).  Every
+// multiply-add is written out (no compiler contraction), so the result does
+// not depend on where this function is inlined.
+template <bool CONTOUR, bool L2ONLY = false>
+__device__ __forceinline__ void force_voxel(const ForceArgs &a, const ContourTables &tab, int N, float w0, float Wxm,
+                                            float Wxp, float Wym, float Wyp, float Wm, float Wp, float T, unsigned Sc,
+                                            unsigned Sxm, unsigned Sxp, unsigned Sym, unsigned Syp, unsigned Sm,
+                                            unsigned Sp, unsigned sb, int ic, int ixm, int ixp, int iym, int iyp,
+                                            int im, int ip, float &dux, float &duy, float &duz, float &r0) {
+    const unsigned A = CONTOUR ? (Sc & Sxm & Sxp & Sym & Syp & Sm & Sp) >> 8 : 0u;
+    const unsigned O = CONTOUR ? (Sc | Sxm | Sxp | Sym | Syp | Sm | Sp) & 0xffu : 0u;
+    force_voxel_ao<CONTOUR, L2ONLY>(a, tab, N, w0, Wxm, Wxp, Wym, Wyp, Wm, Wp, T, A, O, Sc, Sxm, Sxp, Sym, Syp, Sm,
+                                    Sp, sb, ic, ixm, ixp, iym, iyp, im, ip, dux, duy, duz, r0);
 }
 
 // Loads of one plane of pass 2 for one thread's column.  T0 stays raw (its
@@ -711,6 +735,166 @@ __global__ void __launch_bounds__(NT, 2) k_force_pass2(ForceArgs a, int zchunk) 
             if (cur.ur & 0xffu) { ssd = fmaf(r00, r00, ssd); cnt += 1; }
             if (cur.ur >> 8) { ssd = fmaf(r01, r01, ssd); cnt += 1; }
             if (MAXDU) mx = fmaxf(mx, fmaxf(d0x * d0x + d0y * d0y + d0z * d0z, d1x * d1x + d1y * d1y + d1z * d1z));
+            Wm = Wc; Wc = cur.wp; im = ic;
+            Sm = Sc; Sc = cur.sp;
+            ++z;
+            ic += nxy;
+        };
+        for (; z + 1 < ze;) {
+            step(bufA, bufB);
+            step(bufB, bufA);
+        }
+        if (z < ze) step(bufA, bufB);
+    }
+    if (a.partial) {
+        block_partial<NT>(ssd, cnt, sqrtf(mx), a.partial,
+                          (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+        if (a.fin.done) finish_if_last(a.partial, gridDim.x * gridDim.y * gridDim.z, a.fin);
+    }
+}
+
+
+// Pass 2 with four voxels per thread (columns x .. x+3; x a multiple of 4):
+// the stencil loads of I0~ and of the corner-bit words, the static-side
+// loads and the du stores are 16-, 8- or 4-byte vectors, so a voxel takes a
+// quarter of the one-voxel pass's load and address instructions.  Needs nx
+// % 4 == 0 and 16-byte aligned fields (checked by the launcher).  The
+// per-voxel arithmetic is force_voxel_ao, so the bits equal the other passes'.
+struct PlaneLoads4 {
+    float4 wp, wym, wyp;       // I0~ at z+1, y-1, y+1
+    float wxm, wxp;            // I0~ at x-1 and x+4 (clamped)
+    float4 t;                  // T0 (float images)
+    uint2 t16;                 // T0, raw (16-bit images; converted at use)
+    uint2 sp, sym, syp;        // corner-bit words (two per 32-bit half: low half the even voxel)
+    unsigned sxm, sxp;         // corner-bit words at x-1 and x+4
+    unsigned sb, ur;           // static bits / UROI bytes of the four voxels
+};
+
+template <bool CONTOUR, typename IT>
+__device__ __forceinline__ void plane_load4(const ForceArgs &a, int ic, int ip, int oxm, int oxp, int oym, int oyp,
+                                            PlaneLoads4 &L) {
+    const float *__restrict__ W = a.wfield;
+    L.wp = __ldg(reinterpret_cast<const float4 *>(W + ip));
+    L.wym = __ldg(reinterpret_cast<const float4 *>(W + ic + oym));
+    L.wyp = __ldg(reinterpret_cast<const float4 *>(W + ic + oyp));
+    L.wxm = __ldg(W + ic + oxm);
+    L.wxp = __ldg(W + ic + oxp);
+    if (sizeof(IT) == 2) {
+        L.t16 = __ldg(reinterpret_cast<const uint2 *>(static_cast<const IT *>(a.T0) + ic));
+        L.t = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        L.t = __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(a.T0) + ic));
+        L.t16 = make_uint2(0u, 0u);
+    }
+    L.ur = a.uroi ? __ldg(reinterpret_cast<const unsigned *>(a.uroi + ic)) : 0x01010101u;
+    if (CONTOUR) {
+        const uint16_t *__restrict__ S = a.wstate;
+        L.sp = __ldg(reinterpret_cast<const uint2 *>(S + ip));
+        L.sym = __ldg(reinterpret_cast<const uint2 *>(S + ic + oym));
+        L.syp = __ldg(reinterpret_cast<const uint2 *>(S + ic + oyp));
+        L.sxm = __ldg(S + ic + oxm);
+        L.sxp = __ldg(S + ic + oxp);
+        L.sb = __ldg(reinterpret_cast<const unsigned *>(a.sbits + ic));
+    } else {
+        L.sp = L.sym = L.syp = make_uint2(0u, 0u);
+        L.sxm = L.sxp = L.sb = 0u;
+    }
+}
+
+// T0 of the four voxels of a plane load.
+template <typename IT>
+__device__ __forceinline__ float4 t_quad(const PlaneLoads4 &L) {
+    return make_float4(from_raw16<IT>(L.t16.x & 0xffffu), from_raw16<IT>(L.t16.x >> 16),
+                       from_raw16<IT>(L.t16.y & 0xffffu), from_raw16<IT>(L.t16.y >> 16));
+}
+template <>
+__device__ __forceinline__ float4 t_quad<float>(const PlaneLoads4 &L) { return L.t; }
+
+// The corner-bit AND (high byte of each word) and OR (low byte) over the
+// 7-point stencils of two adjacent voxels at once: c the pair's words (low
+// half the left voxel), l the word left of the pair, r the word right of it.
+__device__ __forceinline__ void pair_ao(unsigned c, unsigned l, unsigned r, unsigned ym, unsigned yp, unsigned zm,
+                                        unsigned zp, unsigned &A0, unsigned &O0, unsigned &A1, unsigned &O1) {
+    const unsigned side = (l & 0xffffu) | (r << 16);
+    const unsigned swap = __byte_perm(c, 0u, 0x1032);
+    const unsigned Ap = c & ym & yp & zm & zp & side & swap;
+    const unsigned Op = c | ym | yp | zm | zp | side | swap;
+    A0 = (Ap >> 8) & 0xffu; A1 = Ap >> 24;
+    O0 = Op & 0xffu; O1 = (Op >> 16) & 0xffu;
+}
+
+template <bool CONTOUR, typename IT, bool MAXDU>
+__global__ void __launch_bounds__(NT, 2) k_force_pass4(ForceArgs a, int zchunk) {
+    if (a.stop_flag && *a.stop_flag) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = 4 * (blockIdx.x * TX + threadIdx.x), y = blockIdx.y * TY + threadIdx.y;
+    const int nxy = nx * ny, N = nxy * nz;
+    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
+    float ssd = 0.f, mx = 0.f;
+    int cnt = 0;
+    __shared__ ContourTables tab;
+    if (CONTOUR) {
+        build_tables(a, tab, threadIdx.y * TX + threadIdx.x);
+        __syncthreads();
+    }
+    if (x < nx && y < ny) {
+        float *__restrict__ du = a.du;
+        const int col = y * nx + x;
+        const int oxm = x > 0 ? -1 : 0, oxp = x + 4 < nx ? 4 : 3;
+        const int oym = y > 0 ? -nx : 0, oyp = y < ny - 1 ? nx : 0;
+        int ic = zb * nxy + col;
+        int im = (zb > 0 ? zb - 1 : 0) * nxy + col;
+        float4 Wm = __ldg(reinterpret_cast<const float4 *>(a.wfield + im));
+        float4 Wc = __ldg(reinterpret_cast<const float4 *>(a.wfield + ic));
+        uint2 Sm = make_uint2(0u, 0u), Sc = make_uint2(0u, 0u);
+        if (CONTOUR) {
+            Sm = __ldg(reinterpret_cast<const uint2 *>(a.wstate + im));
+            Sc = __ldg(reinterpret_cast<const uint2 *>(a.wstate + ic));
+        }
+        PlaneLoads4 bufA, bufB;
+        plane_load4<CONTOUR, IT>(a, ic, zb < nz - 1 ? ic + nxy : ic, oxm, oxp, oym, oyp, bufA);
+        int z = zb;
+        auto step = [&](const PlaneLoads4 &cur, PlaneLoads4 &nxt) {
+            const int ip = z < nz - 1 ? ic + nxy : ic;
+            if (z + 1 < ze)
+                plane_load4<CONTOUR, IT>(a, ic + nxy, z + 1 < nz - 1 ? ic + 2 * nxy : ic + nxy, oxm, oxp, oym, oyp,
+                                         nxt);
+            if (a.warped) *reinterpret_cast<float4 *>(a.warped + ic) = Wc;
+            unsigned A[4] = {0u, 0u, 0u, 0u}, O[4] = {0u, 0u, 0u, 0u};
+            if (CONTOUR) {
+                pair_ao(Sc.x, cur.sxm, Sc.y, cur.sym.x, cur.syp.x, Sm.x, cur.sp.x, A[0], O[0], A[1], O[1]);
+                pair_ao(Sc.y, Sc.x >> 16, cur.sxp, cur.sym.y, cur.syp.y, Sm.y, cur.sp.y, A[2], O[2], A[3], O[3]);
+            }
+            const float4 T = t_quad<IT>(cur);
+            const float w[6] = {cur.wxm, Wc.x, Wc.y, Wc.z, Wc.w, cur.wxp};
+            const float wm[4] = {Wm.x, Wm.y, Wm.z, Wm.w}, wp[4] = {cur.wp.x, cur.wp.y, cur.wp.z, cur.wp.w};
+            const float wym[4] = {cur.wym.x, cur.wym.y, cur.wym.z, cur.wym.w};
+            const float wyp[4] = {cur.wyp.x, cur.wyp.y, cur.wyp.z, cur.wyp.w};
+            const float tv[4] = {T.x, T.y, T.z, T.w};
+            // corner-bit words of x-1 .. x+4, and of the y / z neighbours
+            const unsigned sw[6] = {cur.sxm & 0xffffu, Sc.x & 0xffffu, Sc.x >> 16, Sc.y & 0xffffu, Sc.y >> 16,
+                                    cur.sxp & 0xffffu};
+            const unsigned sym[4] = {cur.sym.x & 0xffffu, cur.sym.x >> 16, cur.sym.y & 0xffffu, cur.sym.y >> 16};
+            const unsigned syp[4] = {cur.syp.x & 0xffffu, cur.syp.x >> 16, cur.syp.y & 0xffffu, cur.syp.y >> 16};
+            const unsigned smw[4] = {Sm.x & 0xffffu, Sm.x >> 16, Sm.y & 0xffffu, Sm.y >> 16};
+            const unsigned spw[4] = {cur.sp.x & 0xffffu, cur.sp.x >> 16, cur.sp.y & 0xffffu, cur.sp.y >> 16};
+            float dx[4], dy[4], dz[4], r[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int xm = q == 0 ? ic + oxm : ic + q - 1, xp = q == 3 ? ic + oxp : ic + q + 1;
+                force_voxel_ao<CONTOUR>(a, tab, N, w[q + 1], w[q], w[q + 2], wym[q], wyp[q], wm[q], wp[q], tv[q],
+                                        A[q], O[q], sw[q + 1], sw[q], sw[q + 2], sym[q], syp[q], smw[q], spw[q],
+                                        (cur.sb >> (8 * q)) & 0xffu, ic + q, xm, xp, ic + q + oym, ic + q + oyp,
+                                        im + q, ip + q, dx[q], dy[q], dz[q], r[q]);
+            }
+            *reinterpret_cast<float4 *>(du + ic) = make_float4(dx[0], dx[1], dx[2], dx[3]);
+            *reinterpret_cast<float4 *>(du + N + ic) = make_float4(dy[0], dy[1], dy[2], dy[3]);
+            *reinterpret_cast<float4 *>(du + N + N + ic) = make_float4(dz[0], dz[1], dz[2], dz[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((cur.ur >> (8 * q)) & 0xffu) { ssd = fmaf(r[q], r[q], ssd); cnt += 1; }
+                if (MAXDU) mx = fmaxf(mx, dx[q] * dx[q] + dy[q] * dy[q] + dz[q] * dz[q]);
+            }
             Wm = Wc; Wc = cur.wp; im = ic;
             Sm = Sc; Sc = cur.sp;
             ++z;
@@ -1277,7 +1461,14 @@ __global__ void __launch_bounds__(FT) k_finalize(const double *__restrict__ part
 // z chunk of the force kernels: enough CTAs for about two waves of 4
 // resident CTAs per SM; a chunk re-warps 2 halo planes, so big volumes keep
 // long chunks and small ones get short, parallel marches.
+// Where pass 2 takes four voxels per thread (nx % 4 == 0) its CTAs cover
+// 128 x 8 columns at 2 per SM: about four waves of them, but at least 4
+// planes (each chunk also reads the planes on either side).  512x512x160:
+// 32 planes, 491 us per force step against 525 us with 80-plane chunks (the
+// one-voxel pass's default, 1.7 waves of quad CTAs).
 int force_default_zchunk(int nx, int ny, int nz) {
+    if (nx % 4 == 0)
+        return std::max(std::min(4, nz), pick_zchunk(nz, (long)((nx / 4 + TX - 1) / TX) * ((ny + TY - 1) / TY), 2, 4));
     return pick_zchunk(nz, (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY), 4, 2);
 }
 
@@ -1291,6 +1482,18 @@ size_t force_partial_count(int nx, int ny, int nz, int zchunk) {
     return (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + zchunk - 1) / zchunk);
 }
 
+// Pass 2 takes four voxels per thread where nx % 4 == 0 and every field it
+// reads or writes with vectors is aligned for them.
+// (512x512x160, contour terms on: 525 against 548 us per force step with
+// FP32 images, 482 against 507 with FP16, from twice the bytes in flight per
+// thread at the same 2 CTAs per SM.)
+static bool pass2_quad(const ForceArgs &a) {
+    auto al = [](const void *p, unsigned b) { return p == nullptr || ((uintptr_t)p & (b - 1)) == 0; };
+    const unsigned tb = a.img_dtype == CGDIR_F32 ? 16u : 8u;
+    return a.nx % 4 == 0 && a.pass2_width == 0 && al(a.wfield, 16) && al(a.wstate, 8) && al(a.T0, tb) &&
+           al(a.du, 16) && al(a.warped, 16) && al(a.uroi, 4) && al(a.sbits, 4);
+}
+
 template <typename IT>
 static cudaError_t launch_force_t(const ForceArgs &a, int zchunk, dim3 grid, dim3 block, cudaStream_t s,
                                   int *err) {
@@ -1301,15 +1504,18 @@ static cudaError_t launch_force_t(const ForceArgs &a, int zchunk, dim3 grid, dim
         dim3 g(grid.x, grid.y, (a.nz + zc - 1) / zc);
         // pass 2 marches the caller's (longer) z chunks: fewer CTAs, so fewer
         // end-of-block fences before the fused reduction
-        const bool paired = a.nx % 2 == 0 && !a.single_voxel;
-        dim3 g2 = paired ? dim3((a.nx / 2 + TX - 1) / TX, grid.y, grid.z) : grid;
+        const bool quad = pass2_quad(a);
+        const bool paired = a.nx % 2 == 0 && a.pass2_width != 1;
+        dim3 g2 = quad ? dim3((a.nx / 4 + TX - 1) / TX, grid.y, grid.z)
+                       : paired ? dim3((a.nx / 2 + TX - 1) / TX, grid.y, grid.z) : grid;
         const bool warp = !a.skip_warp;
         // max |du| is reported by the primitive only (a registration's fused
         // reduction keeps the RMS-ID sums alone)
         const bool maxdu = a.partial != nullptr && (a.fin.done == nullptr || a.fin.stats_out != nullptr);
 #define CGDIR_PASS2(C, M)                                                        \
     do {                                                                         \
-        if (paired) k_force_pass2<C, IT, M><<<g2, block, 0, s>>>(a, zchunk);     \
+        if (quad) k_force_pass4<C, IT, M><<<g2, block, 0, s>>>(a, zchunk);       \
+        else if (paired) k_force_pass2<C, IT, M><<<g2, block, 0, s>>>(a, zchunk);\
         else k_force_pass<C, IT, M><<<grid, block, 0, s>>>(a, zchunk);           \
     } while (0)
         if (contour) {
@@ -1362,9 +1568,11 @@ cudaError_t launch_force(const ForceArgs &a, int zchunk, int *nblocks_out, cudaS
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + zchunk - 1) / zchunk);
     dim3 block(TX, TY);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
-    if (nblocks_out && a.wfield != nullptr && (size_t)a.nx * a.ny * a.nz < (size_t)1 << 31 && a.nx % 2 == 0 &&
-        !a.single_voxel)
-        *nblocks_out = (int)(((a.nx / 2 + TX - 1) / TX) * grid.y * grid.z);   // paired pass 2
+    if (nblocks_out && a.wfield != nullptr && (size_t)a.nx * a.ny * a.nz < (size_t)1 << 31) {
+        if (pass2_quad(a)) *nblocks_out = (int)(((a.nx / 4 + TX - 1) / TX) * grid.y * grid.z);
+        else if (a.nx % 2 == 0 && a.pass2_width != 1)
+            *nblocks_out = (int)(((a.nx / 2 + TX - 1) / TX) * grid.y * grid.z);   // paired pass 2
+    }
 
     if (a.img_dtype == CGDIR_F16) return launch_force_t<__half>(a, zchunk, grid, block, s, err);
     if (a.img_dtype == CGDIR_BF16) return launch_force_t<__nv_bfloat16>(a, zchunk, grid, block, s, err);

@@ -946,7 +946,8 @@ static int wide_default_zchunk(int nx, int ny, int nz, int ncomp) {
 // The wide-tile z-march for one component per CTA (nx % 8 == 0, R <= 4).
 template <int R>
 static cudaError_t smooth_wide_r(const float *in, float *out, int ncomp, const Taps &t, int nx, int ny, int nz,
-                                 const int *stop_flag, int *err, cudaStream_t s, bool *launched, int zc_override) {
+                                 const int *stop_flag, int *err, cudaStream_t s, bool *launched, int zc_override,
+                                 int cap) {
     using G = WideGeom<R>;
     CUtensorMap m;
     const uint64_t dims[4] = {(uint64_t)nx, (uint64_t)ny, (uint64_t)nz, (uint64_t)ncomp};
@@ -957,7 +958,8 @@ static cudaError_t smooth_wide_r(const float *in, float *out, int ncomp, const T
     const int nchunks = (nz + zc - 1) / zc;
     dim3 grid((nx + WX - 1) / WX, (ny + WY - 1) / WY, nchunks * ncomp), block(TX, TY);
     constexpr int PB = 1;       // planes per barrier: 2 to 4 measured slower (more x-pass buffers)
-    const size_t smem = G::bytes(PB);
+    // a cap on CTAs per SM is a shared-memory request above 1/(cap+1) of the SM's 228 KB
+    const size_t smem = std::max(G::bytes(PB), cap > 0 ? (size_t)(228 << 10) / (cap + 1) + 1024 : (size_t)0);
     cudaError_t e = ensure_smem((const void *)k_smooth_wide<R, PB>, smem);
     if (e != cudaSuccess) return e;
     k_smooth_wide<R, PB><<<grid, block, smem, s>>>(m, out, t, nx, ny, nz, zc, stop_flag, err);
@@ -967,14 +969,15 @@ static cudaError_t smooth_wide_r(const float *in, float *out, int ncomp, const T
 }
 
 static cudaError_t smooth_wide(const float *in, float *out, int ncomp, const Taps &t, int nx, int ny, int nz,
-                               const int *stop_flag, int *err, cudaStream_t s, bool *launched, int zc = 0) {
+                               const int *stop_flag, int *err, cudaStream_t s, bool *launched, int zc = 0,
+                               int cap = 0) {
     *launched = false;
     if (nx % 8 != 0) return cudaSuccess;
     switch (t.r) {
-        case 1: return smooth_wide_r<1>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
-        case 2: return smooth_wide_r<2>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
-        case 3: return smooth_wide_r<3>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
-        case 4: return smooth_wide_r<4>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc);
+        case 1: return smooth_wide_r<1>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc, cap);
+        case 2: return smooth_wide_r<2>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc, cap);
+        case 3: return smooth_wide_r<3>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc, cap);
+        case 4: return smooth_wide_r<4>(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, launched, zc, cap);
         default: return cudaSuccess;
     }
 }
@@ -1104,7 +1107,8 @@ cudaError_t launch_smooth(const float *in, int ncomp, float sigma, int nx, int n
             return smooth_split(in, nullptr, 0, false, ncomp, t, nx, ny, nz, out, scratch, ch.zchunk, stop_flag, s);
         bool launched = false;
         if (variant != SMOOTH_MARCH_NARROW) {      // the wide-tile z-march where it applies
-            cudaError_t e = smooth_wide(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched, ch.zchunk);
+            cudaError_t e = smooth_wide(in, out, ncomp, t, nx, ny, nz, stop_flag, err, s, &launched, ch.zchunk,
+                                        ch.ctas_per_sm);
             if (e != cudaSuccess || launched) return e;
         }
         cudaError_t e =

@@ -205,7 +205,7 @@ int fill_force_args(cgdir_ctx *ctx, ForceArgs &a, int k, const float *lambda, co
             return fail(ctx, CGDIR_EINVAL, "sign must be +1 or -1 for the primitives");
         a.half_sign[j] = sign ? 0.5f * (float)sign[j] : 0.5f;
     }
-    a.single_voxel = ctx->force_single ? 1 : 0;
+    a.pass2_width = ctx->force_width;
     return CGDIR_OK;
 }
 
@@ -318,8 +318,12 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     const char *kern = std::getenv("CGDIR_KERNELS");
     c->plain_kernels = kern && std::strcmp(kern, "plain") == 0;
     c->fused_force = kern && std::strcmp(kern, "fused") == 0;
-    const char *fsv = std::getenv("CGDIR_FORCE_SINGLE");
-    c->force_single = fsv && std::strcmp(fsv, "1") == 0;
+    const char *ssch = std::getenv("CGDIR_SERVE_SCHEDULE");
+    c->serve_schedule = !ssch ? 2 : std::strcmp(ssch, "shared") == 0 ? 0 : std::strcmp(ssch, "alone") == 0 ? 1 : 2;
+    const char *swc = std::getenv("CGDIR_SHARED_WIDE_CAP");
+    if (swc) c->shared_wide_cap = std::atoi(swc);
+    const char *fw = std::getenv("CGDIR_FORCE_WIDTH");
+    c->force_width = fw && (std::strcmp(fw, "1") == 0 || std::strcmp(fw, "2") == 0) ? std::atoi(fw) : 0;
     const char *fz = std::getenv("CGDIR_FORCE_ZCHUNK");
     c->force_zchunk = fz ? std::atoi(fz) : 0;
     const char *sz = std::getenv("CGDIR_SMOOTH_ZCHUNK");

@@ -100,7 +100,10 @@ struct cgdir_ctx {
     bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
     bool fused_force = false;     // CGDIR_KERNELS=fused: one-pass TMA force kernel instead of two passes
     int smooth_variant = 0;       // SMOOTH_AUTO / MARCH / TILE (CGDIR_SMOOTH=auto|march|tile)
-    bool force_single = false;    // CGDIR_FORCE_SINGLE=1: force pass 2 one voxel per thread
+    int serve_schedule = 2;       // served requests' schedule (CGDIR_SERVE_SCHEDULE=shared|alone|auto:
+                                  // 0|1|2): auto takes the latency one when nothing else is running
+    int shared_wide_cap = 2;      // CGDIR_SHARED_WIDE_CAP=n: wide z-march CTAs per SM in batches (0: no cap)
+    int force_width = 0;          // CGDIR_FORCE_WIDTH=1|2: force pass 2 voxels per thread (0: widest)
     int force_zchunk = 0;         // CGDIR_FORCE_ZCHUNK: force-pass z chunk for every level (0 = tuned / default)
     int smooth_zchunk = 0;        // CGDIR_SMOOTH_ZCHUNK: z-march smoothing z chunk (0 = tuned / default)
     long coop_max_voxels = 0;     // levels below the finest with at most this many voxels run

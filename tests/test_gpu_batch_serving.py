@@ -317,16 +317,17 @@ def test_smoothing_variants_give_the_same_registration(variant):
 
 @pytest.mark.parametrize("contour", [True, False])
 def test_force_pass_variants_agree_bitwise(contour):
-    """Pass 2 with one voxel per thread and with two, at several z chunks:
+    """Pass 2 with one, two and four voxels per thread, at several z chunks:
     the same du, bit for bit (the per-voxel arithmetic is one function with
-    every multiply-add written out)."""
+    every multiply-add written out); the RMS-ID sums agree to rounding."""
     c = phantom.make_case("headneck256", shape=(20, 48, 64))
     bits = lambda m: dev(np.bitwise_or.reduce([(x.astype(np.uint8) << j) for j, x in enumerate(m)], axis=0))
     I0, T0, mb, sb = dev(c.moving), dev(c.static), bits(c.moving_masks), bits(c.static_masks)
     u = dev((0.5 * c.u_gt).astype(np.float32))
     outs = []
-    for env in ({"CGDIR_FORCE_SINGLE": "1", "CGDIR_FORCE_ZCHUNK": "1"}, {"CGDIR_FORCE_SINGLE": "1", "CGDIR_FORCE_ZCHUNK": "5"},
-                {"CGDIR_FORCE_SINGLE": "0", "CGDIR_FORCE_ZCHUNK": "1"}, {"CGDIR_FORCE_SINGLE": "0", "CGDIR_FORCE_ZCHUNK": "4"}):
+    for env in ({"CGDIR_FORCE_WIDTH": "1", "CGDIR_FORCE_ZCHUNK": "1"}, {"CGDIR_FORCE_WIDTH": "1", "CGDIR_FORCE_ZCHUNK": "5"},
+                {"CGDIR_FORCE_WIDTH": "2", "CGDIR_FORCE_ZCHUNK": "1"}, {"CGDIR_FORCE_WIDTH": "2", "CGDIR_FORCE_ZCHUNK": "4"},
+                {"CGDIR_FORCE_ZCHUNK": "1"}, {"CGDIR_FORCE_ZCHUNK": "3"}):
         ctx = _ctx_with_env(env)
         try:
             du, st = ctx.force(I0, T0, mb, sb, c.lam, c.signs, u, contour=contour, want_stats=True)
