@@ -479,12 +479,12 @@ def run_cgdir(args):
     fine = {p["kernel"]: p for p in prof if p["level"] == L - 1 and p["launches"]}
     fine_variant = next((t["smooth"] for t in tuning if tuple(t["shape"]) == tuple(host.shape)), None)
     roofline, roofline_force = None, None
-    if "smooth_u" in fine and fine_variant == "march":
+    if "smooth_u" in fine and fine_variant in ("march", "march32"):
         p = fine["smooth_u"]
         avg_ms = p["total_ms"] / p["launches"]
         bytes_per_launch = SMOOTH_BYTES_PER_VOXEL * N
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-        kname = "k_smooth_wide" if host.shape[2] % 8 == 0 else "k_smooth_tma"
+        kname = "k_smooth_wide" if host.shape[2] % 8 == 0 and fine_variant == "march" else "k_smooth_tma"
         roofline = {"bound": "hbm", "kernel": f"{kname} (z-march Gaussian of u, finest level; the same kernel "
                                               "also smooths du there)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -497,7 +497,9 @@ def run_cgdir(args):
         avg_ms = p["total_ms"] / p["launches"]
         bytes_per_launch = (FORCE_BYTES_PER_VOXEL if args.storage == "f32" else FORCE_BYTES_PER_VOXEL_16)[True] * N
         achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-        roofline_force = {"bound": "hbm", "kernel": "force step = k_warp_pass + k_force_pass2 (finest level, "
+        nx = host.shape[2]
+        pass2 = "k_force_pass4" if nx % 4 == 0 else "k_force_pass2" if nx % 2 == 0 else "k_force_pass"
+        roofline_force = {"bound": "hbm", "kernel": f"force step = k_warp_pass + {pass2} (finest level, "
                                                     "contour terms on)",
                           "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                           "traffic": traffic_record("force", args.workload, FORCE_SOURCES)

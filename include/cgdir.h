@@ -480,11 +480,12 @@ int cgdir_selftest_wait_timeout(cgdir_ctx *ctx, int limit_us);
                                   smooth_ms / force_ms are then those kernels' times (the
                                   per-step alternative is kept but not reported; a loaded
                                   table that says FUSED picks the per-step kernels by size) */
+#define CGDIR_SMOOTH_MARCH32 5 /* the 32 x 16 z-march where the 64 x 16 one would apply */
 typedef struct {
     int   nx, ny, nz;           /* level shape                                   */
     int   contour;              /* structure terms on at this level               */
     int   storage_dtype;        /* CGDIR_F32 / F16 / BF16                          */
-    int   smooth_variant;       /* CGDIR_SMOOTH_MARCH / _TILE / _SPLIT / _FUSED     */
+    int   smooth_variant;       /* CGDIR_SMOOTH_MARCH / _TILE / _SPLIT / _FUSED / _MARCH32 */
     int   smooth_zchunk;        /* z chunk of the z-march (0 = default / n/a)       */
     int   force_zchunk;         /* z chunk of the force stencil pass                */
     float smooth_ms, force_ms;  /* best times: steps 2-4 of one iteration; force   */

@@ -65,7 +65,7 @@ class cgdir_tuning(ctypes.Structure):
                 ("default_force_ms", c_float)]
 
 
-CGDIR_SMOOTH_MARCH, CGDIR_SMOOTH_TILE, CGDIR_SMOOTH_SPLIT, CGDIR_SMOOTH_FUSED = 1, 2, 3, 4
+CGDIR_SMOOTH_MARCH, CGDIR_SMOOTH_TILE, CGDIR_SMOOTH_SPLIT, CGDIR_SMOOTH_FUSED, CGDIR_SMOOTH_MARCH32 = 1, 2, 3, 4, 5
 
 
 class cgdir_kernel_time(ctypes.Structure):
@@ -374,7 +374,7 @@ class Context:
         buf = (cgdir_tuning * max(n, 1))()
         n = load().cgdir_tuning_read(self._h, buf, n)
         names = {CGDIR_SMOOTH_MARCH: "march", CGDIR_SMOOTH_TILE: "tile", CGDIR_SMOOTH_SPLIT: "split",
-                 CGDIR_SMOOTH_FUSED: "fused"}
+                 CGDIR_SMOOTH_FUSED: "fused", CGDIR_SMOOTH_MARCH32: "march32"}
         return [{"shape": (b.nz, b.ny, b.nx), "contour": bool(b.contour), "storage_dtype": b.storage_dtype,
                  "smooth": names.get(b.smooth_variant, str(b.smooth_variant)), "smooth_zchunk": b.smooth_zchunk,
                  "force_zchunk": b.force_zchunk, "smooth_ms": b.smooth_ms, "force_ms": b.force_ms,
@@ -390,7 +390,7 @@ class Context:
         """Install a tuning table as tuning() returns it (e.g. saved as JSON by
         an earlier process); registrations of those shapes then use it."""
         codes = {"march": CGDIR_SMOOTH_MARCH, "tile": CGDIR_SMOOTH_TILE, "split": CGDIR_SMOOTH_SPLIT,
-                 "fused": CGDIR_SMOOTH_FUSED}
+                 "fused": CGDIR_SMOOTH_FUSED, "march32": CGDIR_SMOOTH_MARCH32}
         buf = (cgdir_tuning * max(len(table), 1))()
         for b, t in zip(buf, table):
             b.nz, b.ny, b.nx = t["shape"]

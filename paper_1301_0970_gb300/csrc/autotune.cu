@@ -199,17 +199,25 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     if (rc == CGDIR_OK) {
         float bt = 1e30f;
         const int d = smooth_default_zchunk(nx, ny, nz, 3);
-        SmoothChoice cand[7];
+        SmoothChoice cand[16];
         int nc = 0;
+        auto add = [&](int variant, int zc) {
+            for (int r = 0; r < nc; ++r)
+                if (cand[r].variant == variant && cand[r].zchunk == zc) return;
+            cand[nc].variant = variant;
+            cand[nc++].zchunk = zc;
+        };
         if (nx % 4 == 0) {
-            // z chunks: the default, half, double and four times (longer
-            // chunks reload fewer halo planes; shorter ones fill more SMs)
-            const int zs[4] = {d, std::max(1, d / 2), std::min(nz, 2 * d), std::min(nz, 4 * d)};
-            for (int q = 0; q < 4; ++q) {
-                bool seen = false;
-                for (int r = 0; r < nc; ++r) seen = seen || cand[r].zchunk == zs[q];
-                if (!seen) { cand[nc].variant = SMOOTH_MARCH; cand[nc++].zchunk = zs[q]; }
-            }
+            // z chunks: the default and the volume cut into 1 .. 16 chunks
+            // (longer chunks reload fewer halo planes; more chunks fill more
+            // SMs, and the count of CTAs against whole waves decides which
+            // wins); the 32 x 16 z-march with 2, 4 and 8 chunks where the
+            // 64 x 16 one applies (more CTAs per chunk on small levels)
+            add(SMOOTH_MARCH, d);
+            const int nch[7] = {1, 2, 3, 4, 6, 8, 16};
+            for (int q = 0; q < 7; ++q) add(SMOOTH_MARCH, (nz + nch[q] - 1) / nch[q]);
+            if (nx % 8 == 0)
+                for (int c = 2; c <= 8; c *= 2) add(SMOOTH_MARCH_NARROW, (nz + c - 1) / c);
         }
         cand[nc].variant = SMOOTH_TILE; cand[nc++].zchunk = 0;
         cand[nc].variant = SMOOTH_SPLIT; cand[nc++].zchunk = 0;
@@ -341,7 +349,7 @@ int cgdir_tuning_load(cgdir_ctx *ctx, const cgdir_tuning *in, int n) {
         const cgdir_tuning &t = in[i];
         if (!dims_ok(t.nx, t.ny, t.nz) || (t.contour != 0 && t.contour != 1) || t.storage_dtype < CGDIR_F32 ||
             t.storage_dtype > CGDIR_BF16 || t.smooth_variant < CGDIR_SMOOTH_MARCH ||
-            t.smooth_variant > CGDIR_SMOOTH_FUSED || t.smooth_zchunk < 0 || t.smooth_zchunk > t.nz ||
+            t.smooth_variant > CGDIR_SMOOTH_MARCH32 || t.smooth_zchunk < 0 || t.smooth_zchunk > t.nz ||
             t.force_zchunk < 1 || t.force_zchunk > t.nz)
             return fail(ctx, CGDIR_EINVAL, "tuning_load: bad entry");
     }

@@ -186,6 +186,10 @@ cudaError_t launch_finalize(const double *partial, int nblocks, LevelState st, i
 // 32 x 16 one (same bits; a context setting for comparisons, never tuned).
 enum { SMOOTH_AUTO = 0, SMOOTH_MARCH = 1, SMOOTH_TILE = 2, SMOOTH_SPLIT = 3, SMOOTH_FUSED = 4,
        SMOOTH_MARCH_NARROW = 5 };
+static_assert(SMOOTH_MARCH == CGDIR_SMOOTH_MARCH && SMOOTH_TILE == CGDIR_SMOOTH_TILE &&
+                  SMOOTH_SPLIT == CGDIR_SMOOTH_SPLIT && SMOOTH_FUSED == CGDIR_SMOOTH_FUSED &&
+                  SMOOTH_MARCH_NARROW == CGDIR_SMOOTH_MARCH32,
+              "internal smoothing variants are the public tuning codes");
 int smooth_auto_variant(int nx, int ny, int nz);
 // Kernel choice for one smoothing launch: variant and (z-march) z chunk, 0 = default.
 struct SmoothChoice {

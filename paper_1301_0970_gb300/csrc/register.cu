@@ -702,9 +702,25 @@ int cgdir_submit(cgdir_ctx *ctx, const cgdir_volume *S, const cgdir_volume *M, c
     // admission by the device-memory budget: what this request must add
     if (ctx->budget && ctx->in_use + best > ctx->budget)
         return fail(ctx, CGDIR_EBUSY, "submit: the device-memory budget cannot admit this request now");
+    // the request's stream: ranked by age among the running requests (one
+    // submitted while n others run is n priority levels below the highest),
+    // so the device schedules the older requests' kernels first and the
+    // younger ones fill the gaps; a graph runs at the priority of the stream
+    // it is launched into
+    int prio = 0;
+    if (ctx->serve_priority) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        prio = std::min(least, greatest + running);
+    }
+    if (sl.stream && sl.own_stream && sl.priority != prio) {
+        CK(cudaStreamDestroy(sl.stream));      // idle: its last request completed
+        sl.stream = nullptr;
+    }
     if (!sl.stream) {
-        CK(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio));
         sl.own_stream = true;
+        sl.priority = prio;
     }
     if (!sl.done) CK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
     if (!sl.ready) CK(cudaEventCreateWithFlags(&sl.ready, cudaEventDisableTiming));

@@ -318,6 +318,8 @@ int cgdir_create(cgdir_ctx **out, const cgdir_config *cfg) {
     const char *kern = std::getenv("CGDIR_KERNELS");
     c->plain_kernels = kern && std::strcmp(kern, "plain") == 0;
     c->fused_force = kern && std::strcmp(kern, "fused") == 0;
+    const char *spr = std::getenv("CGDIR_SERVE_PRIORITY");
+    c->serve_priority = !(spr && std::strcmp(spr, "0") == 0);
     const char *ssch = std::getenv("CGDIR_SERVE_SCHEDULE");
     c->serve_schedule = !ssch ? 2 : std::strcmp(ssch, "shared") == 0 ? 0 : std::strcmp(ssch, "alone") == 0 ? 1 : 2;
     const char *swc = std::getenv("CGDIR_SHARED_WIDE_CAP");

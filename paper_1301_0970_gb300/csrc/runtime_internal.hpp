@@ -71,6 +71,7 @@ struct Slot {
     WsSet ws;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int priority = 0;                  // of stream (served requests: by age)
     double *h_hist = nullptr;          // pinned copies of the stop state
     int *h_meta = nullptr;
     size_t h_hist_cap = 0;
@@ -100,6 +101,7 @@ struct cgdir_ctx {
     bool plain_kernels = false;   // CGDIR_KERNELS=plain at creation: no TMA kernels
     bool fused_force = false;     // CGDIR_KERNELS=fused: one-pass TMA force kernel instead of two passes
     int smooth_variant = 0;       // SMOOTH_AUTO / MARCH / TILE (CGDIR_SMOOTH=auto|march|tile)
+    bool serve_priority = true;   // served requests' streams ranked by age (CGDIR_SERVE_PRIORITY=0: off)
     int serve_schedule = 2;       // served requests' schedule (CGDIR_SERVE_SCHEDULE=shared|alone|auto:
                                   // 0|1|2): auto takes the latency one when nothing else is running
     int shared_wide_cap = 2;      // CGDIR_SHARED_WIDE_CAP=n: wide z-march CTAs per SM in batches (0: no cap)
