@@ -542,6 +542,7 @@ def run_cgdir(args):
                                         for p in breakdown},
                 "tuning": [{"shape_zyx": list(t["shape"]), "smooth": t["smooth"],
                             "smooth_zchunk": t["smooth_zchunk"], "force_zchunk": t["force_zchunk"],
+                            "force_width": t.get("force_width", 0),
                             "smooth_ms": round(t["smooth_ms"], 4), "force_ms": round(t["force_ms"], 4),
                             "untuned_smooth_ms": round(t["default_smooth_ms"], 4),
                             "untuned_force_ms": round(t["default_force_ms"], 4)} for t in tuning]}

@@ -490,6 +490,8 @@ typedef struct {
     int   force_zchunk;         /* z chunk of the force stencil pass                */
     float smooth_ms, force_ms;  /* best times: steps 2-4 of one iteration; force   */
     float default_smooth_ms, default_force_ms;   /* the untuned choice's times     */
+    int   force_width;          /* voxels per thread of the stencil pass: 0 = the
+                                   widest the shape allows (4 where nx % 4 == 0), 2 */
 } cgdir_tuning;
 
 /* Tune every level of a `levels`-level pyramid whose finest level is

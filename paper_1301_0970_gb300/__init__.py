@@ -62,7 +62,7 @@ class cgdir_tuning(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("contour", c_int), ("storage_dtype", c_int),
                 ("smooth_variant", c_int), ("smooth_zchunk", c_int), ("force_zchunk", c_int),
                 ("smooth_ms", c_float), ("force_ms", c_float), ("default_smooth_ms", c_float),
-                ("default_force_ms", c_float)]
+                ("default_force_ms", c_float), ("force_width", c_int)]
 
 
 CGDIR_SMOOTH_MARCH, CGDIR_SMOOTH_TILE, CGDIR_SMOOTH_SPLIT, CGDIR_SMOOTH_FUSED, CGDIR_SMOOTH_MARCH32 = 1, 2, 3, 4, 5
@@ -377,7 +377,8 @@ class Context:
                  CGDIR_SMOOTH_FUSED: "fused", CGDIR_SMOOTH_MARCH32: "march32"}
         return [{"shape": (b.nz, b.ny, b.nx), "contour": bool(b.contour), "storage_dtype": b.storage_dtype,
                  "smooth": names.get(b.smooth_variant, str(b.smooth_variant)), "smooth_zchunk": b.smooth_zchunk,
-                 "force_zchunk": b.force_zchunk, "smooth_ms": b.smooth_ms, "force_ms": b.force_ms,
+                 "force_zchunk": b.force_zchunk, "force_width": b.force_width,
+                 "smooth_ms": b.smooth_ms, "force_ms": b.force_ms,
                  "default_smooth_ms": b.default_smooth_ms, "default_force_ms": b.default_force_ms}
                 for b in buf[:n]]
 
@@ -397,6 +398,7 @@ class Context:
             b.contour, b.storage_dtype = int(bool(t["contour"])), int(t["storage_dtype"])
             b.smooth_variant, b.smooth_zchunk = codes[t["smooth"]], int(t["smooth_zchunk"])
             b.force_zchunk = int(t["force_zchunk"])
+            b.force_width = int(t.get("force_width", 0))
             b.smooth_ms, b.force_ms = t["smooth_ms"], t["force_ms"]
             b.default_smooth_ms, b.default_force_ms = t["default_smooth_ms"], t["default_force_ms"]
         self._check(load().cgdir_tuning_load(self._h, buf, len(table)), "cgdir_tuning_load")

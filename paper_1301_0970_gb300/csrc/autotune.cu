@@ -98,6 +98,14 @@ bool use_level_coop(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, i
     return (long)nx * ny * nz <= ctx->coop_max_voxels;
 }
 
+// Voxels per thread of the force's stencil pass (0: the widest the shape
+// and alignment allow).
+int force_width_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
+    if (ctx->force_width > 0) return ctx->force_width;
+    if (const TunedLevel *t = find_tuned(ctx, nx, ny, nz, contour, sdt)) return t->force_width;
+    return 0;
+}
+
 // Never below force_zchunk_min: the registration's partial-sum buffer is
 // sized for that chunk (a loaded table may hold any chunk).
 int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt) {
@@ -185,16 +193,30 @@ int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int s
     {
         const int d = force_default_zchunk(nx, ny, nz);
         const int cand[4] = {d, std::max(1, d / 2), std::max(1, d / 4), std::min(nz, 2 * d)};
+        // the stencil pass's width: four voxels per thread (the default where
+        // nx % 4 == 0) or two (twice the CTAs, for small levels)
+        const int widths[2] = {0, 2};
+        const int nw = (nx % 4 == 0 && ctx->force_width == 0) ? 2 : 1;
         float bt = 1e30f;
-        for (int ci = 0; ci < 4 && rc == CGDIR_OK; ++ci) {
-            bool seen = false;
-            for (int cj = 0; cj < ci; ++cj) seen = seen || cand[cj] == cand[ci];
-            if (seen) continue;
-            float ms = 0.f;
-            rc = time_ms(ctx, e0, e1, reps, &ms, [&](cudaStream_t st) { return launch_force(a, cand[ci], nullptr, st, kerr(ctx)); });
-            if (ci == 0) best.default_force_ms = ms;
-            if (rc == CGDIR_OK && ms < bt) { bt = ms; best.force_zchunk = cand[ci]; best.force_ms = ms; }
+        for (int wi = 0; wi < nw && rc == CGDIR_OK; ++wi) {
+            a.pass2_width = ctx->force_width > 0 ? ctx->force_width : widths[wi];
+            for (int ci = 0; ci < 4 && rc == CGDIR_OK; ++ci) {
+                bool seen = false;
+                for (int cj = 0; cj < ci; ++cj) seen = seen || cand[cj] == cand[ci];
+                if (seen) continue;
+                float ms = 0.f;
+                rc = time_ms(ctx, e0, e1, reps, &ms,
+                             [&](cudaStream_t st) { return launch_force(a, cand[ci], nullptr, st, kerr(ctx)); });
+                if (wi == 0 && ci == 0) best.default_force_ms = ms;
+                if (rc == CGDIR_OK && ms < bt) {
+                    bt = ms;
+                    best.force_zchunk = cand[ci];
+                    best.force_width = widths[wi];
+                    best.force_ms = ms;
+                }
+            }
         }
+        a.pass2_width = ctx->force_width > 0 ? ctx->force_width : best.force_width;
     }
     if (rc == CGDIR_OK) {
         float bt = 1e30f;
@@ -336,6 +358,7 @@ int cgdir_tuning_read(const cgdir_ctx *ctx, cgdir_tuning *out, int cap) {
             o.smooth_ms = t.fused ? t.fused_smooth_ms : t.smooth_ms;
             o.force_ms = t.fused ? t.fused_force_ms : t.force_ms;
             o.default_smooth_ms = kv.second.default_smooth_ms; o.default_force_ms = kv.second.default_force_ms;
+            o.force_width = t.force_width;
         }
         ++n;
     }
@@ -350,7 +373,7 @@ int cgdir_tuning_load(cgdir_ctx *ctx, const cgdir_tuning *in, int n) {
         if (!dims_ok(t.nx, t.ny, t.nz) || (t.contour != 0 && t.contour != 1) || t.storage_dtype < CGDIR_F32 ||
             t.storage_dtype > CGDIR_BF16 || t.smooth_variant < CGDIR_SMOOTH_MARCH ||
             t.smooth_variant > CGDIR_SMOOTH_MARCH32 || t.smooth_zchunk < 0 || t.smooth_zchunk > t.nz ||
-            t.force_zchunk < 1 || t.force_zchunk > t.nz)
+            t.force_zchunk < 1 || t.force_zchunk > t.nz || t.force_width < 0 || t.force_width > 2)
             return fail(ctx, CGDIR_EINVAL, "tuning_load: bad entry");
     }
     for (int i = 0; i < n; ++i) {
@@ -365,6 +388,7 @@ int cgdir_tuning_load(cgdir_ctx *ctx, const cgdir_tuning *in, int n) {
             v.smooth_ms = t.smooth_ms; v.force_ms = t.force_ms;
         }
         v.force_zchunk = t.force_zchunk;
+        v.force_width = t.force_width;
         v.default_smooth_ms = t.default_smooth_ms; v.default_force_ms = t.default_force_ms;
         ctx->tuned[TuneKey{t.nx, t.ny, t.nz, t.contour, t.storage_dtype}] = v;
     }

@@ -583,8 +583,10 @@ __global__ void __launch_bounds__(NT, 2) k_smooth_wide(const __grid_constant__ C
 }
 
 // Composite update u_new = du + u(x + du) (trilinear, clamped) or u + du,
-// one voxel per thread along x-y tiles marching a few planes in z.
-__global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict__ u, const float *__restrict__ du,
+// one voxel per thread along x-y tiles marching a few planes in z.  The
+// update is bound by the latency of its 24 gathers per voxel, which resident
+// warps hide: 5 CTAs per SM (40 warps) rather than 4.
+__global__ void __launch_bounds__(NT, 5) k_compose_tiles(const float *__restrict__ u, const float *__restrict__ du,
                                                          int mode, int nx, int ny, int nz, int zc,
                                                          float *__restrict__ out, const int *stop_flag) {
     if (stop_flag && *stop_flag) return;
@@ -638,6 +640,59 @@ __global__ void __launch_bounds__(NT, 4) k_compose_tiles(const float *__restrict
         out[i] = dx + tri(cx);
         out[N + i] = dy + tri(cy);
         out[2 * N + i] = dz + tri(cz);
+    }
+}
+
+// The composite update for volumes below 2^31 voxels: the same arithmetic
+// with 32-bit indices from per-component base pointers (one multiply-add
+// per gather address, 48 registers at 5 CTAs per SM without spills).
+// 512x512x160: 313 us per launch against 345 us for the 64-bit kernel at 4
+// CTAs per SM; 6 CTAs per SM (40 registers) measured slower.
+__global__ void __launch_bounds__(NT, 5) k_compose_tiles32(const float *__restrict__ u,
+                                                                       const float *__restrict__ du, int nx, int ny,
+                                                                       int nz, int zc, float *__restrict__ out,
+                                                                       const int *stop_flag) {
+    if (stop_flag && *stop_flag) return;
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const int zb = blockIdx.z * zc, ze = min(zb + zc, nz);
+    const int nxy = nx * ny, N = nxy * nz;
+    const float *__restrict__ ux = u, *__restrict__ uy = u + N, *__restrict__ uz = uy + N;
+    const float *__restrict__ dx_ = du, *__restrict__ dy_ = du + N, *__restrict__ dz_ = dy_ + N;
+    float *__restrict__ ox = out, *__restrict__ oy = out + N, *__restrict__ oz = oy + N;
+    const float fxmax = (float)(nx - 1), fymax = (float)(ny - 1), fzmax = (float)(nz - 1);
+    int i = zb * nxy + y * nx + x;
+    float nx0 = 0.f, ny0 = 0.f, nz0 = 0.f;
+    if (zb < ze) { nx0 = __ldg(dx_ + i); ny0 = __ldg(dy_ + i); nz0 = __ldg(dz_ + i); }
+    for (int z = zb; z < ze; ++z, i += nxy) {
+        const float dx = nx0, dy = ny0, dz = nz0;
+        const float px = fminf(fmaxf((float)x + dx, 0.f), fxmax);
+        const float py = fminf(fmaxf((float)y + dy, 0.f), fymax);
+        const float pz = fminf(fmaxf((float)z + dz, 0.f), fzmax);
+        const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+        const float wx = px - fx, wy = py - fy, wz = pz - fz;
+        const int ddx = ix < nx - 1 ? 1 : 0, ddy = iy < ny - 1 ? nx : 0, ddz = iz < nz - 1 ? nxy : 0;
+        const int b0 = iz * nxy + iy * nx + ix;
+        const int o[8] = {b0, b0 + ddx, b0 + ddy, b0 + ddy + ddx, b0 + ddz, b0 + ddz + ddx, b0 + ddz + ddy,
+                          b0 + ddz + ddy + ddx};
+        float cx[8], cy[8], cz[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            cx[q] = __ldg(ux + o[q]);
+            cy[q] = __ldg(uy + o[q]);
+            cz[q] = __ldg(uz + o[q]);
+        }
+        if (z + 1 < ze) { nx0 = __ldg(dx_ + i + nxy); ny0 = __ldg(dy_ + i + nxy); nz0 = __ldg(dz_ + i + nxy); }
+        auto tri = [&](const float *c) {
+            const float e00 = fmaf(wx, c[1] - c[0], c[0]), e10 = fmaf(wx, c[3] - c[2], c[2]);
+            const float e01 = fmaf(wx, c[5] - c[4], c[4]), e11 = fmaf(wx, c[7] - c[6], c[6]);
+            const float f0 = fmaf(wy, e10 - e00, e00), f1 = fmaf(wy, e11 - e01, e01);
+            return fmaf(wz, f1 - f0, f0);
+        };
+        ox[i] = dx + tri(cx);
+        oy[i] = dy + tri(cy);
+        oz[i] = dz + tri(cz);
     }
 }
 
@@ -1146,6 +1201,11 @@ cudaError_t launch_compose(const float *u, const float *du, int mode, int nx, in
     const long tiles = (long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
     const int zc = pick_zchunk(nz, tiles, 8, 4);
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + zc - 1) / zc), block(TX, TY);
+    if (mode != CGDIR_ADDITIVE && (size_t)nx * ny * nz < ((size_t)1 << 31)) {
+        k_compose_tiles32<<<grid, block, 0, s>>>(u, du, nx, ny, nz, zc, out, stop_flag);
+        note_launch();
+        return cudaGetLastError();
+    }
     k_compose_tiles<<<grid, block, 0, s>>>(u, du, mode, nx, ny, nz, zc, out, stop_flag);
     note_launch();
     return cudaGetLastError();

@@ -344,6 +344,7 @@ int plan_enqueue(cgdir_ctx *ctx, const RegPlan &pl, cudaStream_t s, ProfList *pr
         a.contour = ((P->contour_level_mask >> l) & 1u) && k > 0;
         if (pl.fscr) force_scratch_assign(a, pl.fscr, pl.Nl[l]);
         const int zc = force_zchunk_for(ctx, lx, ly, lz, a.contour, sdt);
+        a.pass2_width = force_width_for(ctx, lx, ly, lz, a.contour, sdt);
         const SmoothChoice sch = smooth_choice(ctx, lx, ly, lz, a.contour, sdt, !pl.shared_gpu);
         const int cap = P->iters[l];
         a.fin.done = done + l;

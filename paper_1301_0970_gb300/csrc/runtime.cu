@@ -412,6 +412,7 @@ static int force_impl(cgdir_ctx *ctx, const ForceArgs &a, double *stats_host) {
     void *part = nullptr, *st = nullptr;
     ForceArgs b = a;
     const int zc = force_zchunk_for(ctx, a.nx, a.ny, a.nz, a.contour && a.k > 0, a.img_dtype);
+    b.pass2_width = force_width_for(ctx, a.nx, a.ny, a.nz, a.contour && a.k > 0, a.img_dtype);
     if (b.contour && b.k > 0 && !ctx->plain_kernels && b.mtex == nullptr) {
         // the TMA kernel gathers interleaved {I0, bits} texels
         const size_t N = (size_t)a.nx * a.ny * a.nz;

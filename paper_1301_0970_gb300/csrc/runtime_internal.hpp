@@ -53,6 +53,7 @@ struct TunedLevel {
     int smooth_variant = 0;    // best per-step smoothing: SMOOTH_MARCH / TILE / SPLIT (0 = by size)
     int smooth_zchunk = 0;     // z chunk of the z-march smoothing (0 = default)
     int force_zchunk = 0;      // z chunk of the force stencil pass (0 = default)
+    int force_width = 0;       // voxels per thread of the stencil pass: 0 = the widest, 2, 1
     float smooth_ms = 0.f, force_ms = 0.f;   // best per-step times measured
     float default_smooth_ms = 0.f, default_force_ms = 0.f;
     int fused = 0;             // the fused schedule beat the best per-step one (alone on the GPU)
@@ -191,6 +192,7 @@ int force_zchunk_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, 
 bool use_level_coop(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
 // Smallest force z chunk any tuning may choose (sizes the partial buffers).
 int force_zchunk_min(int nx, int ny, int nz);
+int force_width_for(const cgdir_ctx *ctx, int nx, int ny, int nz, int contour, int sdt);
 // Time the candidate kernels of one level shape on synthetic data and
 // record the fastest (autotune.cu).  k structures, sigma of the smoothing.
 int tune_level(cgdir_ctx *ctx, int nx, int ny, int nz, int k, int contour, int sdt, float sigma);

@@ -56,7 +56,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     compare every struct size and field offset with the ctypes mirror."""
     structs = {"cgdir_config": cg.cgdir_config, "cgdir_volume": cg.cgdir_volume,
                "cgdir_masks": cg.cgdir_masks, "cgdir_params": cg.cgdir_params,
-               "cgdir_level_stats": cg.cgdir_level_stats}
+               "cgdir_level_stats": cg.cgdir_level_stats, "cgdir_tuning": cg.cgdir_tuning,
+               "cgdir_kernel_time": cg.cgdir_kernel_time}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cgdir.h"', "int main(void){"]
     expect = []
     for name, cls in structs.items():
