@@ -209,14 +209,35 @@ def test_tuning_table_round_trip():
         b.load_tuning(tab2)
         got = b.tuning()
         key = lambda t: (tuple(t["shape"]), t["contour"], t["storage_dtype"])
-        assert sorted((key(t), t["smooth"], t["smooth_zchunk"], t["force_zchunk"]) for t in got) == \
-            sorted((key(t), t["smooth"], t["smooth_zchunk"], t["force_zchunk"]) for t in tab)
+        choice = lambda t: (key(t), t["smooth"], t["smooth_zchunk"], t["force_zchunk"], t["force_width"])
+        assert sorted(choice(t) for t in got) == sorted(choice(t) for t in tab)
         rb, _ = single(b, c, kw)
         assert torch.equal(ra, rb)
-        bad = dict(tab2[0], force_zchunk=0)
-        with pytest.raises(cg.CgdirError):
-            b.load_tuning([bad])
+        for bad in (dict(tab2[0], force_zchunk=0), dict(tab2[0], force_width=3)):
+            with pytest.raises(cg.CgdirError):
+                b.load_tuning([bad])
         assert len(b.tuning()) == len(tab)
+
+
+@pytest.mark.parametrize("smooth, force_width", [("march32", 0), ("march", 2), ("march32", 2), ("tile", 0)])
+def test_every_tuned_variant_and_pass2_width_gives_the_same_bits(smooth, force_width):
+    """Tables naming the 32 x 16 z-march (at a short z chunk), the two-voxel
+    pass 2 or the tile smoothing, installed in a context: the registration
+    equals an untuned context's bit for bit (a schedule picks kernels, never
+    results)."""
+    c = phantom.make_case("headneck256", shape=(20, 48, 64))
+    kw = dict(levels=2, iters=[6, 5], lam=c.lam, sign=c.signs, stop_mode=cg.CGDIR_STOP_FIXED)
+    with cg.Context(0) as a:
+        ref, _ = single(a, c, kw)
+        tab = a.autotune(c.shape, c.k, 2)
+    forced = [dict(t, smooth=smooth, smooth_zchunk=3 if smooth != "tile" else 0, force_width=force_width,
+                   force_zchunk=max(1, t["force_zchunk"]))
+              for t in tab]
+    with cg.Context(0) as b:
+        b.load_tuning(forced)
+        assert all(t["smooth"] == smooth and t["force_width"] == force_width for t in b.tuning())
+        got, _ = single(b, c, kw)
+    assert torch.equal(ref, got)
 
 
 def test_shared_gpu_registrations_take_the_per_step_schedule():
