@@ -152,6 +152,20 @@ def test_auto_sign_matches_oracle(ctx):
     assert got == oracle.auto_sign(c.static, c.static_masks)
 
 
+@pytest.mark.parametrize("flip, sign", [(False, -1), (True, 1)])
+def test_auto_sign_shell_fixture(ctx, flip, sign):
+    """The layered fixture whose sign flips with any other shell (distance 1,
+    distance 3, Euclidean radius 2): the device takes the oracle's reading."""
+    n = 16
+    idx = np.indices((n, n, n))
+    d = np.max(np.maximum(np.maximum(6 - idx, idx - 9), 0), axis=0)
+    T = np.select([d == 0, d == 1, d == 2], [0.0, -100.0, 110.0], default=-1000.0)
+    T = -T if flip else T
+    m = (d == 0).astype(np.uint8)[None]
+    assert oracle.auto_sign(T, m) == [sign]
+    assert ctx.auto_sign(dev(T.astype(np.float32)), dev(pack(m)), 1) == [sign]
+
+
 @pytest.mark.parametrize("sigma", [1.0, 0.6, 2.0, 0.0])
 @pytest.mark.parametrize("shape", [(9, 21, 45), (17, 33, 70), (1, 1, 1), (2, 3, 1), (9, 21, 44),
                                    (17, 33, 72), (30, 8, 4), (3, 5, 8)])

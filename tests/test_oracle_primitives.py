@@ -301,6 +301,29 @@ def test_auto_sign_follows_roi_contrast():
     assert oracle.auto_sign(T, m) == [1, -1]
 
 
+def shell_sign_fixture(flip=False):
+    """A 4^3 ROI (value 0) wrapped in layers at Chebyshev distance 1 (-100),
+    2 (+110) and 3 or more (-1000) from it, or all values negated.  The shell
+    of the sign rule (distance 1 or 2) averages +38.75 (-38.75 flipped), but a
+    shell of distance 1 alone averages -100, one of distance 3 about -503,
+    and a Euclidean shell of radius 2 (the faces of layer 2 only) -18.7: each
+    of those readings gives the other sign."""
+    n = 16
+    idx = np.indices((n, n, n))
+    d = np.max(np.maximum(np.maximum(6 - idx, idx - 9), 0), axis=0)   # Chebyshev distance to [6, 9]^3
+    T = np.select([d == 0, d == 1, d == 2], [0.0, -100.0, 110.0], default=-1000.0)
+    if flip:
+        T = -T
+    m = (d == 0).astype(np.uint8)[None]
+    return T, m
+
+
+@pytest.mark.parametrize("flip, sign", [(False, -1), (True, 1)])
+def test_auto_sign_shell_is_chebyshev_distance_two(flip, sign):
+    T, m = shell_sign_fixture(flip)
+    assert oracle.auto_sign(T, m) == [sign]
+
+
 # ------------------------------------------------------------------ RMS-ID ---
 def test_rms_id_brute_force_over_enumerated_uroi_voxels():
     w = RNG.normal(size=(4, 5, 6))
