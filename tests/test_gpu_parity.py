@@ -123,8 +123,10 @@ def test_restrict_image_and_bits(ctx, shape):
     assert np.array_equal(got.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("shape", [(5, 11, 23), (1, 1, 1), (4, 4, 4)])
+@pytest.mark.parametrize("shape", [(5, 11, 23), (1, 1, 1), (4, 4, 4), (9, 13, 70), (12, 20, 33)])
 def test_prolong(ctx, shape):
+    """Several 64 x 8 x 8 fine tiles with ragged tails in x, y and z, odd and
+    even fine sizes."""
     fine = tuple(2 * s - (i % 2) for i, s in enumerate(shape))   # odd and even fine sizes
     uc = rand_field(shape)
     close_elementwise(host(ctx.prolong(dev(uc), fine)), oracle.prolong(uc, fine))
