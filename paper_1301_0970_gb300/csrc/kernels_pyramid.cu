@@ -279,7 +279,7 @@ __global__ void k_uroi_dilate(const uint32_t *__restrict__ zbits, int rz, int nx
         for (int dz = -rz; dz <= rz; ++dz) {
             const int zz = z + dz;
             if (zz < 0 || zz >= nz) continue;
-            hit |= (__ldg(zbits + i + (ptrdiff_t)dz * (ptrdiff_t)nxy) >> (dz + rz)) & 1u;
+            hit |= ((uint32_t)__ldg(zbits + i + (ptrdiff_t)dz * (ptrdiff_t)nxy) >> (dz + rz)) & 1u;
         }
         out[i] = (uint8_t)hit;
     }
@@ -312,8 +312,11 @@ __global__ void k_uroi_rows_r(const uint8_t *__restrict__ sbits, unsigned mask, 
     rowdist[rb + x] = (uint8_t)d;
 }
 
+// W: the z-mask word, 16 bits where 2 rz + 1 <= 16 (half the bytes written
+// here and read by the z pass), else 32.
+template <typename W>
 __global__ void k_uroi_planes_r(const uint8_t *__restrict__ rowdist, const __grid_constant__ UroiZsets t, int ry,
-                                int nx, int ny, int nz, uint32_t *__restrict__ zbits) {
+                                int nx, int ny, int nz, W *__restrict__ zbits) {
     const int x = blockIdx.x * RB + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= nx) return;
     const size_t i = vox(x, y, z, nx, ny);
@@ -324,14 +327,15 @@ __global__ void k_uroi_planes_r(const uint8_t *__restrict__ rowdist, const __gri
         const int r = __ldg(rowdist + i + (ptrdiff_t)dy * nx);
         if (r != 255) b |= t.zs[dy + ry][r];
     }
-    zbits[i] = b;
+    zbits[i] = (W)b;
 }
 
 // Pass 3 marching z: a thread owns an x position of a row and takes kUroiZc
 // consecutive planes, so each z-mask word it reads for one plane is read
 // again, from L1, for the next 2 rz planes.
 constexpr int kUroiZc = 16;
-__global__ void k_uroi_dilate_r(const uint32_t *__restrict__ zbits, int rz, int nx, int ny, int nz,
+template <typename W>
+__global__ void k_uroi_dilate_r(const W *__restrict__ zbits, int rz, int nx, int ny, int nz,
                                 uint8_t *__restrict__ out) {
     const int x = blockIdx.x * RB + threadIdx.x, y = blockIdx.y;
     if (x >= nx) return;
@@ -553,9 +557,15 @@ cudaError_t launch_uroi(const uint8_t *sbits, int k, int nx, int ny, int nz, con
             }
         const dim3 g = row_grid(nx, ny, nz);
         k_uroi_rows_r<<<g, RB, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist); note_launch();
-        k_uroi_planes_r<<<g, RB, 0, s>>>(rowdist, zt, t.ry, nx, ny, nz, zbits); note_launch();
         const dim3 gz(g.x, g.y, (unsigned)((nz + kUroiZc - 1) / kUroiZc));
-        k_uroi_dilate_r<<<gz, RB, 0, s>>>(zbits, t.rz, nx, ny, nz, out); note_launch();
+        if (2 * t.rz + 1 <= 16) {
+            uint16_t *z16 = reinterpret_cast<uint16_t *>(zbits);
+            k_uroi_planes_r<uint16_t><<<g, RB, 0, s>>>(rowdist, zt, t.ry, nx, ny, nz, z16); note_launch();
+            k_uroi_dilate_r<uint16_t><<<gz, RB, 0, s>>>(z16, t.rz, nx, ny, nz, out); note_launch();
+        } else {
+            k_uroi_planes_r<uint32_t><<<g, RB, 0, s>>>(rowdist, zt, t.ry, nx, ny, nz, zbits); note_launch();
+            k_uroi_dilate_r<uint32_t><<<gz, RB, 0, s>>>(zbits, t.rz, nx, ny, nz, out); note_launch();
+        }
         return cudaGetLastError();
     }
     k_uroi_rows<<<flat_grid(N), 256, 0, s>>>(sbits, mask, t.rx, nx, ny, nz, rowdist); note_launch();

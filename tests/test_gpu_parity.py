@@ -133,6 +133,7 @@ def test_prolong(ctx, shape):
 
 
 @pytest.mark.parametrize("spacing,margin", [((1.97, 1.97, 2.5), 10.0), ((3.94, 3.94, 5.0), 10.0),
+                                            ((1.0, 1.0, 1.0), 10.0),    # 21 z offsets: 32-bit z masks
                                             ((1.0, 1.0, 1.0), 3.0), ((2.0, 1.5, 1.0), 0.0)])
 def test_uroi_bit_exact(ctx, spacing, margin):
     shape = (19, 27, 41)
