@@ -606,30 +606,6 @@ __global__ void __launch_bounds__(NT, 3) k_force_pass(ForceArgs a, int zchunk) {
 // Pass 2 with two voxels per thread (columns x, x+1; x even): the stencil
 // loads, the static-side loads and the du stores move as pairs, which halves
 // their instruction count and address arithmetic.  Needs an even nx.
-template <typename IT>
-struct ImgPair;
-template <>
-struct ImgPair<float> {
-    static __device__ __forceinline__ void ld(const float *p, float &a, float &b) {
-        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-        a = v.x; b = v.y;
-    }
-};
-template <>
-struct ImgPair<__half> {
-    static __device__ __forceinline__ void ld(const __half *p, float &a, float &b) {
-        const __half2 v = __ldg(reinterpret_cast<const __half2 *>(p));
-        a = __low2float(v); b = __high2float(v);
-    }
-};
-template <>
-struct ImgPair<__nv_bfloat16> {
-    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float &a, float &b) {
-        const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
-        a = __low2float(v); b = __high2float(v);
-    }
-};
-
 struct PlaneLoads2 {
     float2 wp, wym, wyp;       // I0~ pairs at z+1, y-1, y+1
     float wxm, wxp;            // I0~ at x-1 and x+2 (clamped)
@@ -665,7 +641,9 @@ __device__ __forceinline__ void plane_load2(const ForceArgs &a, int ic, int ip, 
         L.t16 = __ldg(reinterpret_cast<const unsigned *>(static_cast<const IT *>(a.T0) + ic));
         L.t0 = L.t1 = 0.f;
     } else {
-        ImgPair<float>::ld(static_cast<const float *>(a.T0) + ic, L.t0, L.t1);
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(static_cast<const float *>(a.T0) + ic));
+        L.t0 = t.x;
+        L.t1 = t.y;
         L.t16 = 0u;
     }
     L.ur = a.uroi ? (unsigned)__ldg(reinterpret_cast<const unsigned short *>(a.uroi + ic)) : 0x0101u;

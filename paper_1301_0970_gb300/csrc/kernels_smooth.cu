@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(NT) k_smooth_tile(const float *__restrict__ in
                                                     const int *stop_flag) {
     if (stop_flag && *stop_flag) return;
     using G = TileGeom<R>;
-    constexpr int K = 2 * R + 1, AX = G::AX, AY = G::AY, AZ = G::AZ;
+    constexpr int K = 2 * R + 1, AX = G::AX, AY = G::AY;
     extern __shared__ float sm[];
     float *A = sm, *B = sm + G::IN;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
