@@ -7,9 +7,12 @@ synthetic case: 512 x 512 x 160 float32 CT, 6 structure masks, 3 levels with
 100 / 50 / 25 iterations, FIXED stopping (the largest single-GPU workload).
 Metric: voxel-iterations/s = sum over levels of (voxels x iterations) per
 step / step time.  The same JSON line carries the 256 x 256 x 96
-head-and-neck case as a secondary key and, under "batched", the uneven-size
-mix of 32 registrations run as one batch with FP16 image storage against
-plain FP32 registrations one at a time.
+head-and-neck case as a secondary key, under "batched" the uneven-size mix
+of 32 registrations run as one batch with FP16 image storage against plain
+FP32 registrations one at a time, and under "e2e" the same registration
+through the public API from pinned host buffers, copies included (two in
+flight through cgdir_submit / cgdir_wait, and one at a time through
+cgdir_register).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgdir|reference]
 
