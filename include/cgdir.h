@@ -463,15 +463,19 @@ int cgdir_selftest_wait_timeout(cgdir_ctx *ctx, int limit_us);
 
 /* ---- autotuner (not in the paper: an execution choice) --------------------
  * For each level shape of a pyramid it times, on synthetic data of that
- * shape, the candidate configurations of the smoothing with the composite
- * update (steps 2-4 of an iteration: TMA z-march with three z-chunk
- * lengths, 3-D shared-memory tile, split xy + z kernels with the update in
- * the z pass) and of the force stencil pass (three z-chunk lengths) on
- * ctx's stream and keeps the fastest, then times the fused schedule against
- * it.  Later registrations of those shapes use the choices: cgdir_register
- * the fused schedule where it won, batched and served registrations (which
- * share the GPU, so throughput counts) the best per-step schedule.  Only
- * the kernels change: every choice gives the same bits.  Blocking. */
+ * shape shaped like a registration's, the candidate configurations of the
+ * force stencil pass (four z-chunk lengths, four or two voxels per thread)
+ * and of the smoothing with the composite update (steps 2-4 of an
+ * iteration, timed behind a force step: the 64 x 16 TMA z-march with the
+ * volume in 1 to 16 z chunks, the 32 x 16 one with 2, 4 and 8, 3-D
+ * shared-memory tile, split xy + z kernels with the update in the z pass)
+ * on ctx's stream and keeps the fastest, then times the fused schedule
+ * against it.  Later registrations of those shapes use the choices:
+ * cgdir_register, and a request submitted on an idle GPU, the fused
+ * schedule where it won; batched registrations and requests submitted while
+ * others run (they share the GPU, so throughput counts) the best per-step
+ * schedule.  Only the kernels change: every choice gives the same bits.
+ * Blocking. */
 #define CGDIR_SMOOTH_MARCH 1
 #define CGDIR_SMOOTH_TILE  2
 #define CGDIR_SMOOTH_SPLIT 3
